@@ -1,0 +1,954 @@
+/*
+ * mmx_oracle.c -- plain, slow, FP64 CPU oracle of the coupled
+ * electrodynamics-micromagnetics scheme of Yao, Jambunathan, Zeng & Nonaka,
+ * "A Massively Parallel Time-Domain Coupled Electrodynamics-Micromagnetics
+ * Solver" (arXiv 2103.12819).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the reference the CUDA library is
+ * checked against.  Only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg may load it; the product path never does.  It shares no
+ * code, header, constant or helper with the CUDA library.
+ *
+ * What it computes (paper Sec. 3):
+ *   - Yee staggering (Sec. 3.1): E on edges, normal H on faces, all three
+ *     components of M on every face; transverse H on a face is the
+ *     four-point average of the nearest values.
+ *   - materials evaluated at cell centres and averaged to edges (eps, sigma)
+ *     and faces (mu, Ms, alpha, gamma); M given at cell centres, averaged to
+ *     faces and renormalised (Sec. 3.1).
+ *   - leapfrog H(n -> n+1/2), E(n -> n+1), H(n+1/2 -> n+1) (Sec. 3.2).
+ *   - Step 2, the Ampere update with sigma and a soft J source (Sec. 3.2.1).
+ *   - Steps 1/3 of the second-order scheme (Sec. 3.2.2): trapezoidal LLG
+ *     solved with the closed form of Eqs. llg_tra4-llg_tra6, renormalised by
+ *     N(M) = M Ms/|M|, H from Eq. iterate_H, iterated until the domain-wide
+ *     max of |M^r - M^(r-1)|/Ms drops below the tolerance.  Non-magnetic
+ *     faces (Ms = 0) skip the iteration and use mu instead of mu0.
+ *   - Steps 1/3 of the first-order scheme (Sec. 3.2.1, Eq. LLG_scalar with
+ *     forward Euler, Eq. H_update).
+ *   - periodic, PEC and z-PML boundaries (Sec. 3.2.3); soft and hard sources.
+ *
+ * Readings where the paper is silent or garbled (each one is listed in the
+ * design notes of the repository):
+ *   R1  gamma is stored as |gamma|; b = M - kappa M x Heff and
+ *       a = -(kappa Heff + alpha/Ms M^n) with kappa = mu0 |gamma| dt/4.
+ *   R2  residual = max over magnetic faces and components of
+ *       |M_c^r - M_c^(r-1)| / Ms_face; stop at the first r with residual < tol;
+ *       at least one iteration always runs; max_iter caps it.
+ *   R3  Jacobi lagging: H_eff^(r-1) uses every face's previous iterate;
+ *       H^(r=0) = H^n on every face, non-magnetic faces hold their final
+ *       value from r = 1 on.
+ *   R4  transverse averages drop neighbours outside a non-periodic wall
+ *       (2-point average there); periodic axes wrap.
+ *   R5  material averages are arithmetic means of the existing adjacent cells.
+ *   R6  magnetic face <=> Ms_face > 0; magnetic faces use mu0.
+ *   R7  PEC: tangential E and normal H are zero on wall edges/faces after
+ *       every update (also on magnetic wall faces, whose M still evolves).
+ *   R8  z-PML, split field, two-step and time-centred (the paper's PML-2SC,
+ *       Sec. 3.2.3): Ex, Ey, Hx, Hy are split into a z-derivative part and
+ *       the rest; each part gets its macroscopic update; the z part is
+ *       multiplied by exp(-sigma_z tau/(2 eps0)) before and again after its
+ *       update, tau = dt for E and dt/2 for each H half step (the magnetic
+ *       conductivity is matched: sigma_m/mu0 = sigma_z/eps0);
+ *       sigma_z = smax (d/L)^3, smax = -4 eps0 c ln(1e-8)/(2L), L = npml dz;
+ *       PEC behind the layers.
+ *   R9  soft J at t = (n+1/2) dt; amp exp(-(t-t0)^2/(2 tp^2)) cos(2 pi f0 t);
+ *       plane source profile sin(pi x/W) (TE10); hard E after the E update at
+ *       t^(n+1), hard H after each H half step at its end time.
+ *   R10 first-order scheme: each half step advances M by dt/2 (the printed
+ *       "Delta t" is read as the half step).
+ *   R11 on a periodic axis the node index n mirrors node index 0.
+ *   R12 initial M on a face whose averaged M is below 1e-6 Ms_face takes the
+ *       lower-index cell's direction; a magnetic face left without any
+ *       direction is an input error.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* CODATA 2018 mu0 and the exact speed of light; eps0 = 1/(mu0 c^2). */
+#define ORC_MU0 1.25663706212e-6
+#define ORC_C0 299792458.0
+#define ORC_PI 3.14159265358979323846
+
+enum { BC_PERIODIC = 0, BC_PEC = 1, BC_PML = 2 };
+enum { ORC_OK = 0, ORC_ERR_INVALID = -1, ORC_ERR_OOM = -2, ORC_ERR_NOT_CONVERGED = -4, ORC_ERR_NONFINITE = -5 };
+enum { SRC_POINT_J = 0, SRC_PLANE_J = 1, SRC_HARD_E = 2, SRC_HARD_H = 3 };
+
+typedef struct { int n[3]; double *v; } grid3;
+
+typedef struct { int kind, comp, i, j, k; double amp, f0, tp, t0; } orc_source;
+
+typedef struct orc_sim {
+    int n[3];
+    double d[3], dt;
+    int bc[3], npml, order, max_iter;
+    double tol, h0[3];
+    long long step;
+    grid3 E[3], H[3], M[3][3];      /* M[face family][component] */
+    grid3 Ez_part[2], Hz_part[2];   /* z-derivative parts of Ex, Ey and Hx, Hy (PML) */
+    grid3 eps[3], sig[3];           /* eps_r and sigma on E edges */
+    grid3 mur[3], ms[3], alp[3], gam[3];   /* mu_r, Ms, alpha, |gamma| on faces */
+    grid3 Hhalf[3];                 /* non-magnetic end-of-half-step H */
+    long long nmag[3], *mag[3];     /* flat indices of magnetic faces per family */
+    int *magix[3];                  /* (i, j, k) of each magnetic face */
+    double *C[3], *Bv[3], *Mn[3], *Mr[3], *Hr[3];  /* per magnetic face work */
+    orc_source *src;
+    int nsrc;
+    int *iters;
+    long long niters, cap_iters;
+    double last_residual;
+} orc_sim;
+
+/* ------------------------------------------------------------------ grids */
+
+static double eps0(void) { return 1.0 / (ORC_MU0 * ORC_C0 * ORC_C0); }
+
+static long long gsize(const grid3 *g) { return (long long)g->n[0] * g->n[1] * g->n[2]; }
+
+static long long at(const grid3 *g, int i, int j, int k)
+{
+    return (long long)i + (long long)g->n[0] * ((long long)j + (long long)g->n[1] * k);
+}
+
+static int galloc(grid3 *g, int ex, int ey, int ez)
+{
+    g->n[0] = ex; g->n[1] = ey; g->n[2] = ez;
+    g->v = (double *)calloc((size_t)gsize(g) > 0 ? (size_t)gsize(g) : 1, sizeof(double));
+    return g->v ? 0 : -1;
+}
+
+/* Edge of component c: nodal on the two other axes, cell-centred along c. */
+static void edge_ext(const orc_sim *s, int c, int e[3])
+{
+    for (int a = 0; a < 3; a++) e[a] = s->n[a] + (a == c ? 0 : 1);
+}
+
+/* Face of family d (normal d): nodal along d, cell-centred on the others. */
+static void face_ext(const orc_sim *s, int d, int e[3])
+{
+    for (int a = 0; a < 3; a++) e[a] = s->n[a] + (a == d ? 1 : 0);
+}
+
+/* Index of a cell-centred neighbour along axis a (idx in [-1, n]); -1 when it
+ * falls outside a non-periodic domain, wrapped on a periodic axis. */
+static int cell_nb(const orc_sim *s, int a, int idx)
+{
+    if (idx >= 0 && idx < s->n[a]) return idx;
+    if (s->bc[a] == BC_PERIODIC) return (idx + s->n[a]) % s->n[a];
+    return -1;
+}
+
+static int nonperiodic_wall(const orc_sim *s, int a, int idx)
+{
+    return s->bc[a] != BC_PERIODIC && (idx == 0 || idx == s->n[a]);
+}
+
+/* PEC (or PEC-backed PML) edge: E component c tangential to a wall. */
+static int wall_edge(const orc_sim *s, int c, const int ix[3])
+{
+    for (int a = 0; a < 3; a++)
+        if (a != c && nonperiodic_wall(s, a, ix[a])) return 1;
+    return 0;
+}
+
+/* Wall face: normal H of family d on a non-periodic wall. */
+static int wall_face(const orc_sim *s, int d, const int ix[3])
+{
+    return nonperiodic_wall(s, d, ix[d]);
+}
+
+/* On a periodic axis node index n is a copy of node index 0 (reading R11). */
+static int periodic_duplicate(const orc_sim *s, const grid3 *g, const int ix[3])
+{
+    for (int a = 0; a < 3; a++)
+        if (s->bc[a] == BC_PERIODIC && g->n[a] == s->n[a] + 1 && ix[a] == s->n[a]) return 1;
+    return 0;
+}
+
+static void sync_periodic(const orc_sim *s, grid3 *g)
+{
+    for (int a = 0; a < 3; a++) {
+        if (s->bc[a] != BC_PERIODIC || g->n[a] != s->n[a] + 1) continue;
+        /* visit only the plane ix[a] = n[a] and copy from ix[a] = 0 */
+        int b = (a + 1) % 3, c = (a + 2) % 3;
+        for (int u = 0; u < g->n[b]; u++)
+            for (int v = 0; v < g->n[c]; v++) {
+                int dst[3], src[3];
+                dst[a] = s->n[a]; dst[b] = u; dst[c] = v;
+                src[a] = 0; src[b] = u; src[c] = v;
+                g->v[at(g, dst[0], dst[1], dst[2])] = g->v[at(g, src[0], src[1], src[2])];
+            }
+    }
+}
+
+/* ------------------------------------------------------------- materials */
+
+static long long cell_at(const orc_sim *s, const int c[3])
+{
+    return (long long)c[0] + (long long)s->n[0] * ((long long)c[1] + (long long)s->n[1] * c[2]);
+}
+
+/* Arithmetic mean of the existing cells adjacent to an edge of component c
+ * (up to 4 cells) or to a face of family d (up to 2 cells) -- reading R5. */
+static double edge_mean(const orc_sim *s, const double *cell, int c, const int ix[3])
+{
+    int a1 = (c + 1) % 3, a2 = (c + 2) % 3;
+    double sum = 0.0;
+    int cnt = 0;
+    for (int o1 = -1; o1 <= 0; o1++)
+        for (int o2 = -1; o2 <= 0; o2++) {
+            int cc[3];
+            cc[c] = ix[c];
+            cc[a1] = cell_nb(s, a1, ix[a1] + o1);
+            cc[a2] = cell_nb(s, a2, ix[a2] + o2);
+            if (cc[a1] < 0 || cc[a2] < 0) continue;
+            sum += cell[cell_at(s, cc)];
+            cnt++;
+        }
+    return sum / cnt;
+}
+
+static double face_mean(const orc_sim *s, const double *cell, int d, const int ix[3])
+{
+    double sum = 0.0;
+    int cnt = 0;
+    for (int o = -1; o <= 0; o++) {
+        int cc[3] = {ix[0], ix[1], ix[2]};
+        cc[d] = cell_nb(s, d, ix[d] + o);
+        if (cc[d] < 0) continue;
+        sum += cell[cell_at(s, cc)];
+        cnt++;
+    }
+    return sum / cnt;
+}
+
+/* ---------------------------------------------------------------- create */
+
+static int alloc_fields(orc_sim *s)
+{
+    int e[3], rc = 0;
+    for (int c = 0; c < 3; c++) {
+        edge_ext(s, c, e);
+        rc |= galloc(&s->E[c], e[0], e[1], e[2]);
+        rc |= galloc(&s->eps[c], e[0], e[1], e[2]);
+        rc |= galloc(&s->sig[c], e[0], e[1], e[2]);
+    }
+    for (int d = 0; d < 3; d++) {
+        face_ext(s, d, e);
+        rc |= galloc(&s->H[d], e[0], e[1], e[2]);
+        rc |= galloc(&s->Hhalf[d], e[0], e[1], e[2]);
+        rc |= galloc(&s->mur[d], e[0], e[1], e[2]);
+        rc |= galloc(&s->ms[d], e[0], e[1], e[2]);
+        rc |= galloc(&s->alp[d], e[0], e[1], e[2]);
+        rc |= galloc(&s->gam[d], e[0], e[1], e[2]);
+        for (int c = 0; c < 3; c++) rc |= galloc(&s->M[d][c], e[0], e[1], e[2]);
+    }
+    for (int c = 0; c < 2; c++) {
+        edge_ext(s, c, e);
+        rc |= galloc(&s->Ez_part[c], e[0], e[1], e[2]);
+        face_ext(s, c, e);
+        rc |= galloc(&s->Hz_part[c], e[0], e[1], e[2]);
+    }
+    return rc;
+}
+
+static void free_mag(orc_sim *s)
+{
+    for (int d = 0; d < 3; d++) {
+        free(s->mag[d]); free(s->magix[d]); free(s->C[d]); free(s->Bv[d]); free(s->Mn[d]); free(s->Mr[d]); free(s->Hr[d]);
+        s->mag[d] = NULL; s->magix[d] = NULL; s->C[d] = s->Bv[d] = s->Mn[d] = s->Mr[d] = s->Hr[d] = NULL;
+        s->nmag[d] = 0;
+    }
+}
+
+void orc_destroy(orc_sim *s);
+
+orc_sim *orc_create(int nx, int ny, int nz, double dx, double dy, double dz, double dt,
+                    const int *bc, int npml, int order, double tol, int max_iter)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || !(dx > 0) || !(dy > 0) || !(dz > 0) || !(dt > 0)) return NULL;
+    if (order != 1 && order != 2) return NULL;
+    if (max_iter < 1 || !(tol > 0)) return NULL;
+    for (int a = 0; a < 3; a++) {
+        if (bc[a] < 0 || bc[a] > 2) return NULL;
+        if (bc[a] == BC_PML && a != 2) return NULL;   /* PML only at the z ends */
+    }
+    if (bc[2] == BC_PML && (npml < 1 || 2 * npml >= nz)) return NULL;
+    orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
+    if (!s) return NULL;
+    s->n[0] = nx; s->n[1] = ny; s->n[2] = nz;
+    s->d[0] = dx; s->d[1] = dy; s->d[2] = dz;
+    s->dt = dt;
+    for (int a = 0; a < 3; a++) s->bc[a] = bc[a];
+    s->npml = bc[2] == BC_PML ? npml : 0;
+    s->order = order;
+    s->tol = tol;
+    s->max_iter = max_iter;
+    if (alloc_fields(s)) { orc_destroy(s); return NULL; }
+    /* default materials: vacuum */
+    for (int c = 0; c < 3; c++)
+        for (long long q = 0; q < gsize(&s->eps[c]); q++) s->eps[c].v[q] = 1.0;
+    for (int d = 0; d < 3; d++)
+        for (long long q = 0; q < gsize(&s->mur[d]); q++) s->mur[d].v[q] = 1.0;
+    return s;
+}
+
+void orc_destroy(orc_sim *s)
+{
+    if (!s) return;
+    for (int c = 0; c < 3; c++) { free(s->E[c].v); free(s->eps[c].v); free(s->sig[c].v); }
+    for (int d = 0; d < 3; d++) {
+        free(s->H[d].v); free(s->Hhalf[d].v); free(s->mur[d].v); free(s->ms[d].v);
+        free(s->alp[d].v); free(s->gam[d].v);
+        for (int c = 0; c < 3; c++) free(s->M[d][c].v);
+    }
+    for (int c = 0; c < 2; c++) { free(s->Ez_part[c].v); free(s->Hz_part[c].v); }
+    free_mag(s);
+    free(s->src);
+    free(s->iters);
+    free(s);
+}
+
+/* PML conductivity at z coordinate z (reading R8); 0 outside the layers. */
+static double pml_sigma(const orc_sim *s, double z)
+{
+    if (s->npml <= 0) return 0.0;
+    double L = s->npml * s->d[2];
+    double zlo = L, zhi = (s->n[2] - s->npml) * s->d[2];
+    double depth;
+    if (z < zlo) depth = (zlo - z) / L;
+    else if (z > zhi) depth = (z - zhi) / L;
+    else return 0.0;
+    double smax = -(3.0 + 1.0) * eps0() * ORC_C0 * log(1e-8) / (2.0 * L);
+    return smax * depth * depth * depth;
+}
+
+static void unravel(const grid3 *g, long long q, int ix[3]);
+
+/* Build the per-family lists of magnetic faces (Ms_face > 0, reading R6). */
+static int build_mag(orc_sim *s)
+{
+    free_mag(s);
+    for (int d = 0; d < 3; d++) {
+        long long cnt = 0, N = gsize(&s->ms[d]);
+        for (long long q = 0; q < N; q++) cnt += s->ms[d].v[q] > 0.0;
+        s->nmag[d] = cnt;
+        size_t m = (size_t)(cnt > 0 ? cnt : 1);
+        s->mag[d] = (long long *)malloc(m * sizeof(long long));
+        s->magix[d] = (int *)malloc(3 * m * sizeof(int));
+        s->C[d] = (double *)malloc(m * sizeof(double));
+        s->Hr[d] = (double *)malloc(m * sizeof(double));
+        s->Bv[d] = (double *)malloc(3 * m * sizeof(double));
+        s->Mn[d] = (double *)malloc(3 * m * sizeof(double));
+        s->Mr[d] = (double *)malloc(3 * m * sizeof(double));
+        if (!s->mag[d] || !s->magix[d] || !s->C[d] || !s->Hr[d] || !s->Bv[d] || !s->Mn[d] || !s->Mr[d]) return ORC_ERR_OOM;
+        cnt = 0;
+        for (long long q = 0; q < N; q++)
+            if (s->ms[d].v[q] > 0.0) {
+                s->mag[d][cnt] = q;
+                unravel(&s->ms[d], q, &s->magix[d][3 * cnt]);
+                cnt++;
+            }
+    }
+    return ORC_OK;
+}
+
+/* Cell-centred materials -> edges/faces (Sec. 3.1, reading R5).  NULL keeps
+ * the default (eps_r 1, sigma 0, mu_r 1, Ms 0, alpha 0, |gamma| 0).  Magnetic
+ * faces start with M = Ms zhat until orc_set_M_cells is called. */
+int orc_set_materials(orc_sim *s, const double *eps_r, const double *sigma, const double *mu_r,
+                      const double *Ms, const double *alpha, const double *gamma_abs)
+{
+    long long ncell = (long long)s->n[0] * s->n[1] * s->n[2];
+    if (Ms && s->npml > 0) {
+        for (int k = 0; k < s->n[2]; k++) {
+            if (k >= s->npml && k < s->n[2] - s->npml) continue;
+            for (long long q = 0; q < (long long)s->n[0] * s->n[1]; q++)
+                if (Ms[(long long)k * s->n[0] * s->n[1] + q] != 0.0) return ORC_ERR_INVALID;
+        }
+    }
+    for (long long q = 0; q < ncell; q++) {
+        if (eps_r && !(eps_r[q] > 0)) return ORC_ERR_INVALID;
+        if (mu_r && !(mu_r[q] > 0)) return ORC_ERR_INVALID;
+        if (Ms && !(Ms[q] >= 0)) return ORC_ERR_INVALID;
+        if (sigma && !(sigma[q] >= 0)) return ORC_ERR_INVALID;
+    }
+    int e[3];
+    for (int c = 0; c < 3; c++) {
+        edge_ext(s, c, e);
+        for (int k = 0; k < e[2]; k++)
+            for (int j = 0; j < e[1]; j++)
+                for (int i = 0; i < e[0]; i++) {
+                    int ix[3] = {i, j, k};
+                    long long q = at(&s->eps[c], i, j, k);
+                    s->eps[c].v[q] = eps_r ? edge_mean(s, eps_r, c, ix) : 1.0;
+                    s->sig[c].v[q] = sigma ? edge_mean(s, sigma, c, ix) : 0.0;
+                }
+    }
+    for (int d = 0; d < 3; d++) {
+        face_ext(s, d, e);
+        for (int k = 0; k < e[2]; k++)
+            for (int j = 0; j < e[1]; j++)
+                for (int i = 0; i < e[0]; i++) {
+                    int ix[3] = {i, j, k};
+                    long long q = at(&s->mur[d], i, j, k);
+                    s->mur[d].v[q] = mu_r ? face_mean(s, mu_r, d, ix) : 1.0;
+                    s->ms[d].v[q] = Ms ? face_mean(s, Ms, d, ix) : 0.0;
+                    s->alp[d].v[q] = alpha ? face_mean(s, alpha, d, ix) : 0.0;
+                    s->gam[d].v[q] = gamma_abs ? face_mean(s, gamma_abs, d, ix) : 0.0;
+                    s->M[d][0].v[q] = 0.0;
+                    s->M[d][1].v[q] = 0.0;
+                    s->M[d][2].v[q] = s->ms[d].v[q];
+                }
+    }
+    return build_mag(s);
+}
+
+void orc_set_bias(orc_sim *s, double hx, double hy, double hz)
+{
+    s->h0[0] = hx; s->h0[1] = hy; s->h0[2] = hz;
+}
+
+/* Renormalisation N(M) = M Ms/|M| (Sec. 3.2). */
+static void renorm(double m[3], double Ms)
+{
+    double nrm = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+    double f = Ms / nrm;
+    m[0] *= f; m[1] *= f; m[2] *= f;
+}
+
+/* Initial M: cell-centred values averaged to faces and renormalised so that
+ * |M| = Ms holds discretely (Sec. 3.1, reading R12). */
+int orc_set_M_cells(orc_sim *s, const double *mx, const double *my, const double *mz)
+{
+    const double *mc[3] = {mx, my, mz};
+    int e[3];
+    for (int d = 0; d < 3; d++) {
+        face_ext(s, d, e);
+        for (int k = 0; k < e[2]; k++)
+            for (int j = 0; j < e[1]; j++)
+                for (int i = 0; i < e[0]; i++) {
+                    int ix[3] = {i, j, k};
+                    long long q = at(&s->ms[d], i, j, k);
+                    double Ms = s->ms[d].v[q];
+                    double m[3] = {0.0, 0.0, 0.0};
+                    if (Ms > 0.0) {
+                        for (int c = 0; c < 3; c++) m[c] = face_mean(s, mc[c], d, ix);
+                        double nrm = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+                        if (!(nrm >= 1e-6 * Ms)) {
+                            /* lower-index cell's direction, else the upper one */
+                            int found = 0;
+                            for (int o = -1; o <= 0 && !found; o++) {
+                                int cc[3] = {i, j, k};
+                                cc[d] = cell_nb(s, d, ix[d] + o);
+                                if (cc[d] < 0) continue;
+                                long long cq = cell_at(s, cc);
+                                double v[3] = {mx[cq], my[cq], mz[cq]};
+                                if (v[0] * v[0] + v[1] * v[1] + v[2] * v[2] > 0.0) {
+                                    m[0] = v[0]; m[1] = v[1]; m[2] = v[2];
+                                    found = 1;
+                                }
+                            }
+                            if (!found) return ORC_ERR_INVALID;
+                        }
+                        renorm(m, Ms);
+                    }
+                    for (int c = 0; c < 3; c++) s->M[d][c].v[q] = m[c];
+                }
+    }
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------------- fields */
+
+static grid3 *field_grid(orc_sim *s, int id)
+{
+    if (id >= 0 && id < 3) return &s->E[id];
+    if (id >= 3 && id < 6) return &s->H[id - 3];
+    if (id >= 6 && id < 15) return &s->M[(id - 6) / 3][(id - 6) % 3];
+    if (id == 15 || id == 16) return &s->Ez_part[id - 15];
+    if (id == 17 || id == 18) return &s->Hz_part[id - 17];
+    return NULL;
+}
+
+long long orc_field_size(orc_sim *s, int id)
+{
+    grid3 *g = field_grid(s, id);
+    return g ? gsize(g) : -1;
+}
+
+int orc_set_field(orc_sim *s, int id, const double *src)
+{
+    grid3 *g = field_grid(s, id);
+    if (!g) return ORC_ERR_INVALID;
+    memcpy(g->v, src, (size_t)gsize(g) * sizeof(double));
+    sync_periodic(s, g);
+    return ORC_OK;
+}
+
+int orc_get_field(orc_sim *s, int id, double *dst)
+{
+    grid3 *g = field_grid(s, id);
+    if (!g) return ORC_ERR_INVALID;
+    memcpy(dst, g->v, (size_t)gsize(g) * sizeof(double));
+    return ORC_OK;
+}
+
+/* Material readback: which = 0-2 eps_r on Ex/Ey/Ez edges, 3-5 sigma on edges,
+ * 6-8 mu_r on x/y/z faces, 9-11 Ms, 12-14 alpha, 15-17 |gamma| on faces. */
+int orc_get_material(orc_sim *s, int which, double *dst)
+{
+    grid3 *g;
+    if (which < 0 || which > 17) return ORC_ERR_INVALID;
+    switch (which / 3) {
+    case 0: g = &s->eps[which % 3]; break;
+    case 1: g = &s->sig[which % 3]; break;
+    case 2: g = &s->mur[which % 3]; break;
+    case 3: g = &s->ms[which % 3]; break;
+    case 4: g = &s->alp[which % 3]; break;
+    default: g = &s->gam[which % 3]; break;
+    }
+    memcpy(dst, g->v, (size_t)gsize(g) * sizeof(double));
+    return ORC_OK;
+}
+
+int orc_add_source(orc_sim *s, int kind, int comp, int i, int j, int k, double amp, double f0,
+                   double tp, double t0)
+{
+    if (kind < 0 || kind > 3 || comp < 0 || comp > 2 || !(tp > 0)) return ORC_ERR_INVALID;
+    int e[3];
+    if (kind == SRC_HARD_H) face_ext(s, comp, e); else edge_ext(s, comp, e);
+    int ix[3] = {i, j, k};
+    if (kind == SRC_PLANE_J) {
+        if (comp == 2 || k < 0 || k > s->n[2]) return ORC_ERR_INVALID;
+    } else {
+        for (int a = 0; a < 3; a++)
+            if (ix[a] < 0 || ix[a] >= e[a]) return ORC_ERR_INVALID;
+    }
+    orc_source *ns = (orc_source *)realloc(s->src, (size_t)(s->nsrc + 1) * sizeof(orc_source));
+    if (!ns) return ORC_ERR_OOM;
+    s->src = ns;
+    orc_source *q = &s->src[s->nsrc++];
+    q->kind = kind; q->comp = comp; q->i = i; q->j = j; q->k = k;
+    q->amp = amp; q->f0 = f0; q->tp = tp; q->t0 = t0;
+    return ORC_OK;
+}
+
+/* Modulated Gaussian waveform (the pulse of Sec. 5.2.1 with a free t0). */
+static double waveform(const orc_source *q, double t)
+{
+    double u = t - q->t0;
+    return q->amp * exp(-u * u / (2.0 * q->tp * q->tp)) * cos(2.0 * ORC_PI * q->f0 * t);
+}
+
+/* Soft J on edge (c, ix) at time t (reading R9). */
+static double j_source(const orc_sim *s, int c, const int ix[3], double t)
+{
+    double J = 0.0;
+    for (int n = 0; n < s->nsrc; n++) {
+        const orc_source *q = &s->src[n];
+        if (q->comp != c) continue;
+        if (q->kind == SRC_POINT_J) {
+            if (q->i == ix[0] && q->j == ix[1] && q->k == ix[2]) J += waveform(q, t);
+        } else if (q->kind == SRC_PLANE_J) {
+            if (ix[2] != q->k) continue;
+            /* x position of the edge measured from the lower x wall */
+            double x = (c == 0 ? ix[0] + 0.5 : (double)ix[0]) * s->d[0];
+            double W = s->n[0] * s->d[0];
+            J += waveform(q, t) * sin(ORC_PI * x / W);
+        }
+    }
+    return J;
+}
+
+/* ------------------------------------------------------------- curls */
+
+/* (curl H) on E edge (c, ix) split into the z-derivative part and the rest;
+ * 2nd-order central differences of the face values (Sec. 3.1). */
+static void curl_h(const orc_sim *s, int c, const int ix[3], double *rest, double *zpart)
+{
+    int i = ix[0], j = ix[1], k = ix[2];
+    const grid3 *Hx = &s->H[0], *Hy = &s->H[1], *Hz = &s->H[2];
+    if (c == 0) {        /* dHz/dy - dHy/dz at (i+1/2, j, k) */
+        int jm = cell_nb(s, 1, j - 1), jp = cell_nb(s, 1, j);
+        int km = cell_nb(s, 2, k - 1), kp = cell_nb(s, 2, k);
+        *rest = (Hz->v[at(Hz, i, jp, k)] - Hz->v[at(Hz, i, jm, k)]) / s->d[1];
+        *zpart = -(Hy->v[at(Hy, i, j, kp)] - Hy->v[at(Hy, i, j, km)]) / s->d[2];
+    } else if (c == 1) { /* dHx/dz - dHz/dx at (i, j+1/2, k) */
+        int im = cell_nb(s, 0, i - 1), ip = cell_nb(s, 0, i);
+        int km = cell_nb(s, 2, k - 1), kp = cell_nb(s, 2, k);
+        *zpart = (Hx->v[at(Hx, i, j, kp)] - Hx->v[at(Hx, i, j, km)]) / s->d[2];
+        *rest = -(Hz->v[at(Hz, ip, j, k)] - Hz->v[at(Hz, im, j, k)]) / s->d[0];
+    } else {             /* dHy/dx - dHx/dy at (i, j, k+1/2) */
+        int im = cell_nb(s, 0, i - 1), ip = cell_nb(s, 0, i);
+        int jm = cell_nb(s, 1, j - 1), jp = cell_nb(s, 1, j);
+        *rest = (Hy->v[at(Hy, ip, j, k)] - Hy->v[at(Hy, im, j, k)]) / s->d[0]
+              - (Hx->v[at(Hx, i, jp, k)] - Hx->v[at(Hx, i, jm, k)]) / s->d[1];
+        *zpart = 0.0;
+    }
+}
+
+/* (curl E) on H face (d, ix), split the same way. */
+static void curl_e(const orc_sim *s, int d, const int ix[3], double *rest, double *zpart)
+{
+    int i = ix[0], j = ix[1], k = ix[2];
+    const grid3 *Ex = &s->E[0], *Ey = &s->E[1], *Ez = &s->E[2];
+    if (d == 0) {        /* dEz/dy - dEy/dz at (i, j+1/2, k+1/2) */
+        *rest = (Ez->v[at(Ez, i, j + 1, k)] - Ez->v[at(Ez, i, j, k)]) / s->d[1];
+        *zpart = -(Ey->v[at(Ey, i, j, k + 1)] - Ey->v[at(Ey, i, j, k)]) / s->d[2];
+    } else if (d == 1) { /* dEx/dz - dEz/dx at (i+1/2, j, k+1/2) */
+        *zpart = (Ex->v[at(Ex, i, j, k + 1)] - Ex->v[at(Ex, i, j, k)]) / s->d[2];
+        *rest = -(Ez->v[at(Ez, i + 1, j, k)] - Ez->v[at(Ez, i, j, k)]) / s->d[0];
+    } else {             /* dEy/dx - dEx/dy at (i+1/2, j+1/2, k) */
+        *rest = (Ey->v[at(Ey, i + 1, j, k)] - Ey->v[at(Ey, i, j, k)]) / s->d[0]
+              - (Ex->v[at(Ex, i, j + 1, k)] - Ex->v[at(Ex, i, j, k)]) / s->d[1];
+        *zpart = 0.0;
+    }
+}
+
+/* H vector on face (d, ix) from face-normal values in Hsrc: the normal
+ * component is the face's own value, each transverse component the mean of
+ * the nearest four values of that family (Sec. 3.1, reading R4). */
+static void h_vector(const orc_sim *s, grid3 *const Hsrc[3], int d, const int ix[3], double h[3])
+{
+    h[d] = Hsrc[d]->v[at(Hsrc[d], ix[0], ix[1], ix[2])];
+    for (int t = 0; t < 3; t++) {
+        if (t == d) continue;
+        double sum = 0.0;
+        int cnt = 0;
+        for (int od = -1; od <= 0; od++) {
+            int nd = cell_nb(s, d, ix[d] + od);
+            if (nd < 0) continue;
+            for (int ot = 0; ot <= 1; ot++) {
+                int q[3] = {ix[0], ix[1], ix[2]};
+                q[d] = nd;
+                q[t] = ix[t] + ot;
+                sum += Hsrc[t]->v[at(Hsrc[t], q[0], q[1], q[2])];
+                cnt++;
+            }
+        }
+        h[t] = sum / cnt;
+    }
+}
+
+static void cross(const double a[3], const double b[3], double r[3])
+{
+    r[0] = a[1] * b[2] - a[2] * b[1];
+    r[1] = a[2] * b[0] - a[0] * b[2];
+    r[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static void unravel(const grid3 *g, long long q, int ix[3])
+{
+    ix[0] = (int)(q % g->n[0]);
+    q /= g->n[0];
+    ix[1] = (int)(q % g->n[1]);
+    ix[2] = (int)(q / g->n[1]);
+}
+
+/* ------------------------------------------------------- Step 2: E update */
+
+/* E^(n+1) = (sigma/2 + eps/dt)^-1 [curl H^(n+1/2) - (sigma/2 - eps/dt) E^n
+ * - J_src^(n+1/2)] on every edge (Sec. 3.2.1, Step 2), with the time-centred
+ * z-PML split of reading R8 and PEC walls held at zero. */
+static void e_update(orc_sim *s)
+{
+    double t = (s->step + 0.5) * s->dt;
+    double e0 = eps0();
+    int e[3];
+    for (int c = 0; c < 3; c++) {
+        grid3 *E = &s->E[c];
+        edge_ext(s, c, e);
+        for (int k = 0; k < e[2]; k++)
+            for (int j = 0; j < e[1]; j++)
+                for (int i = 0; i < e[0]; i++) {
+                    int ix[3] = {i, j, k};
+                    long long q = at(E, i, j, k);
+                    if (periodic_duplicate(s, E, ix)) continue;
+                    if (wall_edge(s, c, ix)) {
+                        E->v[q] = 0.0;
+                        if (c < 2) s->Ez_part[c].v[q] = 0.0;
+                        continue;
+                    }
+                    double rest, zp;
+                    curl_h(s, c, ix, &rest, &zp);
+                    double eps = e0 * s->eps[c].v[q], sg = s->sig[c].v[q];
+                    double den = sg / 2.0 + eps / s->dt;
+                    double keep = sg / 2.0 - eps / s->dt;
+                    double J = j_source(s, c, ix, t);
+                    double sz = (c < 2) ? pml_sigma(s, k * s->d[2]) : 0.0;
+                    if (sz > 0.0) {
+                        double half = exp(-sz * s->dt / (2.0 * e0));
+                        double ez = s->Ez_part[c].v[q];
+                        double er = E->v[q] - ez;
+                        double ez1 = (zp - keep * (ez * half)) / den * half;
+                        double er1 = (rest - keep * er - J) / den;
+                        s->Ez_part[c].v[q] = ez1;
+                        E->v[q] = er1 + ez1;
+                    } else {
+                        E->v[q] = (rest + zp - keep * E->v[q] - J) / den;
+                    }
+                }
+        sync_periodic(s, E);
+        if (c < 2) sync_periodic(s, &s->Ez_part[c]);
+    }
+}
+
+/* ------------------------------------------- Steps 1/3: the H/M half step */
+
+/* Non-magnetic faces: H^(n+1/2) = H^n - dt/(2 mu) curl E (Eq. iterate_H with
+ * mu in place of mu0), time-centred z-PML split per reading R8; wall faces
+ * are zero.  Magnetic faces keep H^n here. */
+static void h_nonmagnetic(orc_sim *s)
+{
+    double e0 = eps0();
+    int e[3];
+    for (int d = 0; d < 3; d++) {
+        grid3 *H = &s->H[d], *Hh = &s->Hhalf[d];
+        face_ext(s, d, e);
+        for (int k = 0; k < e[2]; k++)
+            for (int j = 0; j < e[1]; j++)
+                for (int i = 0; i < e[0]; i++) {
+                    int ix[3] = {i, j, k};
+                    long long q = at(H, i, j, k);
+                    if (periodic_duplicate(s, H, ix)) continue;
+                    if (s->ms[d].v[q] > 0.0) { Hh->v[q] = H->v[q]; continue; }
+                    if (wall_face(s, d, ix)) {
+                        Hh->v[q] = 0.0;
+                        if (d < 2) s->Hz_part[d].v[q] = 0.0;
+                        continue;
+                    }
+                    double rest, zp;
+                    curl_e(s, d, ix, &rest, &zp);
+                    double f = s->dt / (2.0 * ORC_MU0 * s->mur[d].v[q]);
+                    double sz = (d < 2) ? pml_sigma(s, (k + 0.5) * s->d[2]) : 0.0;
+                    if (sz > 0.0) {
+                        double half = exp(-sz * (s->dt / 4.0) / e0);
+                        double hz = s->Hz_part[d].v[q];
+                        double hr = H->v[q] - hz;
+                        double hz1 = (hz * half - f * zp) * half;
+                        double hr1 = hr - f * rest;
+                        s->Hz_part[d].v[q] = hz1;
+                        Hh->v[q] = hr1 + hz1;
+                    } else {
+                        Hh->v[q] = H->v[q] - f * (rest + zp);
+                    }
+                }
+        sync_periodic(s, Hh);
+        if (d < 2) sync_periodic(s, &s->Hz_part[d]);
+    }
+}
+
+/* One H/M half step (Step 1 or Step 3; both use the E currently stored). */
+static int hm_half_step(orc_sim *s)
+{
+    double dt = s->dt;
+    grid3 *Hcur[3] = {&s->H[0], &s->H[1], &s->H[2]};
+    int rc = ORC_OK;
+
+    h_nonmagnetic(s);
+
+    long long nmag = s->nmag[0] + s->nmag[1] + s->nmag[2];
+    if (nmag == 0) {
+        for (int d = 0; d < 3; d++) memcpy(s->H[d].v, s->Hhalf[d].v, (size_t)gsize(&s->H[d]) * sizeof(double));
+        if (s->niters < s->cap_iters) s->iters[s->niters] = 0;
+        s->niters++;
+        s->last_residual = 0.0;
+        return ORC_OK;
+    }
+
+    /* Per magnetic face: C = H^n + M^n_perp - dt/(2 mu0) curl E (Eq. iterate_H),
+     * M^n kept, and b = M^n - kappa M^n x Heff^n (Eq. llg_tra6) with
+     * Heff^n = H0 + H^n (averaged). */
+    for (int d = 0; d < 3; d++) {
+        for (long long m = 0; m < s->nmag[d]; m++) {
+            long long q = s->mag[d][m];
+            const int *ix = &s->magix[d][3 * m];
+            double rest, zp;
+            curl_e(s, d, ix, &rest, &zp);
+            double Mn[3] = {s->M[d][0].v[q], s->M[d][1].v[q], s->M[d][2].v[q]};
+            s->C[d][m] = s->H[d].v[q] + Mn[d] - dt / (2.0 * ORC_MU0) * (rest + zp);
+            for (int c = 0; c < 3; c++) s->Mn[d][3 * m + c] = Mn[c];
+            if (s->order == 2) {
+                double h[3], heff[3], mxh[3];
+                h_vector(s, Hcur, d, ix, h);
+                for (int c = 0; c < 3; c++) heff[c] = s->h0[c] + h[c];
+                double kappa = ORC_MU0 * s->gam[d].v[q] * dt / 4.0;
+                cross(Mn, heff, mxh);
+                for (int c = 0; c < 3; c++) s->Bv[d][3 * m + c] = Mn[c] - kappa * mxh[c];
+            }
+        }
+    }
+
+    if (s->order == 1) {
+        /* First-order scheme (Sec. 3.2.1, Steps 1/3): forward Euler of the
+         * Landau-Lifshitz form (Eq. LLG_scalar) over the half step, N(), then
+         * H from Eq. H_update; no iteration. */
+        for (int d = 0; d < 3; d++) {
+            for (long long m = 0; m < s->nmag[d]; m++) {
+                long long q = s->mag[d][m];
+                const int *ix = &s->magix[d][3 * m];
+                double h[3], heff[3], mxh[3], mxmxh[3];
+                h_vector(s, Hcur, d, ix, h);
+                for (int c = 0; c < 3; c++) heff[c] = s->h0[c] + h[c];
+                double Ms = s->ms[d].v[q], al = s->alp[d].v[q];
+                double gL = s->gam[d].v[q] / (1.0 + al * al);
+                double *Mn = &s->Mn[d][3 * m];
+                cross(Mn, heff, mxh);
+                cross(Mn, mxh, mxmxh);
+                double x[3];
+                for (int c = 0; c < 3; c++)
+                    x[c] = Mn[c] + (dt / 2.0) * (-ORC_MU0 * gL * mxh[c] - al * ORC_MU0 * gL / Ms * mxmxh[c]);
+                renorm(x, Ms);
+                for (int c = 0; c < 3; c++) s->Mr[d][3 * m + c] = x[c];
+                s->Hr[d][m] = wall_face(s, d, ix) ? 0.0 : s->C[d][m] - x[d];
+            }
+        }
+        for (int d = 0; d < 3; d++) {
+            memcpy(s->H[d].v, s->Hhalf[d].v, (size_t)gsize(&s->H[d]) * sizeof(double));
+            for (long long m = 0; m < s->nmag[d]; m++) {
+                long long q = s->mag[d][m];
+                s->H[d].v[q] = s->Hr[d][m];
+                for (int c = 0; c < 3; c++) s->M[d][c].v[q] = s->Mr[d][3 * m + c];
+            }
+            sync_periodic(s, &s->H[d]);
+            for (int c = 0; c < 3; c++) sync_periodic(s, &s->M[d][c]);
+        }
+        if (s->niters < s->cap_iters) s->iters[s->niters] = 1;
+        s->niters++;
+        return ORC_OK;
+    }
+
+    /* Second-order scheme (Sec. 3.2.2): iterate r = 1, 2, ... */
+    int r;
+    double rho = 0.0;
+    for (r = 1;; r++) {
+        /* Jacobi sweep over magnetic faces using H^(r-1) stored in s->H. */
+        rho = 0.0;
+        for (int d = 0; d < 3; d++) {
+            for (long long m = 0; m < s->nmag[d]; m++) {
+                long long q = s->mag[d][m];
+                const int *ix = &s->magix[d][3 * m];
+                double h[3], heff[3];
+                h_vector(s, Hcur, d, ix, h);
+                for (int c = 0; c < 3; c++) heff[c] = s->h0[c] + h[c];
+                double Ms = s->ms[d].v[q], al = s->alp[d].v[q];
+                double kappa = ORC_MU0 * s->gam[d].v[q] * dt / 4.0;
+                const double *Mn = &s->Mn[d][3 * m], *b = &s->Bv[d][3 * m];
+                /* a = -[kappa Heff^(r-1) + alpha/Ms M^n]  (Eq. llg_tra5) */
+                double a[3];
+                for (int c = 0; c < 3; c++) a[c] = -(kappa * heff[c] + al / Ms * Mn[c]);
+                /* M^r = (b + (a.b) a - a x b)/(1 + |a|^2)  (Eq. llg_tra4) */
+                double ab = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+                double aa = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+                double axb[3], x[3];
+                cross(a, b, axb);
+                for (int c = 0; c < 3; c++) x[c] = (b[c] + ab * a[c] - axb[c]) / (1.0 + aa);
+                renorm(x, Ms);
+                for (int c = 0; c < 3; c++) {
+                    double dm = fabs(x[c] - s->M[d][c].v[q]) / Ms;
+                    if (dm > rho) rho = dm;
+                    s->Mr[d][3 * m + c] = x[c];
+                }
+                s->Hr[d][m] = wall_face(s, d, ix) ? 0.0 : s->C[d][m] - x[d];
+            }
+        }
+        /* non-magnetic faces take their final value from r = 1 on (R3) */
+        if (r == 1)
+            for (int d = 0; d < 3; d++)
+                memcpy(s->H[d].v, s->Hhalf[d].v, (size_t)gsize(&s->H[d]) * sizeof(double));
+        for (int d = 0; d < 3; d++)
+            for (long long m = 0; m < s->nmag[d]; m++) {
+                long long q = s->mag[d][m];
+                s->H[d].v[q] = s->Hr[d][m];
+                for (int c = 0; c < 3; c++) s->M[d][c].v[q] = s->Mr[d][3 * m + c];
+            }
+        for (int d = 0; d < 3; d++) {
+            sync_periodic(s, &s->H[d]);
+            for (int c = 0; c < 3; c++) sync_periodic(s, &s->M[d][c]);
+        }
+        if (rho < s->tol) break;
+        if (r >= s->max_iter) { rc = ORC_ERR_NOT_CONVERGED; break; }
+    }
+    s->last_residual = rho;
+    if (s->niters < s->cap_iters) s->iters[s->niters] = r;
+    s->niters++;
+    return rc;
+}
+
+/* ------------------------------------------------------------ sources */
+
+static void hard_e(orc_sim *s, double t)
+{
+    for (int n = 0; n < s->nsrc; n++) {
+        const orc_source *q = &s->src[n];
+        if (q->kind != SRC_HARD_E) continue;
+        grid3 *E = &s->E[q->comp];
+        E->v[at(E, q->i, q->j, q->k)] = waveform(q, t);
+    }
+}
+
+static void hard_h(orc_sim *s, double t)
+{
+    for (int n = 0; n < s->nsrc; n++) {
+        const orc_source *q = &s->src[n];
+        if (q->kind != SRC_HARD_H) continue;
+        grid3 *H = &s->H[q->comp];
+        H->v[at(H, q->i, q->j, q->k)] = waveform(q, t);
+    }
+}
+
+static int all_finite(orc_sim *s)
+{
+    for (int c = 0; c < 3; c++)
+        for (long long q = 0; q < gsize(&s->E[c]); q++)
+            if (!isfinite(s->E[c].v[q])) return 0;
+    for (int d = 0; d < 3; d++) {
+        for (long long q = 0; q < gsize(&s->H[d]); q++)
+            if (!isfinite(s->H[d].v[q])) return 0;
+        for (int c = 0; c < 3; c++)
+            for (long long q = 0; q < gsize(&s->M[d][c]); q++)
+                if (!isfinite(s->M[d][c].v[q])) return 0;
+    }
+    return 1;
+}
+
+/* Advance nsteps full steps: H/M half step with E^n, E update, H/M half step
+ * with E^(n+1) (Sec. 3.2). */
+int orc_step(orc_sim *s, int nsteps)
+{
+    int rc = ORC_OK;
+    if (s->cap_iters < s->niters + 2LL * nsteps) {
+        long long cap = s->niters + 2LL * nsteps + 16;
+        int *ni = (int *)realloc(s->iters, (size_t)cap * sizeof(int));
+        if (!ni) return ORC_ERR_OOM;
+        s->iters = ni;
+        s->cap_iters = cap;
+    }
+    for (int n = 0; n < nsteps; n++) {
+        int r1 = hm_half_step(s);
+        hard_h(s, (s->step + 0.5) * s->dt);
+        e_update(s);
+        hard_e(s, (s->step + 1.0) * s->dt);
+        int r2 = hm_half_step(s);
+        hard_h(s, (s->step + 1.0) * s->dt);
+        s->step++;
+        if (r1 != ORC_OK) rc = r1;
+        if (r2 != ORC_OK) rc = r2;
+    }
+    if (!all_finite(s)) rc = ORC_ERR_NONFINITE;
+    return rc;
+}
+
+/* Iteration counts of every half step so far (1 per half step for the
+ * first-order scheme, 0 with no magnetic faces).  Returns the total count. */
+long long orc_iter_log(orc_sim *s, int *dst, long long cap)
+{
+    long long n = s->niters < cap ? s->niters : cap;
+    if (n > s->cap_iters) n = s->cap_iters;
+    if (dst && n > 0) memcpy(dst, s->iters, (size_t)n * sizeof(int));
+    return s->niters;
+}
+
+double orc_last_residual(orc_sim *s) { return s->last_residual; }
+long long orc_steps_done(orc_sim *s) { return s->step; }
