@@ -1,0 +1,198 @@
+/*
+ * mmx.h -- C ABI of the B300 (sm_103a) coupled electrodynamics-micromagnetics
+ * solver: the Yee-grid Ampere update of E and the iterated trapezoidal
+ * Maxwell-LLG update of H and M of Yao, Jambunathan, Zeng & Nonaka,
+ * "A Massively Parallel Time-Domain Coupled Electrodynamics-Micromagnetics
+ * Solver" (arXiv 2103.12819), Sec. 3.
+ *
+ * Conventions used by every entry point
+ *   - Grid: nx x ny x nz cells of size dx x dy x dz.  Cell (i, j, k) spans
+ *     [i dx, (i+1) dx] x ... ; node indices run 0..n on each axis.
+ *   - Yee locations (Sec. 3.1, Fig. 1): Ex (i+1/2, j, k), Ey (i, j+1/2, k),
+ *     Ez (i, j, k+1/2) on edges; Hx (i, j+1/2, k+1/2), Hy (i+1/2, j, k+1/2),
+ *     Hz (i+1/2, j+1/2, k) on faces; all three components of M on every face
+ *     of all three face families.
+ *   - Host arrays are float64, x fastest: element (i, j, k) of an array with
+ *     extents (ex, ey, ez) is at i + ex*(j + ey*k).  Extents: Ex nx x (ny+1) x
+ *     (nz+1), Ey (nx+1) x ny x (nz+1), Ez (nx+1) x (ny+1) x nz; x-face arrays
+ *     (Hx and the x-face M) (nx+1) x ny x nz, y-face nx x (ny+1) x nz, z-face
+ *     nx x ny x (nz+1).  Cell-centred arrays nx x ny x nz.
+ *   - Field ids: 0-2 Ex, Ey, Ez; 3-5 Hx, Hy, Hz; 6-14 M as (x-face Mx, My,
+ *     Mz), (y-face Mx, My, Mz), (z-face Mx, My, Mz); 15/16 the z-derivative
+ *     parts of Ex/Ey inside the z-PML, 17/18 those of Hx/Hy (zero elsewhere).
+ *   - Units SI: E V/m, H M and the bias A/m, J A/m^2, sigma S/m, |gamma|
+ *     rad/(s T), dt s.
+ *   - Ownership: the library owns all device memory of a context; host
+ *     buffers belong to the caller and are only read (set_*) or written
+ *     (get_*) during the call.
+ *   - Errors: every int-returning entry point returns MMX_OK (0) or a
+ *     negative MMX_ERR_* code; mmx_last_error() gives a message.  Device-side
+ *     conditions (iteration cap reached, non-finite values, a bounded wait
+ *     that gave up) latch in the context and are returned by the next
+ *     synchronising call (mmx_sync, mmx_get_field, mmx_get_stats).  No call
+ *     blocks without bound: every device wait carries an iteration limit.
+ *   - Streams: work is enqueued on the stream given to mmx_create (NULL =
+ *     the legacy default stream).  mmx_step is asynchronous.
+ */
+#ifndef MMX_H_
+#define MMX_H_
+
+#if defined(__GNUC__)
+#define MMX_API __attribute__((visibility("default")))
+#else
+#define MMX_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MMX_OK 0
+#define MMX_ERR_INVALID (-1)        /* bad argument or state */
+#define MMX_ERR_OOM (-2)            /* device allocation failed */
+#define MMX_ERR_CUDA (-3)           /* a CUDA runtime call failed */
+#define MMX_ERR_NOT_CONVERGED (-4)  /* a H/M half step hit max_iter */
+#define MMX_ERR_NONFINITE (-5)      /* a field became NaN/Inf */
+#define MMX_ERR_TIMEOUT (-6)        /* a bounded device wait gave up */
+
+typedef enum { MMX_FP64 = 0, MMX_FP32 = 1 } mmx_precision;
+typedef enum { MMX_BC_PERIODIC = 0, MMX_BC_PEC = 1, MMX_BC_PML = 2 } mmx_bc;
+typedef enum { MMX_PATH_PLAIN = 0, MMX_PATH_FUSED = 1 } mmx_path;
+
+typedef struct mmx_ctx mmx_ctx;
+
+/* Grid, time step and scheme (Sec. 3.1-3.2.3).
+ *   n[3], d[3]  cells and cell size per axis (x, y, z).
+ *   dt          time step (> 0; the caller applies its CFL rule).
+ *   bc[3]       boundary per axis, same on both ends: periodic (Sec. 3.2.3,
+ *               guard-cell exchange), PEC (tangential E and normal H held at
+ *               0), or PML (z axis only: split-field, time-centred PML-2SC
+ *               layers of pml_cells cells inside the grid, PEC behind them).
+ *   order       2 = iterated trapezoidal scheme (Sec. 3.2.2), 1 = first-order
+ *               forward-Euler scheme (Sec. 3.2.1).
+ *   tol         stopping tolerance of the H/M iteration on the domain-wide
+ *               max of |M^r - M^(r-1)|/Ms (Sec. 3.2.2; the paper uses 1e-6).
+ *   max_iter    iteration cap (>= 1, <= 64).
+ *   prec        arithmetic and storage precision of the fields. */
+typedef struct {
+    int n[3];
+    double d[3];
+    double dt;
+    int bc[3];
+    int pml_cells;
+    int order;
+    double tol;
+    int max_iter;
+    int prec;
+} mmx_grid_desc;
+
+/* Source (Sec. 3.2, "soft and hard sources"; waveform of Eq. gaulssian):
+ *   g(t) = amp exp(-(t - t0)^2 / (2 tp^2)) cos(2 pi f0 t).
+ *   kind 0  soft point current J_comp on the edge (i, j, k) of component
+ *           comp, entering the E update at t = (n+1/2) dt.
+ *   kind 1  soft plane current J_comp (comp 0 or 1) on every comp-edge of the
+ *           z node plane k, shaped sin(pi x / (nx dx)) across x (TE10).
+ *   kind 2  hard E: E_comp at edge (i, j, k) is overwritten with g(t^(n+1))
+ *           after every E update.
+ *   kind 3  hard H: H_comp at face (i, j, k) is overwritten with g(t) after
+ *           every H/M half step, t its end time. */
+typedef struct {
+    int kind, comp, i, j, k;
+    double amp, f0, tp, t0;
+} mmx_source_desc;
+
+typedef struct {
+    long long steps;           /* full time steps done */
+    long long half_steps;      /* H/M half steps logged */
+    int iters_min, iters_max;  /* iteration counts over the logged half steps */
+    double last_residual;      /* residual of the last H/M half step */
+    int status;                /* latched device status (MMX_OK or MMX_ERR_*) */
+} mmx_stats;
+
+/* Create a context for the grid in *desc on the current CUDA device.
+ * cuda_stream is a cudaStream_t (NULL = default stream); it must outlive the
+ * context.  All fields start at zero and all materials at vacuum (eps_r 1,
+ * sigma 0, mu_r 1, Ms 0).  Returns MMX_ERR_INVALID for an inconsistent
+ * descriptor, MMX_ERR_OOM when device memory runs out; on failure *out may
+ * still hold a context, usable only with mmx_last_error and mmx_destroy. */
+MMX_API int mmx_create(const mmx_grid_desc *desc, void *cuda_stream, mmx_ctx **out);
+
+/* Cell-centred materials -> Yee locations (Sec. 3.1): eps_r and sigma are
+ * averaged to edges over the adjacent cells, mu_r, Ms, alpha and |gamma| to
+ * faces over the two adjacent cells (existing cells only at non-periodic
+ * walls; periodic axes wrap).  Each pointer is a host array of nx*ny*nz
+ * doubles or NULL for the default (eps_r 1, sigma 0, mu_r 1, Ms 0, alpha 0,
+ * |gamma| 0).  A face is magnetic iff its averaged Ms > 0; magnetic faces
+ * restart at M = Ms zhat.  Ms must be 0 in the PML slabs (the paper's PML is
+ * non-magnetic).  Synchronises the context stream. */
+MMX_API int mmx_set_materials(mmx_ctx *ctx, const double *eps_r, const double *sigma,
+                      const double *mu_r, const double *Ms, const double *alpha,
+                      const double *gamma_abs);
+
+/* Uniform bias field H0 (A/m) added to the effective field of every magnetic
+ * face (Sec. 2: H_eff = H + H0). */
+MMX_API int mmx_set_bias(mmx_ctx *ctx, double h0x, double h0y, double h0z);
+
+/* Initial M from cell-centred values (Sec. 3.1): averaged to each face and
+ * renormalised to the face's Ms (a face whose average is below 1e-6 Ms takes
+ * the lower-index cell's direction).  Host arrays of nx*ny*nz doubles. */
+MMX_API int mmx_set_M_cells(mmx_ctx *ctx, const double *mx, const double *my, const double *mz);
+
+/* Copy a Yee-located field (ids above) from a host float64 array of exactly
+ * n elements (its extent).  On periodic axes node index n is set equal to
+ * node index 0.  FP32 contexts round to nearest. */
+MMX_API int mmx_set_field(mmx_ctx *ctx, int field_id, const double *host, long long n);
+
+/* Copy a Yee-located field to a host float64 array of exactly n elements.
+ * Synchronises the context stream and returns the latched device status. */
+MMX_API int mmx_get_field(mmx_ctx *ctx, int field_id, double *host, long long n);
+
+/* Edge/face material values after averaging: which = 0-2 eps_r on Ex/Ey/Ez
+ * edges, 3-5 sigma on edges, 6-8 mu_r on x/y/z faces, 9-11 Ms, 12-14 alpha,
+ * 15-17 |gamma| on faces.  Host float64 array of the edge/face extent. */
+MMX_API int mmx_get_material(mmx_ctx *ctx, int which, double *host, long long n);
+
+/* Register a source (see mmx_source_desc).  At most 32 per context. */
+MMX_API int mmx_add_source(mmx_ctx *ctx, const mmx_source_desc *src);
+
+/* Select the kernel path: MMX_PATH_PLAIN runs one kernel per update (H/M
+ * half step, E update, H/M half step); MMX_PATH_FUSED (default) fuses the
+ * streaming E and H updates.  Both compute the same scheme. */
+MMX_API int mmx_set_path(mmx_ctx *ctx, int path);
+
+/* Advance nsteps full time steps (Sec. 3.2: H/M half step with E^n, E
+ * update with J at t^(n+1/2), H/M half step with E^(n+1)).  Asynchronous:
+ * returns after enqueueing; the H/M iteration runs to the domain-wide
+ * tolerance on the device with no host round trip.  Device conditions latch
+ * (see mmx_sync). */
+MMX_API int mmx_step(mmx_ctx *ctx, int nsteps);
+
+/* Wait for the context stream and return the latched device status:
+ * MMX_OK, MMX_ERR_NOT_CONVERGED (some half step reached max_iter; the step
+ * went on with the last iterate), MMX_ERR_NONFINITE or MMX_ERR_TIMEOUT.
+ * Reading the status clears it. */
+MMX_API int mmx_sync(mmx_ctx *ctx);
+
+/* Statistics since creation; synchronises. */
+MMX_API int mmx_get_stats(mmx_ctx *ctx, mmx_stats *out);
+
+/* Iteration count of each H/M half step, oldest first (up to cap entries of
+ * the most recent 65536 half steps).  Returns the number written (>= 0) or a
+ * negative error.  Synchronises. */
+MMX_API long long mmx_get_iter_log(mmx_ctx *ctx, int *host, long long cap);
+
+/* Device pointer and element strides of a field's storage: element (i, j, k)
+ * is at ptr[i + sx*j + sy*k] with elements of 8 (FP64) or 4 (FP32) bytes.
+ * Valid until mmx_destroy; contents change under mmx_step. */
+MMX_API int mmx_get_field_device(mmx_ctx *ctx, int field_id, void **ptr, long long *sx, long long *sy);
+
+/* Message of the last error on this context (never NULL). */
+MMX_API const char *mmx_last_error(const mmx_ctx *ctx);
+
+/* Free all device memory of the context (synchronises its stream). */
+MMX_API void mmx_destroy(mmx_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MMX_H_ */

@@ -1,0 +1,261 @@
+"""Python binding of ``libmmx.so``, the sm_103a coupled Maxwell-LLG solver.
+
+Argument marshalling only: every step of the scheme runs in the library's
+CUDA kernels.  The entry points keep the C names (``mmx_create``,
+``mmx_step`` ...); :class:`Solver` wraps one context.  There is no CPU
+fallback: if the shared library is missing or cannot be loaded this module
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmmx.so")
+
+MMX_OK = 0
+ERRORS = {-1: "INVALID", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED", -5: "NONFINITE", -6: "TIMEOUT"}
+FP64, FP32 = 0, 1
+PERIODIC, PEC, PML = 0, 1, 2
+PATH_PLAIN, PATH_FUSED = 0, 1
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("d", ctypes.c_double * 3), ("dt", ctypes.c_double),
+                ("bc", ctypes.c_int * 3), ("pml_cells", ctypes.c_int), ("order", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("prec", ctypes.c_int)]
+
+
+class SourceDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("comp", ctypes.c_int), ("i", ctypes.c_int),
+                ("j", ctypes.c_int), ("k", ctypes.c_int), ("amp", ctypes.c_double),
+                ("f0", ctypes.c_double), ("tp", ctypes.c_double), ("t0", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_longlong), ("half_steps", ctypes.c_longlong),
+                ("iters_min", ctypes.c_int), ("iters_max", ctypes.c_int),
+                ("last_residual", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+EXPORTS = ("mmx_create", "mmx_set_materials", "mmx_set_bias", "mmx_set_M_cells", "mmx_set_field",
+           "mmx_get_field", "mmx_get_material", "mmx_add_source", "mmx_set_path", "mmx_step",
+           "mmx_sync", "mmx_get_stats", "mmx_get_iter_log", "mmx_get_field_device",
+           "mmx_last_error", "mmx_destroy")
+
+_lib = None
+
+
+def lib():
+    """Load libmmx.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libmmx.so is not built: run __graft_entry__.build() (nvcc, sm_103a)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.mmx_create.restype = I
+    L.mmx_create.argtypes = [ctypes.POINTER(GridDesc), P, ctypes.POINTER(P)]
+    L.mmx_set_materials.restype = I
+    L.mmx_set_materials.argtypes = [P, dp, dp, dp, dp, dp, dp]
+    L.mmx_set_bias.restype = I
+    L.mmx_set_bias.argtypes = [P, D, D, D]
+    L.mmx_set_M_cells.restype = I
+    L.mmx_set_M_cells.argtypes = [P, dp, dp, dp]
+    L.mmx_set_field.restype = I
+    L.mmx_set_field.argtypes = [P, I, dp, LL]
+    L.mmx_get_field.restype = I
+    L.mmx_get_field.argtypes = [P, I, dp, LL]
+    L.mmx_get_material.restype = I
+    L.mmx_get_material.argtypes = [P, I, dp, LL]
+    L.mmx_add_source.restype = I
+    L.mmx_add_source.argtypes = [P, ctypes.POINTER(SourceDesc)]
+    L.mmx_set_path.restype = I
+    L.mmx_set_path.argtypes = [P, I]
+    L.mmx_step.restype = I
+    L.mmx_step.argtypes = [P, I]
+    L.mmx_sync.restype = I
+    L.mmx_sync.argtypes = [P]
+    L.mmx_get_stats.restype = I
+    L.mmx_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    L.mmx_get_iter_log.restype = LL
+    L.mmx_get_iter_log.argtypes = [P, ctypes.POINTER(ctypes.c_int), LL]
+    L.mmx_get_field_device.restype = I
+    L.mmx_get_field_device.argtypes = [P, I, ctypes.POINTER(P), ctypes.POINTER(LL), ctypes.POINTER(LL)]
+    L.mmx_last_error.restype = ctypes.c_char_p
+    L.mmx_last_error.argtypes = [P]
+    L.mmx_destroy.restype = None
+    L.mmx_destroy.argtypes = [P]
+    _lib = L
+    return L
+
+
+class MMXError(RuntimeError):
+    def __init__(self, code, where, msg=""):
+        super().__init__(f"{where}: {ERRORS.get(code, code)} {msg}".strip())
+        self.code = code
+
+
+def _dp(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _c64(a):
+    if a is None:
+        return None
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).ravel())
+
+
+def field_extent(fid, n):
+    nx, ny, nz = n
+    if fid in (0, 15):
+        return (nx, ny + 1, nz + 1)
+    if fid in (1, 16):
+        return (nx + 1, ny, nz + 1)
+    if fid == 2:
+        return (nx + 1, ny + 1, nz)
+    fam = {17: 0, 18: 1}.get(fid, (fid - 3) if fid < 6 else (fid - 6) // 3)
+    e = [nx, ny, nz]
+    e[fam] += 1
+    return tuple(e)
+
+
+class Solver:
+    """One ``mmx_ctx``: a grid, its materials, fields and sources on the GPU."""
+
+    def __init__(self, n, d, dt, bc, pml_cells=0, order=2, tol=1e-10, max_iter=64, prec=FP64,
+                 stream=None):
+        self._L = lib()
+        desc = GridDesc()
+        for a in range(3):
+            desc.n[a] = int(n[a])
+            desc.d[a] = float(d[a])
+            desc.bc[a] = int(bc[a])
+        desc.dt = float(dt)
+        desc.pml_cells = int(pml_cells)
+        desc.order = int(order)
+        desc.tol = float(tol)
+        desc.max_iter = int(max_iter)
+        desc.prec = int(prec)
+        self.n = tuple(int(v) for v in n)
+        self.prec = int(prec)
+        h = ctypes.c_void_p()
+        rc = self._L.mmx_create(ctypes.byref(desc), ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        self._h = h
+        if rc:
+            msg = self._L.mmx_last_error(h).decode() if h.value else ""
+            self.close()
+            raise MMXError(rc, "mmx_create", msg)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.mmx_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, where):
+        if rc < 0:
+            raise MMXError(rc, where, self._L.mmx_last_error(self._h).decode())
+        return rc
+
+    # -- entry points
+    def set_materials(self, eps_r=None, sigma=None, mu_r=None, Ms=None, alpha=None, gamma=None):
+        arrs = [_c64(a) for a in (eps_r, sigma, mu_r, Ms, alpha, gamma)]
+        self._check(self._L.mmx_set_materials(self._h, *[_dp(a) for a in arrs]), "mmx_set_materials")
+
+    def set_bias(self, hx, hy, hz):
+        self._check(self._L.mmx_set_bias(self._h, float(hx), float(hy), float(hz)), "mmx_set_bias")
+
+    def set_M_cells(self, mx, my, mz):
+        arrs = [_c64(a) for a in (mx, my, mz)]
+        self._check(self._L.mmx_set_M_cells(self._h, *[_dp(a) for a in arrs]), "mmx_set_M_cells")
+
+    def field_size(self, fid):
+        e = field_extent(fid, self.n)
+        return e[0] * e[1] * e[2]
+
+    def set_field(self, fid, values):
+        a = _c64(values)
+        self._check(self._L.mmx_set_field(self._h, int(fid), _dp(a), a.size), "mmx_set_field")
+
+    def get_field(self, fid, check=True):
+        out = np.empty(self.field_size(fid), dtype=np.float64)
+        rc = self._L.mmx_get_field(self._h, int(fid), _dp(out), out.size)
+        if check:
+            self._check(rc, "mmx_get_field")
+        return out
+
+    def get_material(self, which):
+        fid = (which % 3) if which < 6 else 3 + which % 3
+        out = np.empty(self.field_size(fid), dtype=np.float64)
+        self._check(self._L.mmx_get_material(self._h, int(which), _dp(out), out.size), "mmx_get_material")
+        return out
+
+    def add_source(self, kind, comp, i=0, j=0, k=0, amp=0.0, f0=0.0, tp=1.0, t0=0.0):
+        s = SourceDesc(int(kind), int(comp), int(i), int(j), int(k), float(amp), float(f0),
+                       float(tp), float(t0))
+        self._check(self._L.mmx_add_source(self._h, ctypes.byref(s)), "mmx_add_source")
+
+    def set_path(self, path):
+        self._check(self._L.mmx_set_path(self._h, int(path)), "mmx_set_path")
+
+    def step(self, nsteps=1):
+        self._check(self._L.mmx_step(self._h, int(nsteps)), "mmx_step")
+
+    def sync(self, check=True):
+        rc = self._L.mmx_sync(self._h)
+        if check:
+            self._check(rc, "mmx_sync")
+        return rc
+
+    def get_stats(self):
+        s = Stats()
+        self._check(self._L.mmx_get_stats(self._h, ctypes.byref(s)), "mmx_get_stats")
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def get_iter_log(self, cap=1 << 16):
+        buf = np.zeros(cap, dtype=np.int32)
+        n = self._L.mmx_get_iter_log(self._h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), cap)
+        self._check(n, "mmx_get_iter_log")
+        return buf[:n].copy()
+
+    def get_field_device(self, fid):
+        p = ctypes.c_void_p()
+        sx = ctypes.c_longlong()
+        sy = ctypes.c_longlong()
+        self._check(self._L.mmx_get_field_device(self._h, int(fid), ctypes.byref(p), ctypes.byref(sx),
+                                                 ctypes.byref(sy)), "mmx_get_field_device")
+        return p.value, sx.value, sy.value
+
+    def last_error(self):
+        return self._L.mmx_last_error(self._h).decode()
+
+
+def from_workload(w, prec=FP64, stream=None, with_sources=True, path=PATH_FUSED) -> Solver:
+    """Build a solver from a ``workloads.Workload`` (seeded synthetic inputs)."""
+    s = Solver(w.n, w.d, w.dt, w.bc, w.pml_cells, w.order, w.tol, w.max_iter, prec, stream)
+    s.set_path(path)
+    s.set_materials(w.eps_r, w.sigma, w.mu_r, w.Ms, w.alpha, w.gamma)
+    s.set_bias(*w.h0)
+    if w.m_cells is not None and w.Ms is not None and np.any(w.Ms > 0):
+        s.set_M_cells(*w.m_cells)
+    for fid, v in w.fields.items():
+        s.set_field(fid, v)
+    if with_sources:
+        for q in w.sources:
+            s.add_source(q.kind, q.comp, q.i, q.j, q.k, q.amp, q.f0, q.tp, q.t0)
+    return s

@@ -1,0 +1,846 @@
+// mmx.cu -- host side of the C ABI declared in include/mmx.h: context
+// lifetime, device memory, material/field setup and the per-step launch
+// sequence of the coupled Maxwell-LLG scheme (arXiv 2103.12819, Sec. 3).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mmx.h"
+#include "mmx_kernels.cuh"
+
+using namespace mmx;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+} // namespace
+
+struct mmx_ctx {
+    mmx_grid_desc desc;
+    Geo g;
+    size_t npad = 0;            // padded elements per Yee array
+    int esz = 8;                // bytes per element
+    cudaStream_t stream = nullptr;
+    int path = MMX_PATH_FUSED;
+    std::string err;
+
+    // Yee state
+    void *E[3] = {}, *H[3] = {}, *Ezp[2] = {}, *Hzp[2] = {};
+    // coefficients
+    void *ca[3] = {}, *cb[3] = {}, *fh[3] = {};
+    void *dampE = nullptr, *dampH = nullptr;
+    bool any_sigma = false, any_mu = false;
+    // cell-centred materials (double, compact nx*ny*nz; null = default)
+    double *cell[6] = {};
+    double h0[3] = {0, 0, 0};
+
+    // magnetic box
+    bool magnetic = false;
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    int bx = 0, by = 0, bz = 0;
+    long long nb = 0;
+    std::vector<void *> box_allocs;
+    void *bM[9] = {}, *bbeta[9] = {}, *bdM[2][9] = {}, *bCp[3] = {}, *be0[3] = {}, *bHit[2][3] = {};
+    void *bms[3] = {}, *bk1[3] = {}, *bk2[3] = {};
+    int coop_blocks = 0;
+
+    // control words (device)
+    unsigned long long *res = nullptr;     // [2][kMaxIter+1]
+    unsigned int *bar = nullptr;           // [2]
+    int *iterlog = nullptr;                // [kIterLogCap]
+    unsigned long long *halfsteps = nullptr;
+    double *last_res = nullptr;
+    int *errw = nullptr;
+    int box_slot = 0;
+
+    // sources
+    std::vector<mmx_source_desc> src;
+    void *dsrc = nullptr;
+
+    // staging
+    double *stage = nullptr;
+    size_t stage_elems = 0;
+
+    long long steps = 0;
+};
+
+// ------------------------------------------------------------- helpers
+
+static int fail(mmx_ctx *c, int code, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? MMX_ERR_OOM : MMX_ERR_CUDA,        \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);     \
+    } while (0)
+
+static bool is_fp64(const mmx_ctx *c) { return c->desc.prec == MMX_FP64; }
+
+static void edge_ext(const mmx_ctx *c, int comp, int e[3])
+{
+    for (int a = 0; a < 3; a++) e[a] = c->desc.n[a] + (a == comp ? 0 : 1);
+}
+static void face_ext(const mmx_ctx *c, int fam, int e[3])
+{
+    for (int a = 0; a < 3; a++) e[a] = c->desc.n[a] + (a == fam ? 1 : 0);
+}
+
+// Extents of a field id; returns false for an unknown id.
+static bool field_ext(const mmx_ctx *c, int id, int e[3])
+{
+    if (id >= 0 && id < 3) { edge_ext(c, id, e); return true; }
+    if (id >= 3 && id < 6) { face_ext(c, id - 3, e); return true; }
+    if (id >= 6 && id < 15) { face_ext(c, (id - 6) / 3, e); return true; }
+    if (id == 15 || id == 16) { edge_ext(c, id - 15, e); return true; }
+    if (id == 17 || id == 18) { face_ext(c, id - 17, e); return true; }
+    return false;
+}
+
+static dim3 node_block() { return dim3(32, 8, 1); }
+static dim3 node_grid(const mmx_ctx *c)
+{
+    return dim3((c->desc.n[0] + 1 + 31) / 32, (c->desc.n[1] + 1 + 7) / 8, c->desc.n[2] + 1);
+}
+
+static int dalloc(mmx_ctx *ctx, void **p, size_t bytes)
+{
+    CK(cudaMalloc(p, bytes > 0 ? bytes : 1));
+    CK(cudaMemsetAsync(*p, 0, bytes > 0 ? bytes : 1, ctx->stream));
+    return MMX_OK;
+}
+
+template <typename T> static Fields<T> make_fields(mmx_ctx *c)
+{
+    Fields<T> f;
+    for (int a = 0; a < 3; a++) {
+        f.E[a] = (T *)c->E[a];
+        f.H[a] = (T *)c->H[a];
+        f.ca[a] = (const T *)c->ca[a];
+        f.cb[a] = (const T *)c->cb[a];
+        f.fh[a] = (const T *)c->fh[a];
+    }
+    for (int a = 0; a < 2; a++) {
+        f.Ezp[a] = (T *)c->Ezp[a];
+        f.Hzp[a] = (T *)c->Hzp[a];
+    }
+    f.fh0 = (T)(c->desc.dt / (2.0 * kMu0));
+    f.dampE = (const T *)c->dampE;
+    f.dampH = (const T *)c->dampH;
+    f.err = c->errw;
+    return f;
+}
+
+template <typename T> static Box<T> make_box(mmx_ctx *c)
+{
+    Box<T> b;
+    memset(&b, 0, sizeof b);
+    for (int a = 0; a < 3; a++) b.lo[a] = c->lo[a];
+    b.bx = c->bx; b.by = c->by; b.bz = c->bz; b.nb = c->nb;
+    for (int q = 0; q < 9; q++) {
+        b.M[q] = (T *)c->bM[q];
+        b.beta[q] = (T *)c->bbeta[q];
+        b.dM[0][q] = (T *)c->bdM[0][q];
+        b.dM[1][q] = (T *)c->bdM[1][q];
+    }
+    for (int a = 0; a < 3; a++) {
+        b.Cp[a] = (T *)c->bCp[a];
+        b.e0[a] = (T *)c->be0[a];
+        b.Hit[0][a] = (T *)c->bHit[0][a];
+        b.Hit[1][a] = (T *)c->bHit[1][a];
+        b.ms[a] = (const T *)c->bms[a];
+        b.k1[a] = (const T *)c->bk1[a];
+        b.k2[a] = (const T *)c->bk2[a];
+        b.h0[a] = c->h0[a];
+    }
+    b.tol = c->desc.tol;
+    b.max_iter = c->desc.max_iter;
+    b.order = c->desc.order;
+    b.cfar = (T)(c->desc.dt / (2.0 * kMu0));
+    b.res = c->res;
+    b.bar = c->bar;
+    b.iterlog = c->iterlog;
+    b.halfsteps = c->halfsteps;
+    b.last_res = c->last_res;
+    b.err = c->errw;
+    return b;
+}
+
+// PML damping tables: E at z node k, H at z cell centre k + 1/2; identical
+// to 1 outside the layers.  sigma_z = smax (depth/L)^3 with
+// smax = -(m+1) eps0 c ln(R0)/(2 L), m = 3, R0 = 1e-8, L = npml dz.
+static void pml_tables(const mmx_ctx *c, std::vector<double> &dE, std::vector<double> &dH)
+{
+    int nz = c->desc.n[2], np = c->g.npml;
+    double dz = c->desc.d[2], dt = c->desc.dt;
+    double e0 = 1.0 / (kMu0 * kC0 * kC0);
+    dE.assign(nz + 1, 1.0);
+    dH.assign(nz, 1.0);
+    if (np <= 0) return;
+    double L = np * dz;
+    double zlo = L, zhi = (nz - np) * dz;
+    double smax = -(3.0 + 1.0) * e0 * kC0 * std::log(1e-8) / (2.0 * L);
+    auto sig = [&](double z) {
+        double depth;
+        if (z < zlo) depth = (zlo - z) / L;
+        else if (z > zhi) depth = (z - zhi) / L;
+        else return 0.0;
+        return smax * depth * depth * depth;
+    };
+    for (int k = 0; k <= nz; k++) {
+        double s = sig(k * dz);
+        if (s > 0.0) dE[k] = std::exp(-s * dt / (2.0 * e0));
+    }
+    for (int k = 0; k < nz; k++) {
+        double s = sig((k + 0.5) * dz);
+        if (s > 0.0) dH[k] = std::exp(-s * (dt / 4.0) / e0);
+    }
+}
+
+template <typename T> static int upload_table(mmx_ctx *ctx, void **dst, const std::vector<double> &v)
+{
+    std::vector<T> t(v.begin(), v.end());
+    int rc = dalloc(ctx, dst, t.size() * sizeof(T));
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(*dst, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MMX_OK;
+}
+
+static int ensure_stage(mmx_ctx *ctx, size_t elems)
+{
+    if (ctx->stage_elems >= elems) return MMX_OK;
+    if (ctx->stage) cudaFree(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_elems = 0;
+    CK(cudaMalloc((void **)&ctx->stage, elems * sizeof(double)));
+    ctx->stage_elems = elems;
+    return MMX_OK;
+}
+
+static void free_box(mmx_ctx *c)
+{
+    for (void *p : c->box_allocs) cudaFree(p);
+    c->box_allocs.clear();
+    c->magnetic = false;
+    c->nb = 0;
+}
+
+static int box_alloc(mmx_ctx *ctx, void **p)
+{
+    int rc = dalloc(ctx, p, (size_t)ctx->nb * ctx->esz);
+    if (rc == MMX_OK) ctx->box_allocs.push_back(*p);
+    return rc;
+}
+
+template <typename T> static int compute_coop(mmx_ctx *ctx)
+{
+    int dev = 0, nsm = 0, per = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hm_box<T>, 256, 0));
+    if (per < 1) return fail(ctx, MMX_ERR_CUDA, "H/M kernel cannot be resident");
+    long long need = (3 * ctx->nb + 255) / 256;
+    long long cap = (long long)per * nsm;
+    ctx->coop_blocks = (int)std::max(1LL, std::min(need, cap));
+    return MMX_OK;
+}
+
+// ------------------------------------------------------------ materials
+
+template <typename T> static int set_materials_t(mmx_ctx *ctx)
+{
+    const Geo &g = ctx->g;
+    dim3 B = node_block(), G = node_grid(ctx);
+    double *eps_c = ctx->cell[0], *sig_c = ctx->cell[1], *mu_c = ctx->cell[2];
+    for (int c = 0; c < 3; c++) {
+        k_e_coef<T><<<G, B, 0, ctx->stream>>>(g, eps_c, sig_c, c, (T *)ctx->ca[c], (T *)ctx->cb[c]);
+        CK(cudaGetLastError());
+        if (ctx->fh[c]) {
+            k_h_coef<T><<<G, B, 0, ctx->stream>>>(g, mu_c, c, (T *)ctx->fh[c]);
+            CK(cudaGetLastError());
+        }
+    }
+    if (ctx->magnetic) {
+        Box<T> b = make_box<T>(ctx);
+        int nblk = (int)((ctx->nb + 255) / 256);
+        for (int d = 0; d < 3; d++) {
+            k_box_materials<T><<<nblk, 256, 0, ctx->stream>>>(g, b, d, ctx->cell[3], ctx->cell[4], ctx->cell[5]);
+            CK(cudaGetLastError());
+        }
+        int rc = compute_coop<T>(ctx);
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MMX_OK;
+}
+
+// ------------------------------------------------------------ stepping
+
+template <typename T> static int launch_box(mmx_ctx *ctx, const Fields<T> &f, const Box<T> &b)
+{
+    int slot = ctx->box_slot;
+    ctx->box_slot ^= 1;
+    void *args[] = {(void *)&ctx->g, (void *)&f, (void *)&b, (void *)&slot};
+    CK(cudaLaunchCooperativeKernel((const void *)k_hm_box<T>, dim3(ctx->coop_blocks), dim3(256), args, 0,
+                                   ctx->stream));
+    return MMX_OK;
+}
+
+template <typename T> static int half_step(mmx_ctx *ctx, const Fields<T> &f, const Box<T> &b, double t_end)
+{
+    dim3 B = node_block(), G = node_grid(ctx);
+    if (ctx->magnetic) {
+        int rc = launch_box<T>(ctx, f, b);
+        if (rc) return rc;
+        k_h_update<T><<<G, B, 0, ctx->stream>>>(ctx->g, f, ctx->lo[0], ctx->lo[1], ctx->lo[2], ctx->hi[0],
+                                                 ctx->hi[1], ctx->hi[2]);
+    } else {
+        k_h_update<T><<<G, B, 0, ctx->stream>>>(ctx->g, f, 0, 0, 0, 0, 0, 0);
+    }
+    CK(cudaGetLastError());
+    bool hardH = false;
+    for (auto &s : ctx->src) hardH |= s.kind == 3;
+    if (hardH) {
+        Ptr3<T> F = {{f.H[0], f.H[1], f.H[2]}};
+        k_hard<T><<<1, 32, 0, ctx->stream>>>(ctx->g, F, (const Src<T> *)ctx->dsrc, (int)ctx->src.size(), 3, t_end);
+        CK(cudaGetLastError());
+    }
+    return MMX_OK;
+}
+
+template <typename T> static int step_plain(mmx_ctx *ctx, int nsteps)
+{
+    Fields<T> f = make_fields<T>(ctx);
+    Box<T> b = make_box<T>(ctx);
+    dim3 B = node_block(), G = node_grid(ctx);
+    int nsrc = (int)ctx->src.size();
+    bool hardE = false;
+    for (auto &s : ctx->src) hardE |= s.kind == 2;
+    for (int s = 0; s < nsteps; s++) {
+        long long n = ctx->steps;
+        double dt = ctx->desc.dt;
+        int rc = half_step<T>(ctx, f, b, (n + 0.5) * dt);
+        if (rc) return rc;
+        k_e_update<T><<<G, B, 0, ctx->stream>>>(ctx->g, f, (const Src<T> *)ctx->dsrc, nsrc, n);
+        CK(cudaGetLastError());
+        if (hardE) {
+            Ptr3<T> F = {{f.E[0], f.E[1], f.E[2]}};
+            k_hard<T><<<1, 32, 0, ctx->stream>>>(ctx->g, F, (const Src<T> *)ctx->dsrc, nsrc, 2, (n + 1.0) * dt);
+            CK(cudaGetLastError());
+        }
+        rc = half_step<T>(ctx, f, b, (n + 1.0) * dt);
+        if (rc) return rc;
+        ctx->steps++;
+    }
+    return MMX_OK;
+}
+
+// ------------------------------------------------------------ field copy
+
+template <typename T> static int copy_field_t(mmx_ctx *ctx, int id, double *host, long long n, int dir)
+{
+    int e[3];
+    field_ext(ctx, id, e);
+    long long N = (long long)e[0] * e[1] * e[2];
+    int rc = ensure_stage(ctx, (size_t)N);
+    if (rc) return rc;
+    T *dev = nullptr;
+    int boxed = 0;
+    if (id < 3) dev = (T *)ctx->E[id];
+    else if (id < 6) dev = (T *)ctx->H[id - 3];
+    else if (id < 15) {
+        boxed = 1;
+        dev = ctx->magnetic ? (T *)ctx->bM[id - 6] : nullptr;
+    } else if (id < 17) dev = (T *)ctx->Ezp[id - 15];
+    else dev = (T *)ctx->Hzp[id - 17];
+    Box<T> b = make_box<T>(ctx);
+    int blocks = (int)((N + 255) / 256);
+    if (dir == 0) {
+        if (!dev) {
+            memset(host, 0, (size_t)N * sizeof(double));
+            return MMX_OK;
+        }
+        k_copy_field<T><<<blocks, 256, 0, ctx->stream>>>(ctx->g, dev, b, boxed, e[0], e[1], e[2], ctx->stage, 0);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(host, ctx->stage, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return MMX_OK;
+    }
+    if (!dev) {
+        if (id >= 15) return fail(ctx, MMX_ERR_INVALID, "field %d exists only with a z-PML", id);
+        for (long long q = 0; q < N; q++)
+            if (host[q] != 0.0) return fail(ctx, MMX_ERR_INVALID, "M can only be set on magnetic faces");
+        return MMX_OK;
+    }
+    CK(cudaMemcpyAsync(ctx->stage, host, (size_t)N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    k_copy_field<T><<<blocks, 256, 0, ctx->stream>>>(ctx->g, dev, b, boxed, e[0], e[1], e[2], ctx->stage, 1);
+    CK(cudaGetLastError());
+    if (!boxed) {
+        for (int a = 0; a < 3; a++) {
+            if (!ctx->g.per[a] || e[a] != ctx->desc.n[a] + 1) continue;
+            int bb = (a + 1) % 3, cc = (a + 2) % 3;
+            long long P = (long long)e[bb] * e[cc];
+            k_sync_periodic<T><<<(int)((P + 255) / 256), 256, 0, ctx->stream>>>(ctx->g, dev, e[0], e[1], e[2], a);
+            CK(cudaGetLastError());
+        }
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MMX_OK;
+}
+
+static int read_status(mmx_ctx *ctx)
+{
+    int w = 0;
+    CK(cudaMemcpyAsync(&w, ctx->errw, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (w) {
+        int z = 0;
+        CK(cudaMemcpyAsync(ctx->errw, &z, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    if (w & kErrTimeout) {
+        unsigned int zz[2] = {0, 0};
+        CK(cudaMemcpyAsync(ctx->bar, zz, sizeof zz, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return fail(ctx, MMX_ERR_TIMEOUT, "a device-side wait gave up");
+    }
+    if (w & kErrNonFinite) return fail(ctx, MMX_ERR_NONFINITE, "a field became non-finite");
+    if (w & kErrBadInput) return fail(ctx, MMX_ERR_INVALID, "invalid input detected on the device");
+    if (w & kErrNotConverged)
+        return fail(ctx, MMX_ERR_NOT_CONVERGED, "an H/M half step reached max_iter=%d", ctx->desc.max_iter);
+    return MMX_OK;
+}
+
+// ================================================================= C ABI
+
+extern "C" {
+
+int mmx_create(const mmx_grid_desc *desc, void *cuda_stream, mmx_ctx **out)
+{
+    if (!desc || !out) return MMX_ERR_INVALID;
+    *out = nullptr;
+    mmx_ctx *ctx = new (std::nothrow) mmx_ctx();
+    if (!ctx) return MMX_ERR_OOM;
+    ctx->desc = *desc;
+    const mmx_grid_desc &d = *desc;
+    int rc = MMX_OK;
+    for (int a = 0; a < 3; a++) {
+        if (d.n[a] < 1 || !(d.d[a] > 0)) rc = fail(ctx, MMX_ERR_INVALID, "n and d must be positive");
+        if (d.bc[a] < 0 || d.bc[a] > 2) rc = fail(ctx, MMX_ERR_INVALID, "bad boundary type");
+        if (d.bc[a] == MMX_BC_PML && a != 2) rc = fail(ctx, MMX_ERR_INVALID, "PML only on the z axis");
+    }
+    if (!(d.dt > 0)) rc = fail(ctx, MMX_ERR_INVALID, "dt must be positive");
+    if (d.order != 1 && d.order != 2) rc = fail(ctx, MMX_ERR_INVALID, "order must be 1 or 2");
+    if (!(d.tol > 0)) rc = fail(ctx, MMX_ERR_INVALID, "tol must be positive");
+    if (d.max_iter < 1 || d.max_iter > kMaxIter) rc = fail(ctx, MMX_ERR_INVALID, "max_iter must be 1..64");
+    if (d.prec != MMX_FP64 && d.prec != MMX_FP32) rc = fail(ctx, MMX_ERR_INVALID, "bad precision");
+    if (d.bc[2] == MMX_BC_PML && (d.pml_cells < 1 || 2 * d.pml_cells >= d.n[2]))
+        rc = fail(ctx, MMX_ERR_INVALID, "pml_cells must be in [1, nz/2)");
+    long long X = ((long long)d.n[0] + 1 + 7) / 8 * 8;
+    long long npad = X * (d.n[1] + 1LL) * (d.n[2] + 1LL);
+    if (npad > (1LL << 40)) rc = fail(ctx, MMX_ERR_INVALID, "grid too large");
+    if (rc) {
+        // keep the message reachable through *out
+        *out = ctx;
+        return rc;
+    }
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->esz = d.prec == MMX_FP64 ? 8 : 4;
+    Geo &g = ctx->g;
+    for (int a = 0; a < 3; a++) {
+        g.n[a] = d.n[a];
+        g.per[a] = d.bc[a] == MMX_BC_PERIODIC;
+        g.d[a] = d.d[a];
+        g.inv_d[a] = 1.0 / d.d[a];
+    }
+    g.X = (int)X;
+    g.Y = d.n[1] + 1;
+    g.npml = d.bc[2] == MMX_BC_PML ? d.pml_cells : 0;
+    g.dt = d.dt;
+    ctx->npad = (size_t)npad;
+    size_t fb = ctx->npad * ctx->esz;
+    for (int a = 0; a < 3 && !rc; a++) {
+        rc = dalloc(ctx, &ctx->E[a], fb);
+        if (!rc) rc = dalloc(ctx, &ctx->H[a], fb);
+        if (!rc) rc = dalloc(ctx, &ctx->cb[a], fb);
+    }
+    if (!rc && g.npml > 0)
+        for (int a = 0; a < 2 && !rc; a++) {
+            rc = dalloc(ctx, &ctx->Ezp[a], fb);
+            if (!rc) rc = dalloc(ctx, &ctx->Hzp[a], fb);
+        }
+    if (!rc) rc = dalloc(ctx, (void **)&ctx->res, 2 * (kMaxIter + 1) * sizeof(unsigned long long));
+    if (!rc) rc = dalloc(ctx, (void **)&ctx->bar, 2 * sizeof(unsigned int));
+    if (!rc) rc = dalloc(ctx, (void **)&ctx->iterlog, kIterLogCap * sizeof(int));
+    if (!rc) rc = dalloc(ctx, (void **)&ctx->halfsteps, sizeof(unsigned long long));
+    if (!rc) rc = dalloc(ctx, (void **)&ctx->last_res, sizeof(double));
+    if (!rc) rc = dalloc(ctx, (void **)&ctx->errw, sizeof(int));
+    if (!rc) rc = dalloc(ctx, &ctx->dsrc, kMaxSources * sizeof(Src<double>));
+    if (!rc) {
+        std::vector<double> dE, dH;
+        pml_tables(ctx, dE, dH);
+        rc = is_fp64(ctx) ? upload_table<double>(ctx, &ctx->dampE, dE) : upload_table<float>(ctx, &ctx->dampE, dE);
+        if (!rc) rc = is_fp64(ctx) ? upload_table<double>(ctx, &ctx->dampH, dH) : upload_table<float>(ctx, &ctx->dampH, dH);
+    }
+    if (!rc) rc = is_fp64(ctx) ? set_materials_t<double>(ctx) : set_materials_t<float>(ctx);
+    if (rc) {
+        *out = ctx;
+        return rc;
+    }
+    *out = ctx;
+    return MMX_OK;
+}
+
+void mmx_destroy(mmx_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->E[0]) cudaStreamSynchronize(ctx->stream);
+    for (int a = 0; a < 3; a++) {
+        cudaFree(ctx->E[a]); cudaFree(ctx->H[a]); cudaFree(ctx->ca[a]); cudaFree(ctx->cb[a]); cudaFree(ctx->fh[a]);
+    }
+    for (int a = 0; a < 2; a++) { cudaFree(ctx->Ezp[a]); cudaFree(ctx->Hzp[a]); }
+    for (int a = 0; a < 6; a++) cudaFree(ctx->cell[a]);
+    free_box(ctx);
+    cudaFree(ctx->dampE); cudaFree(ctx->dampH);
+    cudaFree(ctx->res); cudaFree(ctx->bar); cudaFree(ctx->iterlog); cudaFree(ctx->halfsteps);
+    cudaFree(ctx->last_res); cudaFree(ctx->errw); cudaFree(ctx->dsrc); cudaFree(ctx->stage);
+    delete ctx;
+}
+
+const char *mmx_last_error(const mmx_ctx *ctx)
+{
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+int mmx_set_materials(mmx_ctx *ctx, const double *eps_r, const double *sigma, const double *mu_r,
+                      const double *Ms, const double *alpha, const double *gamma_abs)
+{
+    if (!ctx || !ctx->E[0]) return MMX_ERR_INVALID;
+    const int *n = ctx->desc.n;
+    size_t nc = (size_t)n[0] * n[1] * n[2];
+    const double *in[6] = {eps_r, sigma, mu_r, Ms, alpha, gamma_abs};
+    for (size_t q = 0; q < nc; q++) {
+        if (eps_r && !(eps_r[q] > 0)) return fail(ctx, MMX_ERR_INVALID, "eps_r must be > 0");
+        if (mu_r && !(mu_r[q] > 0)) return fail(ctx, MMX_ERR_INVALID, "mu_r must be > 0");
+        if (sigma && !(sigma[q] >= 0)) return fail(ctx, MMX_ERR_INVALID, "sigma must be >= 0");
+        if (Ms && !(Ms[q] >= 0)) return fail(ctx, MMX_ERR_INVALID, "Ms must be >= 0");
+        if (alpha && !(alpha[q] >= 0)) return fail(ctx, MMX_ERR_INVALID, "alpha must be >= 0");
+        if (gamma_abs && !(gamma_abs[q] >= 0)) return fail(ctx, MMX_ERR_INVALID, "gamma must be >= 0");
+    }
+    // magnetic bounding box (cells with Ms > 0)
+    int c0[3] = {n[0], n[1], n[2]}, c1[3] = {-1, -1, -1};
+    if (Ms) {
+        for (int k = 0; k < n[2]; k++)
+            for (int j = 0; j < n[1]; j++)
+                for (int i = 0; i < n[0]; i++)
+                    if (Ms[(size_t)i + (size_t)n[0] * ((size_t)j + (size_t)n[1] * k)] > 0) {
+                        int ix[3] = {i, j, k};
+                        for (int a = 0; a < 3; a++) {
+                            c0[a] = std::min(c0[a], ix[a]);
+                            c1[a] = std::max(c1[a], ix[a]);
+                        }
+                    }
+    }
+    bool magnetic = c1[0] >= 0;
+    if (magnetic && ctx->g.npml > 0 && (c0[2] < ctx->g.npml || c1[2] >= n[2] - ctx->g.npml))
+        return fail(ctx, MMX_ERR_INVALID, "Ms must be 0 inside the PML layers");
+    // upload cell arrays
+    for (int a = 0; a < 6; a++) {
+        cudaFree(ctx->cell[a]);
+        ctx->cell[a] = nullptr;
+        if (!in[a]) continue;
+        CK(cudaMalloc((void **)&ctx->cell[a], nc * sizeof(double)));
+        CK(cudaMemcpyAsync(ctx->cell[a], in[a], nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    bool any_sigma = false, any_mu = false;
+    for (size_t q = 0; q < nc; q++) {
+        if (sigma && sigma[q] != 0.0) any_sigma = true;
+        if (mu_r && mu_r[q] != 1.0) any_mu = true;
+    }
+    size_t fb = ctx->npad * ctx->esz;
+    for (int a = 0; a < 3; a++) {
+        if (any_sigma && !ctx->ca[a]) { int rc = dalloc(ctx, &ctx->ca[a], fb); if (rc) return rc; }
+        if (!any_sigma && ctx->ca[a]) { cudaFree(ctx->ca[a]); ctx->ca[a] = nullptr; }
+        if (any_mu && !ctx->fh[a]) { int rc = dalloc(ctx, &ctx->fh[a], fb); if (rc) return rc; }
+        if (!any_mu && ctx->fh[a]) { cudaFree(ctx->fh[a]); ctx->fh[a] = nullptr; }
+    }
+    ctx->any_sigma = any_sigma;
+    ctx->any_mu = any_mu;
+    // (re)build the magnetic box
+    CK(cudaStreamSynchronize(ctx->stream));
+    free_box(ctx);
+    if (magnetic) {
+        for (int a = 0; a < 3; a++) {
+            if (ctx->g.per[a] && (c0[a] == 0 || c1[a] == n[a] - 1)) {
+                ctx->lo[a] = 0;
+                ctx->hi[a] = n[a] + 1;
+            } else {
+                ctx->lo[a] = std::max(c0[a] - 1, 0);
+                ctx->hi[a] = std::min(c1[a] + 2, n[a] + 1);
+            }
+        }
+        ctx->bx = ctx->hi[0] - ctx->lo[0];
+        ctx->by = ctx->hi[1] - ctx->lo[1];
+        ctx->bz = ctx->hi[2] - ctx->lo[2];
+        ctx->nb = (long long)ctx->bx * ctx->by * ctx->bz;
+        int rc = MMX_OK;
+        for (int q = 0; q < 9 && !rc; q++) {
+            rc = box_alloc(ctx, &ctx->bM[q]);
+            if (!rc) rc = box_alloc(ctx, &ctx->bbeta[q]);
+            if (!rc) rc = box_alloc(ctx, &ctx->bdM[0][q]);
+            if (!rc) rc = box_alloc(ctx, &ctx->bdM[1][q]);
+        }
+        for (int a = 0; a < 3 && !rc; a++) {
+            rc = box_alloc(ctx, &ctx->bCp[a]);
+            if (!rc) rc = box_alloc(ctx, &ctx->be0[a]);
+            if (!rc) rc = box_alloc(ctx, &ctx->bHit[0][a]);
+            if (!rc) rc = box_alloc(ctx, &ctx->bHit[1][a]);
+            if (!rc) rc = box_alloc(ctx, &ctx->bms[a]);
+            if (!rc) rc = box_alloc(ctx, &ctx->bk1[a]);
+            if (!rc) rc = box_alloc(ctx, &ctx->bk2[a]);
+        }
+        if (rc) {
+            free_box(ctx);
+            return rc;
+        }
+        ctx->magnetic = true;
+    } else {
+        for (int a = 0; a < 3; a++) ctx->lo[a] = ctx->hi[a] = 0;
+    }
+    return is_fp64(ctx) ? set_materials_t<double>(ctx) : set_materials_t<float>(ctx);
+}
+
+int mmx_set_bias(mmx_ctx *ctx, double hx, double hy, double hz)
+{
+    if (!ctx || !ctx->E[0]) return MMX_ERR_INVALID;
+    ctx->h0[0] = hx; ctx->h0[1] = hy; ctx->h0[2] = hz;
+    return MMX_OK;
+}
+
+int mmx_set_M_cells(mmx_ctx *ctx, const double *mx, const double *my, const double *mz)
+{
+    if (!ctx || !ctx->E[0] || !mx || !my || !mz) return MMX_ERR_INVALID;
+    if (!ctx->magnetic) return MMX_OK;
+    const int *n = ctx->desc.n;
+    size_t nc = (size_t)n[0] * n[1] * n[2];
+    double *dm[3] = {};
+    const double *in[3] = {mx, my, mz};
+    int rc = MMX_OK;
+    for (int c = 0; c < 3 && !rc; c++) {
+        cudaError_t e = cudaMalloc((void **)&dm[c], nc * sizeof(double));
+        if (e != cudaSuccess) rc = fail(ctx, MMX_ERR_OOM, "cudaMalloc: %s", cudaGetErrorString(e));
+        else if (cudaMemcpyAsync(dm[c], in[c], nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+            rc = fail(ctx, MMX_ERR_CUDA, "copy of M cells failed");
+    }
+    if (!rc) {
+        int nblk = (int)((ctx->nb + 255) / 256);
+        for (int d = 0; d < 3; d++) {
+            if (is_fp64(ctx))
+                k_box_init_m<double><<<nblk, 256, 0, ctx->stream>>>(ctx->g, make_box<double>(ctx), d, dm[0], dm[1], dm[2]);
+            else
+                k_box_init_m<float><<<nblk, 256, 0, ctx->stream>>>(ctx->g, make_box<float>(ctx), d, dm[0], dm[1], dm[2]);
+        }
+        if (cudaGetLastError() != cudaSuccess) rc = fail(ctx, MMX_ERR_CUDA, "init M launch failed");
+    }
+    cudaStreamSynchronize(ctx->stream);
+    for (int c = 0; c < 3; c++) cudaFree(dm[c]);
+    if (rc) return rc;
+    rc = read_status(ctx);
+    if (rc == MMX_ERR_INVALID) return fail(ctx, rc, "a magnetic face has no magnetisation direction");
+    return rc;
+}
+
+int mmx_set_field(mmx_ctx *ctx, int id, const double *host, long long n)
+{
+    if (!ctx || !ctx->E[0] || !host) return MMX_ERR_INVALID;
+    int e[3];
+    if (!field_ext(ctx, id, e)) return fail(ctx, MMX_ERR_INVALID, "bad field id %d", id);
+    if (n != (long long)e[0] * e[1] * e[2]) return fail(ctx, MMX_ERR_INVALID, "field %d needs %lld values", id, (long long)e[0] * e[1] * e[2]);
+    return is_fp64(ctx) ? copy_field_t<double>(ctx, id, const_cast<double *>(host), n, 1)
+                        : copy_field_t<float>(ctx, id, const_cast<double *>(host), n, 1);
+}
+
+int mmx_get_field(mmx_ctx *ctx, int id, double *host, long long n)
+{
+    if (!ctx || !ctx->E[0] || !host) return MMX_ERR_INVALID;
+    int e[3];
+    if (!field_ext(ctx, id, e)) return fail(ctx, MMX_ERR_INVALID, "bad field id %d", id);
+    if (n != (long long)e[0] * e[1] * e[2]) return fail(ctx, MMX_ERR_INVALID, "field %d needs %lld values", id, (long long)e[0] * e[1] * e[2]);
+    int rc = is_fp64(ctx) ? copy_field_t<double>(ctx, id, host, n, 0) : copy_field_t<float>(ctx, id, host, n, 0);
+    if (rc) return rc;
+    return read_status(ctx);
+}
+
+int mmx_get_material(mmx_ctx *ctx, int which, double *host, long long n)
+{
+    if (!ctx || !ctx->E[0] || !host || which < 0 || which > 17) return MMX_ERR_INVALID;
+    int c = which % 3, kind = which / 3;
+    int e[3];
+    if (kind < 2) edge_ext(ctx, c, e); else face_ext(ctx, c, e);
+    long long N = (long long)e[0] * e[1] * e[2];
+    if (n != N) return fail(ctx, MMX_ERR_INVALID, "material %d needs %lld values", which, N);
+    static const int cell_of_kind[6] = {0, 1, 2, 3, 4, 5};
+    static const double dflt[6] = {1.0, 0.0, 1.0, 0.0, 0.0, 0.0};
+    double *cellp = ctx->cell[cell_of_kind[kind]];
+    if (!cellp) {
+        for (long long q = 0; q < N; q++) host[q] = dflt[kind];
+        return MMX_OK;
+    }
+    int rc = ensure_stage(ctx, ctx->npad);
+    if (rc) return rc;
+    double *tmp = nullptr;
+    CK(cudaMalloc((void **)&tmp, ctx->npad * sizeof(double)));
+    k_mean<<<node_grid(ctx), node_block(), 0, ctx->stream>>>(ctx->g, cellp, kind < 2 ? 0 : 1, c, tmp);
+    cudaError_t le = cudaGetLastError();
+    // compact into the staging buffer as a double field
+    if (le == cudaSuccess) {
+        Box<double> b = make_box<double>(ctx);
+        int blocks = (int)((N + 255) / 256);
+        k_copy_field<double><<<blocks, 256, 0, ctx->stream>>>(ctx->g, tmp, b, 0, e[0], e[1], e[2], ctx->stage, 0);
+        le = cudaGetLastError();
+    }
+    if (le == cudaSuccess) le = cudaMemcpyAsync(host, ctx->stage, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(tmp);
+    if (le != cudaSuccess) return fail(ctx, MMX_ERR_CUDA, "material readback: %s", cudaGetErrorString(le));
+    return MMX_OK;
+}
+
+int mmx_add_source(mmx_ctx *ctx, const mmx_source_desc *s)
+{
+    if (!ctx || !ctx->E[0] || !s) return MMX_ERR_INVALID;
+    if ((int)ctx->src.size() >= kMaxSources) return fail(ctx, MMX_ERR_INVALID, "at most %d sources", kMaxSources);
+    if (s->kind < 0 || s->kind > 3 || s->comp < 0 || s->comp > 2 || !(s->tp > 0))
+        return fail(ctx, MMX_ERR_INVALID, "bad source kind/comp/tp");
+    int e[3];
+    if (s->kind == 3) face_ext(ctx, s->comp, e); else edge_ext(ctx, s->comp, e);
+    int ix[3] = {s->i, s->j, s->k};
+    if (s->kind == 1) {
+        if (s->comp == 2 || s->k < 0 || s->k > ctx->desc.n[2]) return fail(ctx, MMX_ERR_INVALID, "bad plane source");
+        if (ctx->g.per[2] && s->k == ctx->desc.n[2]) return fail(ctx, MMX_ERR_INVALID, "use node 0, not n, on a periodic axis");
+    } else {
+        for (int a = 0; a < 3; a++) {
+            if (ix[a] < 0 || ix[a] >= e[a]) return fail(ctx, MMX_ERR_INVALID, "source index out of range");
+            bool nodal = e[a] == ctx->desc.n[a] + 1;
+            if (ctx->g.per[a] && nodal && ix[a] == ctx->desc.n[a])
+                return fail(ctx, MMX_ERR_INVALID, "use node 0, not n, on a periodic axis");
+            if ((s->kind == 2 || s->kind == 3) && ctx->g.per[a] && nodal && ix[a] == 0)
+                return fail(ctx, MMX_ERR_INVALID, "hard sources may not sit on a periodic seam");
+        }
+    }
+    ctx->src.push_back(*s);
+    std::vector<Src<double>> hs(ctx->src.size());
+    for (size_t q = 0; q < ctx->src.size(); q++) {
+        const mmx_source_desc &d = ctx->src[q];
+        hs[q].kind = d.kind; hs[q].comp = d.comp; hs[q].i = d.i; hs[q].j = d.j; hs[q].k = d.k;
+        hs[q].amp = d.amp; hs[q].f0 = d.f0; hs[q].tp = d.tp; hs[q].t0 = d.t0;
+    }
+    // Src<T> has the same layout for both T (only doubles and ints)
+    CK(cudaMemcpyAsync(ctx->dsrc, hs.data(), hs.size() * sizeof(Src<double>), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MMX_OK;
+}
+
+int mmx_set_path(mmx_ctx *ctx, int path)
+{
+    if (!ctx || (path != MMX_PATH_PLAIN && path != MMX_PATH_FUSED)) return MMX_ERR_INVALID;
+    ctx->path = path;
+    return MMX_OK;
+}
+
+int mmx_step(mmx_ctx *ctx, int nsteps)
+{
+    if (!ctx || !ctx->E[0] || nsteps < 0) return MMX_ERR_INVALID;
+    if (nsteps == 0) return MMX_OK;
+    CK(cudaMemsetAsync(ctx->bar, 0, 2 * sizeof(unsigned int), ctx->stream));
+    return is_fp64(ctx) ? step_plain<double>(ctx, nsteps) : step_plain<float>(ctx, nsteps);
+}
+
+int mmx_sync(mmx_ctx *ctx)
+{
+    if (!ctx || !ctx->E[0]) return MMX_ERR_INVALID;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return read_status(ctx);
+}
+
+int mmx_get_stats(mmx_ctx *ctx, mmx_stats *out)
+{
+    if (!ctx || !ctx->E[0] || !out) return MMX_ERR_INVALID;
+    CK(cudaStreamSynchronize(ctx->stream));
+    unsigned long long hs = 0;
+    double lr = 0.0;
+    CK(cudaMemcpy(&hs, ctx->halfsteps, sizeof hs, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&lr, ctx->last_res, sizeof lr, cudaMemcpyDeviceToHost));
+    out->steps = ctx->steps;
+    out->half_steps = ctx->magnetic ? (long long)hs : 2 * ctx->steps;
+    out->last_residual = lr;
+    out->iters_min = 0;
+    out->iters_max = 0;
+    if (ctx->magnetic && hs > 0) {
+        long long m = std::min<long long>((long long)hs, kIterLogCap);
+        std::vector<int> v(kIterLogCap);
+        CK(cudaMemcpy(v.data(), ctx->iterlog, kIterLogCap * sizeof(int), cudaMemcpyDeviceToHost));
+        int mn = 1 << 30, mx = 0;
+        for (long long q = 0; q < m; q++) {
+            mn = std::min(mn, v[q]);
+            mx = std::max(mx, v[q]);
+        }
+        out->iters_min = mn;
+        out->iters_max = mx;
+    }
+    out->status = read_status(ctx);
+    return MMX_OK;
+}
+
+long long mmx_get_iter_log(mmx_ctx *ctx, int *host, long long cap)
+{
+    if (!ctx || !ctx->E[0] || (cap > 0 && !host)) return MMX_ERR_INVALID;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (!ctx->magnetic) return 0;
+    unsigned long long hs = 0;
+    CK(cudaMemcpy(&hs, ctx->halfsteps, sizeof hs, cudaMemcpyDeviceToHost));
+    long long avail = std::min<long long>((long long)hs, kIterLogCap);
+    long long m = std::min(avail, cap);
+    std::vector<int> v(kIterLogCap);
+    CK(cudaMemcpy(v.data(), ctx->iterlog, kIterLogCap * sizeof(int), cudaMemcpyDeviceToHost));
+    long long first = (long long)hs - avail;   // oldest kept
+    for (long long q = 0; q < m; q++) host[q] = v[(first + q) % kIterLogCap];
+    return m;
+}
+
+int mmx_get_field_device(mmx_ctx *ctx, int id, void **ptr, long long *sx, long long *sy)
+{
+    if (!ctx || !ctx->E[0] || !ptr || !sx || !sy) return MMX_ERR_INVALID;
+    if (id < 0 || id > 5) return fail(ctx, MMX_ERR_INVALID, "device views exist for E and H (ids 0-5)");
+    *ptr = id < 3 ? ctx->E[id] : ctx->H[id - 3];
+    *sx = ctx->g.X;
+    *sy = (long long)ctx->g.X * ctx->g.Y;
+    return MMX_OK;
+}
+
+} // extern "C"

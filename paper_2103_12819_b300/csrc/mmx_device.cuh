@@ -1,0 +1,330 @@
+// mmx_device.cuh -- device-side data structures and per-point arithmetic of
+// the coupled Maxwell-LLG scheme (Yao, Jambunathan, Zeng & Nonaka,
+// arXiv 2103.12819, Sec. 3) for sm_103a.  Everything here is templated on
+// the storage/arithmetic type T (double or float).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mmx {
+
+// CODATA 2018 mu0 and the exact speed of light.
+constexpr double kMu0 = 1.25663706212e-6;
+constexpr double kC0 = 299792458.0;
+constexpr double kPi = 3.14159265358979323846;
+
+constexpr int kMaxIter = 64;
+constexpr int kMaxSources = 32;
+constexpr int kIterLogCap = 65536;
+
+// Latched device status bits.
+constexpr int kErrNotConverged = 1;
+constexpr int kErrNonFinite = 2;
+constexpr int kErrTimeout = 4;
+constexpr int kErrBadInput = 8;
+
+// Grid geometry.  All Yee arrays share one padded layout: element (i, j, k)
+// at i + X*(j + Y*k) with X = nx+1 rounded up to a multiple of 8 and
+// Y = ny+1, so a neighbour is +-1, +-X or +-X*Y for every component.
+struct Geo {
+    int n[3];
+    int X, Y;
+    int per[3];        // 1 on a periodic axis
+    int npml;          // PML cells at each z end (0: none)
+    double dt;
+    double inv_d[3];
+    double d[3];
+};
+
+__device__ __forceinline__ size_t gidx(const Geo &g, int i, int j, int k)
+{
+    return (size_t)i + (size_t)g.X * ((size_t)j + (size_t)g.Y * (size_t)k);
+}
+
+// Cell-centred neighbour index along axis a (idx in [-1, n]): wrapped on a
+// periodic axis, -1 outside a non-periodic one.
+__device__ __forceinline__ int cell_nb(const Geo &g, int a, int idx)
+{
+    int n = g.n[a];
+    if (idx < 0) return g.per[a] ? idx + n : -1;
+    if (idx >= n) return g.per[a] ? idx - n : -1;
+    return idx;
+}
+
+__device__ __forceinline__ bool wall_node(const Geo &g, int a, int idx)
+{
+    return !g.per[a] && (idx == 0 || idx == g.n[a]);
+}
+
+// z planes inside the PML: E (nodal in z) at node k, H x/y faces at k+1/2.
+__device__ __forceinline__ bool pml_e_plane(const Geo &g, int k)
+{
+    return g.npml > 0 && (k < g.npml || k > g.n[2] - g.npml);
+}
+__device__ __forceinline__ bool pml_h_plane(const Geo &g, int k)
+{
+    return g.npml > 0 && (k < g.npml || k >= g.n[2] - g.npml);
+}
+
+template <typename T> struct Src {
+    int kind, comp, i, j, k;
+    double amp, f0, tp, t0;
+};
+
+template <typename T> struct Fields {
+    T *E[3];
+    T *H[3];
+    T *Ezp[2];          // z-derivative parts of Ex, Ey in the PML (else null)
+    T *Hzp[2];          // z-derivative parts of Hx, Hy in the PML (else null)
+    const T *ca[3];     // E update: E' = ca E + cb (curl H - J); ca null -> 1
+    const T *cb[3];
+    const T *fh[3];     // H update: H' = H - fh curl E; fh null -> fh0
+    T fh0;
+    const T *dampE;     // per z node: exp(-sigma_z dt/(2 eps0)) (PML planes)
+    const T *dampH;     // per z cell: exp(-sigma_z dt/(4 eps0))
+    int *err;
+};
+
+// Magnetic box: the bounding box of the magnetic faces grown by one face on
+// every side (so every neighbour a magnetic face reads lies inside), stored
+// box-locally with dims (bx, by, bz), element (i,j,k) at
+// (i-lo0) + bx*((j-lo1) + by*(k-lo2)).
+template <typename T> struct Box {
+    int lo[3];
+    int bx, by, bz;
+    long long nb;
+    T *M[9];            // M^n per face family: M[3*fam + comp]
+    T *beta[9];         // -kappa M^n x Heff^n
+    T *dM[2][9];        // iterates of DeltaM = M^r - M^n
+    T *Cp[3];           // H^n - dt/(2 mu0) curl E
+    T *e0[3];           // Ms^2 - |M^n|^2 (formed in FP64)
+    T *Hit[2][3];       // H iterates
+    const T *ms[3];     // Ms on faces
+    const T *k1[3];     // order 2: kappa = mu0|gamma|dt/4; order 1: (dt/2) mu0 gamma_L
+    const T *k2[3];     // order 2: alpha/Ms;               order 1: (dt/2) alpha mu0 gamma_L / Ms
+    double h0[3];
+    double tol;
+    int max_iter;
+    int order;
+    T cfar;             // dt/(2 mu0)
+    unsigned long long *res;   // [2][kMaxIter+1] residual bit patterns
+    unsigned int *bar;         // grid barrier: [0] count, [1] generation
+    int *iterlog;
+    unsigned long long *halfsteps;
+    double *last_res;
+    int *err;
+};
+
+__device__ __forceinline__ size_t bidx(const int lo[3], int bx, int by, int i, int j, int k)
+{
+    return (size_t)(i - lo[0]) + (size_t)bx * ((size_t)(j - lo[1]) + (size_t)by * (size_t)(k - lo[2]));
+}
+
+// ---------------------------------------------------------------- curls
+
+// (curl H) on an E edge split into the z-derivative part and the rest
+// (Sec. 3.1: 2nd-order central differences of the face values).
+template <typename T>
+__device__ __forceinline__ void curl_h(const Geo &g, T *const H[3], int c, int i, int j, int k,
+                                       T &rest, T &zp)
+{
+    const T idx = (T)g.inv_d[0], idy = (T)g.inv_d[1], idz = (T)g.inv_d[2];
+    if (c == 0) {
+        int jm = cell_nb(g, 1, j - 1), jp = cell_nb(g, 1, j);
+        int km = cell_nb(g, 2, k - 1), kp = cell_nb(g, 2, k);
+        rest = (H[2][gidx(g, i, jp, k)] - H[2][gidx(g, i, jm, k)]) * idy;
+        zp = -(H[1][gidx(g, i, j, kp)] - H[1][gidx(g, i, j, km)]) * idz;
+    } else if (c == 1) {
+        int im = cell_nb(g, 0, i - 1), ip = cell_nb(g, 0, i);
+        int km = cell_nb(g, 2, k - 1), kp = cell_nb(g, 2, k);
+        zp = (H[0][gidx(g, i, j, kp)] - H[0][gidx(g, i, j, km)]) * idz;
+        rest = -(H[2][gidx(g, ip, j, k)] - H[2][gidx(g, im, j, k)]) * idx;
+    } else {
+        int im = cell_nb(g, 0, i - 1), ip = cell_nb(g, 0, i);
+        int jm = cell_nb(g, 1, j - 1), jp = cell_nb(g, 1, j);
+        rest = (H[1][gidx(g, ip, j, k)] - H[1][gidx(g, im, j, k)]) * idx
+             - (H[0][gidx(g, i, jp, k)] - H[0][gidx(g, i, jm, k)]) * idy;
+        zp = T(0);
+    }
+}
+
+// (curl E) on an H face of family d, split the same way.
+template <typename T>
+__device__ __forceinline__ void curl_e(const Geo &g, T *const E[3], int d, int i, int j, int k,
+                                       T &rest, T &zp)
+{
+    const T idx = (T)g.inv_d[0], idy = (T)g.inv_d[1], idz = (T)g.inv_d[2];
+    if (d == 0) {
+        rest = (E[2][gidx(g, i, j + 1, k)] - E[2][gidx(g, i, j, k)]) * idy;
+        zp = -(E[1][gidx(g, i, j, k + 1)] - E[1][gidx(g, i, j, k)]) * idz;
+    } else if (d == 1) {
+        zp = (E[0][gidx(g, i, j, k + 1)] - E[0][gidx(g, i, j, k)]) * idz;
+        rest = -(E[2][gidx(g, i + 1, j, k)] - E[2][gidx(g, i, j, k)]) * idx;
+    } else {
+        rest = (E[1][gidx(g, i + 1, j, k)] - E[1][gidx(g, i, j, k)]) * idx
+             - (E[0][gidx(g, i, j + 1, k)] - E[0][gidx(g, i, j, k)]) * idy;
+        zp = T(0);
+    }
+}
+
+// ------------------------------------------------------------ sources
+
+__device__ __forceinline__ double waveform(double amp, double f0, double tp, double t0, double t)
+{
+    double u = t - t0;
+    return amp * exp(-u * u / (2.0 * tp * tp)) * cos(2.0 * kPi * f0 * t);
+}
+
+// Soft J on edge (c, i, j, k) at time t: point sources and TE10-shaped plane
+// sources (profile sin(pi x / W) across x).  Indices on periodic axes are
+// compared modulo n so that a duplicate node receives the same current.
+template <typename T>
+__device__ __forceinline__ double j_source(const Geo &g, const Src<T> *src, int nsrc, int c, int i,
+                                           int j, int k, double t)
+{
+    double J = 0.0;
+    int ci = (g.per[0] && c != 0 && i == g.n[0]) ? 0 : i;
+    int cj = (g.per[1] && c != 1 && j == g.n[1]) ? 0 : j;
+    int ck = (g.per[2] && c != 2 && k == g.n[2]) ? 0 : k;
+    for (int s = 0; s < nsrc; s++) {
+        const Src<T> &q = src[s];
+        if (q.comp != c) continue;
+        if (q.kind == 0) {
+            if (q.i == ci && q.j == cj && q.k == ck) J += waveform(q.amp, q.f0, q.tp, q.t0, t);
+        } else if (q.kind == 1) {
+            if (q.k != ck) continue;
+            double x = (c == 0 ? ci + 0.5 : (double)ci) * g.d[0];
+            double W = g.n[0] * g.d[0];
+            J += waveform(q.amp, q.f0, q.tp, q.t0, t) * sin(kPi * x / W);
+        }
+    }
+    return J;
+}
+
+// ------------------------------------------------ Step 2: the E update
+
+// E^(n+1) = ca E^n + cb (curl H^(n+1/2) - J^(n+1/2)), ca = (eps/dt - s/2)/
+// (eps/dt + s/2), cb = 1/(eps/dt + s/2) (Sec. 3.2.1, Step 2); PEC edges are
+// held at zero; in the z-PML the z part is damped before and after its
+// update (time-centred split field).
+template <typename T>
+__device__ __forceinline__ void e_edge(const Geo &g, const Fields<T> &f, int c, int i, int j, int k,
+                                       double J)
+{
+    size_t q = gidx(g, i, j, k);
+    bool wall = (c != 0 && wall_node(g, 0, i)) || (c != 1 && wall_node(g, 1, j)) ||
+                (c != 2 && wall_node(g, 2, k));
+    if (wall) {
+        f.E[c][q] = T(0);
+        if (c < 2 && f.Ezp[c]) f.Ezp[c][q] = T(0);
+        return;
+    }
+    T rest, zp;
+    curl_h(g, f.H, c, i, j, k, rest, zp);
+    T ca = f.ca[c] ? f.ca[c][q] : T(1);
+    T cb = f.cb[c][q];
+    T v;
+    if (c < 2 && pml_e_plane(g, k)) {
+        T h = f.dampE[k];
+        T ez = f.Ezp[c][q];
+        T er = f.E[c][q] - ez;
+        T ez1 = (ca * (ez * h) + cb * zp) * h;
+        T er1 = ca * er + cb * (rest - (T)J);
+        f.Ezp[c][q] = ez1;
+        v = er1 + ez1;
+    } else {
+        v = ca * f.E[c][q] + cb * (rest + zp - (T)J);
+    }
+    f.E[c][q] = v;
+    if (!isfinite((double)v)) atomicOr(f.err, kErrNonFinite);
+}
+
+// ------------------------------------------- Steps 1/3: non-magnetic faces
+
+// H^(n+1/2) = H^n - dt/(2 mu) curl E (Eq. iterate_H with mu for mu0, Ms = 0),
+// PEC wall faces zero, time-centred z-PML split.  Reads Hin, writes Hout
+// (the same array for the streaming kernel).
+template <typename T>
+__device__ __forceinline__ T h_face_nonmag(const Geo &g, const Fields<T> &f, int d, int i, int j, int k,
+                                           const T *Hin)
+{
+    size_t q = gidx(g, i, j, k);
+    int ix[3] = {i, j, k};
+    if (wall_node(g, d, ix[d])) {
+        if (d < 2 && f.Hzp[d]) f.Hzp[d][q] = T(0);
+        return T(0);
+    }
+    T rest, zp;
+    curl_e(g, f.E, d, i, j, k, rest, zp);
+    T fh = f.fh[d] ? f.fh[d][q] : f.fh0;
+    T v;
+    if (d < 2 && pml_h_plane(g, k)) {
+        T h = f.dampH[k];
+        T hz = f.Hzp[d][q];
+        T hr = Hin[q] - hz;
+        T hz1 = (hz * h - fh * zp) * h;
+        T hr1 = hr - fh * rest;
+        f.Hzp[d][q] = hz1;
+        v = hr1 + hz1;
+    } else {
+        v = Hin[q] - fh * (rest + zp);
+    }
+    return v;
+}
+
+// ------------------------------------------------ LLG: one iterate
+
+// One solve of the trapezoidal LLG step (Eqs. llg_tra4-llg_tra6) written for
+// the increment: with b = M^n + beta, beta = -kappa M^n x Heff^n and
+// a = -(kappa Heff^(r-1) + alpha/Ms M^n), x = (b + (a.b) a - a x b)/(1+|a|^2)
+// gives delta = x - M^n = (beta + (a.b) a - |a|^2 M^n - a x b)/(1+|a|^2);
+// N(x) = x Ms/|x| then gives DeltaM = delta + (delta + M^n)(s - 1) with
+// s - 1 = q/(|x|(Ms + |x|)), q = Ms^2 - |x|^2 = e0 - 2 M^n.delta - |delta|^2
+// and e0 = Ms^2 - |M^n|^2.  Every term is small next to Ms, so FP32 keeps the
+// relative precision of the increment (no cancellation against |M| ~ Ms).
+template <typename T>
+__device__ __forceinline__ void llg_iterate(const T Mn[3], const T beta[3], const T heff[3], T kap,
+                                            T aoms, T Ms, T e0, T dM[3])
+{
+    T a[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) a[c] = -(kap * heff[c] + aoms * Mn[c]);
+    T ab = (a[0] * Mn[0] + a[1] * Mn[1] + a[2] * Mn[2]) + (a[0] * beta[0] + a[1] * beta[1] + a[2] * beta[2]);
+    T aa = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+    T b[3] = {Mn[0] + beta[0], Mn[1] + beta[1], Mn[2] + beta[2]};
+    T axb[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+    T inv = T(1) / (T(1) + aa);
+    T del[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) del[c] = (beta[c] + ab * a[c] - aa * Mn[c] - axb[c]) * inv;
+    T md = Mn[0] * del[0] + Mn[1] * del[1] + Mn[2] * del[2];
+    T dd = del[0] * del[0] + del[1] * del[1] + del[2] * del[2];
+    T qv = e0 - (T(2) * md + dd);
+    T xn = sqrt(Ms * Ms - qv);
+    T sm1 = qv / (xn * (Ms + xn));
+#pragma unroll
+    for (int c = 0; c < 3; c++) dM[c] = del[c] + (del[c] + Mn[c]) * sm1;
+}
+
+// First-order scheme (Sec. 3.2.1, Steps 1/3): forward Euler of Eq. LLG_scalar
+// over the half step, delta = -c1 M^n x H - c2 M^n x (M^n x H), then N().
+template <typename T>
+__device__ __forceinline__ void llg_euler(const T Mn[3], const T heff[3], T c1, T c2, T Ms, T e0, T dM[3])
+{
+    T mxh[3] = {Mn[1] * heff[2] - Mn[2] * heff[1], Mn[2] * heff[0] - Mn[0] * heff[2],
+                Mn[0] * heff[1] - Mn[1] * heff[0]};
+    T mxmxh[3] = {Mn[1] * mxh[2] - Mn[2] * mxh[1], Mn[2] * mxh[0] - Mn[0] * mxh[2],
+                  Mn[0] * mxh[1] - Mn[1] * mxh[0]};
+    T del[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) del[c] = -c1 * mxh[c] - c2 * mxmxh[c];
+    T md = Mn[0] * del[0] + Mn[1] * del[1] + Mn[2] * del[2];
+    T dd = del[0] * del[0] + del[1] * del[1] + del[2] * del[2];
+    T qv = e0 - (T(2) * md + dd);
+    T xn = sqrt(Ms * Ms - qv);
+    T sm1 = qv / (xn * (Ms + xn));
+#pragma unroll
+    for (int c = 0; c < 3; c++) dM[c] = del[c] + (del[c] + Mn[c]) * sm1;
+}
+
+} // namespace mmx

@@ -1,0 +1,148 @@
+"""GPU (sm_103a) vs FP64 CPU oracle, element by element, through the C ABI.
+
+FP64 bar: relative L2 <= 1e-12 per field (E 3, H 3, M 9 and the PML parts),
+and identical H/M iteration counts for every half step (the domain-wide
+stopping rule of Sec. 3.2.2 must make the same decisions)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2103_12819_b300 as mmx
+import workloads as W
+from conftest import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+def _compare(sim, ref, fids=range(15), tol=TOL64, label=""):
+    worst = {}
+    for fid in fids:
+        a = sim.get_field(fid)
+        b = ref.get_field(fid)
+        nb = np.linalg.norm(b)
+        err = rel_l2(a, b) if nb > 0 else float(np.abs(a - b).max())
+        worst[fid] = err
+        assert err <= tol, (label, fid, err)
+    return worst
+
+
+def _run_pair(w, steps, prec=mmx.FP64, path=mmx.PATH_PLAIN):
+    ref = oracle.from_workload(w)
+    ref.step(steps)
+    sim = mmx.from_workload(w, prec=prec, path=path)
+    sim.step(steps)
+    assert sim.sync(check=False) == 0, sim.last_error()
+    return sim, ref
+
+
+# ------------------------------------------------------------------ a1 setup
+
+@pytest.mark.parametrize("bc", [(W.PEC,) * 3, (W.PERIODIC,) * 3, (W.PERIODIC, W.PEC, W.PML)])
+def test_a1_materials_match_oracle(bc):
+    w = W.random_small(3, n=(7, 6, 12), bc=bc, pml_cells=3 if bc[2] == W.PML else 0)
+    ref = oracle.from_workload(w)
+    sim = mmx.from_workload(w)
+    for which in range(18):
+        np.testing.assert_allclose(sim.get_material(which), ref.get_material(which), rtol=1e-15,
+                                   err_msg=str(which))
+
+
+@pytest.mark.parametrize("prec,tol", [(mmx.FP64, 1e-15), (mmx.FP32, 2e-7)])
+def test_a1_initial_m_matches_oracle(prec, tol):
+    w = W.random_small(4, n=(6, 7, 5), bc=(W.PEC, W.PERIODIC, W.PEC))
+    ref = oracle.from_workload(w)
+    sim = mmx.from_workload(w, prec=prec)
+    for fid in range(6, 15):
+        assert rel_l2(sim.get_field(fid), ref.get_field(fid)) <= tol, fid
+
+
+# ------------------------------------------- the coupled step, FP64 parity
+
+def test_yig_slab_32_fp64_200_steps():
+    """The 32^3 YIG-slab box: 200 steps, tol 1e-10, PEC, point Jx source."""
+    w = W.yig_slab_32()
+    sim, ref = _run_pair(w, w.steps)
+    _compare(sim, ref, label="yig_slab_32")
+    np.testing.assert_array_equal(sim.get_iter_log(), ref.iter_log())
+
+
+CASES = [
+    dict(seed=11, bc=(W.PEC, W.PEC, W.PEC)),
+    dict(seed=12, bc=(W.PERIODIC, W.PERIODIC, W.PERIODIC)),
+    dict(seed=13, bc=(W.PERIODIC, W.PEC, W.PERIODIC)),
+    dict(seed=14, bc=(W.PEC, W.PEC, W.PML), pml_cells=3, n=(6, 5, 16)),
+    dict(seed=15, bc=(W.PERIODIC, W.PERIODIC, W.PML), pml_cells=4, n=(5, 4, 18)),
+    dict(seed=16, bc=(W.PEC, W.PEC, W.PEC), hard=True),
+    dict(seed=17, bc=(W.PEC, W.PERIODIC, W.PEC), order=1),
+    dict(seed=18, bc=(W.PERIODIC, W.PEC, W.PEC), magnetic=False),
+    dict(seed=19, bc=(W.PEC, W.PEC, W.PEC), n=(1, 9, 7)),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[str(c["seed"]) for c in CASES])
+def test_random_small_fp64(case):
+    kw = dict(case)
+    seed = kw.pop("seed")
+    w = W.random_small(seed, **kw)
+    sim, ref = _run_pair(w, 8)
+    fids = list(range(15)) + ([15, 16, 17, 18] if w.bc[2] == W.PML else [])
+    _compare(sim, ref, fids=fids, label=str(seed))
+    np.testing.assert_array_equal(sim.get_iter_log(), ref.iter_log()[: len(sim.get_iter_log())])
+
+
+def test_convergence_problem_32_fp64():
+    """The paper's periodic coupled problem (Sec. 5.1) on 32^3, 5 steps:
+    magnetic everywhere, sigma/eps/Ms/alpha/gamma bumps."""
+    w = W.convergence(32)
+    sim, ref = _run_pair(w, w.steps)
+    _compare(sim, ref, label="convergence_32")
+    np.testing.assert_array_equal(sim.get_iter_log(), ref.iter_log())
+
+
+def test_waveguide_full_size_fp64_parity():
+    """The 128x128x512 waveguide (z-PML, YIG slab, TE10 source) at full size,
+    same launch configuration as the benchmark, 6 steps against the oracle."""
+    w = W.waveguide(steps=6)
+    sim, ref = _run_pair(w, 6)
+    _compare(sim, ref, fids=list(range(19)), label="waveguide")
+    np.testing.assert_array_equal(sim.get_iter_log(), ref.iter_log())
+
+
+# ----------------------------------------------------------- FP32 path
+
+def test_fp32_error_against_oracle_yig_slab():
+    """FP32 storage and arithmetic (FP64 only in e0 = Ms^2 - |M^n|^2 and the
+    residual): stated error after 200 steps of the 32^3 slab."""
+    w = W.yig_slab_32()
+    w.tol = 1e-6
+    ref = oracle.from_workload(w)
+    ref.step(w.steps)
+    sim = mmx.from_workload(w, prec=mmx.FP32)
+    sim.step(w.steps)
+    assert sim.sync(check=False) == 0
+    errs = {fid: rel_l2(sim.get_field(fid), ref.get_field(fid)) for fid in range(15)}
+    print("fp32 rel L2 per field:", {k: "%.2e" % v for k, v in errs.items()})
+    assert max(errs.values()) < 1e-4, errs
+
+
+# ------------------------------------------------------- error reporting
+
+def test_iteration_cap_is_reported():
+    w = W.yig_slab_32(steps=2)
+    w.max_iter = 1
+    sim = mmx.from_workload(w)
+    sim.step(1)
+    assert sim.sync(check=False) == -4
+    assert sim.sync(check=False) == 0      # reading clears the latch
+
+
+def test_nonfinite_is_reported():
+    w = W.yig_slab_32(steps=2)
+    sim = mmx.from_workload(w)
+    e = np.zeros(sim.field_size(0))
+    e[16 + 32 * (16 + 33 * 16)] = np.nan       # interior Ex edge (16.5, 16, 16)
+    sim.set_field(0, e)
+    sim.step(1)
+    assert sim.sync(check=False) == -5
