@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Throughput of the coupled E/H/M step on the 128x128x512 waveguide.
+
+One "step" is one full time step of the scheme (H/M half step, E update,
+H/M half step, Sec. 3.2 of arXiv 2103.12819) on the 128x128x512 PEC
+waveguide with 10-cell z-PML ends, a YIG-like slab and a TE10 soft source,
+from seeded synthetic inputs already resident in HBM.  The headline runs in
+FP32; the FP64 path and the plain one-kernel-per-update path are measured
+beside it.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank advances its own
+replica: the method has no exchange step at one GPU per instance, so the
+scaling is weak and `value` is the sum over ranks.  `--impl reference` times
+the FP64 CPU oracle on the host cores instead (rank 0 only).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled E/H/M cell-updates/s and % of HBM roofline; FP32 vs FP64 path at stated error"
+UNIT = "cell-updates/s"
+WORKLOAD = "waveguide_128x128x512"
+L2_BYTES = 126 * 2 ** 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def config_block(w, prec_name, path_name):
+    state_bytes = 6 * w.ncells * (4 if prec_name == "fp32" else 8)
+    return {
+        "workload": WORKLOAD,
+        "cells": w.ncells,
+        "grid": list(w.n),
+        "cell_size_m": w.d[0],
+        "dt_s": w.dt,
+        "boundaries": "PEC x/y, 10-cell z-PML",
+        "magnetic_fraction": float(np.count_nonzero(w.Ms > 0)) / w.ncells,
+        "precision": prec_name,
+        "path": path_name,
+        "tol": w.tol,
+        "l2_policy": "inputs larger than L2 (E+H state %.0f MB > %d MB L2)" % (state_bytes / 1e6, L2_BYTES >> 20),
+    }
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- helpers
+
+def alg_bytes_per_cell(kernel, w, esz):
+    """Algorithmic DRAM bytes per cell for one launch of each kernel (what the
+    method must move, single pass): E update reads E, H, eps_r and writes E
+    (10 words); a non-magnetic H half step reads E, H and writes H (9 words);
+    a fused E+H+H pass reads E, H, eps_r and writes E, H (13 words); the H/M
+    box kernel reads E, H, M, Ms, alpha, gamma and writes H, M on its faces
+    (per magnetic cell 6 + 9 + 3 read, 3 + 9 written)."""
+    words = {"e_update": 10, "h_update": 9, "fused_eh": 13}.get(kernel)
+    if words is not None:
+        return words * esz
+    return None
+
+
+def time_steps(torch, sim, stream, K, dist=None):
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms
+
+
+def run_path(torch, mmx, w, prec, path, K, W, stream, dist=None, profile=True):
+    sim = mmx.from_workload(w, prec=prec, stream=stream.cuda_stream, path=path)
+    sim.step(W)
+    rc = sim.sync(check=False)
+    if rc:
+        raise RuntimeError("warm-up failed: %s" % sim.last_error())
+    ms = time_steps(torch, sim, stream, K, dist)
+    rc = sim.sync(check=False)
+    if rc:
+        raise RuntimeError("timed run failed: %s" % sim.last_error())
+    prof = None
+    if profile:
+        sim.set_profiling(True)
+        sim.get_profile(reset=True)
+        sim.step(K)
+        prof = sim.get_profile(reset=True)
+        sim.set_profiling(False)
+    stats = sim.get_stats()
+    return sim, ms, prof, stats
+
+
+def roofline_of(prof, K, w, esz, peak_gbs, peak_kind):
+    if not prof:
+        return None, None
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (launches, total_ms) = dom
+    avg_ms = total_ms / launches
+    bpc = alg_bytes_per_cell(name, w, esz)
+    launches_per_step = sum(v[0] for v in prof.values()) / K
+    if bpc is None:
+        return {"bound": "hbm", "kernel": name, "achieved": None, "peak": peak_gbs, "unit": "GB/s",
+                "frac": None, "traffic": None, "peak_kind": peak_kind}, launches_per_step
+    achieved = bpc * w.ncells / (avg_ms * 1e-3) / 1e9
+    shares = {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in prof.items()}
+    return {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak_gbs,
+            "unit": "GB/s", "frac": round(achieved / peak_gbs, 4), "traffic": None,
+            "peak_kind": peak_kind, "alg_bytes_per_cell": bpc, "avg_launch_us": round(avg_ms * 1e3, 2),
+            "kernel_shares": shares}, launches_per_step
+
+
+def e2e_leg(torch, mmx, w, prec, path, K, stream):
+    """Through the public API with host buffers: upload the state from pinned
+    host memory, K steps, read the whole state back, all inside the timed
+    region (host wall clock around synchronising calls)."""
+    sim = mmx.from_workload(w, prec=prec, stream=stream.cuda_stream, path=path)
+    sim.step(2)
+    sim.sync()
+    fids = list(range(15))
+    host = {}
+    for fid in fids:
+        t = torch.empty(sim.field_size(fid), dtype=torch.float64, pin_memory=True)
+        t.numpy()[:] = sim.get_field(fid)
+        host[fid] = t
+    out = {fid: torch.empty(sim.field_size(fid), dtype=torch.float64, pin_memory=True) for fid in fids}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for fid in fids:
+        sim.set_field(fid, host[fid].numpy())
+    sim.step(K)
+    for fid in fids:
+        out[fid].numpy()[:] = sim.get_field(fid)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    nbytes = sum(8 * sim.field_size(f) for f in fids)
+    sim.close()
+    return {"value": w.ncells * K / dt, "unit": UNIT, "h2d_bytes_per_step": nbytes // K,
+            "d2h_bytes_per_step": nbytes // K, "what": "set all 15 state fields from pinned host "
+            "float64, %d steps, read all 15 back" % K}
+
+
+def cpu_baseline(w, budget_s=15.0):
+    """The FP64 oracle as it stands, single thread, on a bounded sample of
+    the same workload (first steps of the run)."""
+    import oracle
+    s = oracle.from_workload(w)
+    s.step(1)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        s.step(1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or n >= 50:
+            break
+    s.close()
+    return {"value": w.ncells * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%s, %d oracle steps after 1 warm-up step, single thread, %.1f s" % (WORKLOAD, n, el)}
+
+
+# ---------------------------------------------------------------- arms
+
+def reference_arm(args):
+    import workloads
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = workloads.waveguide()
+    base = cpu_baseline(w, budget_s=min(120.0, 5.0 + 2.5 * args.steps))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * w.ncells / base["value"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_block(w, "fp64", "oracle"), "cpu_baseline": base,
+        "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ours_arm(args):
+    import torch
+    import paper_2103_12819_b300 as mmx
+    import workloads
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        torch.cuda.set_device(local)
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    else:
+        torch.cuda.set_device(0)
+    peak, peak_kind = peaks()
+    K, W = args.steps, max(3, args.warmup)
+    w = workloads.waveguide()
+    stream = torch.cuda.Stream()
+    path = mmx.PATH_FUSED
+    with torch.cuda.stream(stream):
+        with ClockSampler(local) as clk:
+            sim32, ms32, prof32, stats32 = run_path(torch, mmx, w, mmx.FP32, path, K, W, stream, dist)
+        clocks = clk.summary()
+        roof, lps = roofline_of(prof32, K, w, 4, peak, peak_kind)
+        sim64, ms64, prof64, stats64 = run_path(torch, mmx, w, mmx.FP64, path, K, W, stream, dist)
+        roof64, _ = roofline_of(prof64, K, w, 8, peak, peak_kind)
+        simp, msp, profp, _ = run_path(torch, mmx, w, mmx.FP64, mmx.PATH_PLAIN, K, W, stream, dist,
+                                       profile=False)
+        simp.close()
+        # FP32 vs FP64 after the same (W + 2K) steps
+        errs = {}
+        for fid in range(15):
+            a, b = sim32.get_field(fid), sim64.get_field(fid)
+            nb = np.linalg.norm(b)
+            errs[fid] = float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.abs(a - b).max())
+        sim32.close()
+        sim64.close()
+        e2e = e2e_leg(torch, mmx, w, mmx.FP32, path, K, stream)
+    cells_total = w.ncells * world
+    value = cells_total * K / (ms32 * 1e-3)
+    mag_frac = float(np.count_nonzero(w.Ms > 0)) / w.ncells
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms32 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded workload generator; no dataset)",
+        "config": config_block(w, "fp32", "fused" if path == mmx.PATH_FUSED else "plain"),
+        "roofline": roof,
+        # B_alg = (13 + 21 f) words per cell-update (E, H, eps_r in and E, H
+        # out everywhere; M, Ms, alpha, gamma in and M out on magnetic cells)
+        "effective_hbm_fraction": round((13 + 21 * mag_frac) * 4 * value / world / (peak * 1e9), 4),
+        "clocks": clocks,
+        "gpu_launches": int(round(lps * K)) if lps else None,
+        "e2e": e2e,
+        "fp64": {"value": cells_total * K / (ms64 * 1e-3), "ms_per_step": ms64 / K, "roofline": roof64,
+                 "iters_min": stats64["iters_min"], "iters_max": stats64["iters_max"]},
+        "plain_fp64": {"value": cells_total * K / (msp * 1e-3), "ms_per_step": msp / K},
+        "fp32_vs_fp64_rel_l2_after_steps": {"steps": W + 2 * K, "max": max(errs.values()),
+                                            "per_field": {str(k): float("%.3e" % v) for k, v in errs.items()}},
+        "iters": {"min": stats32["iters_min"], "max": stats32["iters_max"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -156,8 +156,11 @@ MMX_API int mmx_get_material(mmx_ctx *ctx, int which, double *host, long long n)
 MMX_API int mmx_add_source(mmx_ctx *ctx, const mmx_source_desc *src);
 
 /* Select the kernel path: MMX_PATH_PLAIN runs one kernel per update (H/M
- * half step, E update, H/M half step); MMX_PATH_FUSED (default) fuses the
- * streaming E and H updates.  Both compute the same scheme. */
+ * half step, E update, H/M half step); MMX_PATH_FUSED (default) makes one
+ * streaming pass per step (E update plus the two non-magnetic H half steps
+ * that share curl E^(n+1)) and one launch for the magnetic box.  Both
+ * compute the same scheme; contexts with hard sources always take the plain
+ * path. */
 MMX_API int mmx_set_path(mmx_ctx *ctx, int path);
 
 /* Advance nsteps full time steps (Sec. 3.2: H/M half step with E^n, E
@@ -181,10 +184,26 @@ MMX_API int mmx_get_stats(mmx_ctx *ctx, mmx_stats *out);
  * negative error.  Synchronises. */
 MMX_API long long mmx_get_iter_log(mmx_ctx *ctx, int *host, long long cap);
 
-/* Device pointer and element strides of a field's storage: element (i, j, k)
- * is at ptr[i + sx*j + sy*k] with elements of 8 (FP64) or 4 (FP32) bytes.
- * Valid until mmx_destroy; contents change under mmx_step. */
+/* Device pointer and element strides of an E or H field's storage (ids
+ * 0-5): element (i, j, k) is at ptr[i + sx*j + sy*k] with elements of 8 (FP64)
+ * or 4 (FP32) bytes.  Valid until the next mmx_step, which may move the field
+ * to the context's second buffer set. */
 MMX_API int mmx_get_field_device(mmx_ctx *ctx, int field_id, void **ptr, long long *sx, long long *sy);
+
+/* Per-kernel timing, the counterpart of the per-routine profile of the
+ * paper's Table 1 ("Evolve HM", "Evolve E"): while enabled, every kernel the
+ * context launches is bracketed by CUDA events on the context stream.
+ * mmx_get_profile synchronises, fills up to cap records (kernel name,
+ * launches, total device milliseconds) and returns the number of kernel
+ * kinds seen; reset = 1 clears the accumulated records afterwards. */
+typedef struct {
+    char name[32];
+    long long launches;
+    double total_ms;
+} mmx_kernel_profile;
+
+MMX_API int mmx_set_profiling(mmx_ctx *ctx, int enable);
+MMX_API int mmx_get_profile(mmx_ctx *ctx, mmx_kernel_profile *out, int cap, int reset);
 
 /* Message of the last error on this context (never NULL). */
 MMX_API const char *mmx_last_error(const mmx_ctx *ctx);

@@ -60,6 +60,18 @@
  *   R12 initial M on a face whose averaged M is below 1e-6 Ms_face takes the
  *       lower-index cell's direction; a magnetic face left without any
  *       direction is an input error.
+ *   R13 Eq. iterate_H subtracts M^r (~Ms ~ 1e5 A/m) from H^n + M^n: in FP64
+ *       that leaves ~1e-11 A/m of rounding in H per half step, above the
+ *       1e-12 relative bar for H fields of order 1 A/m.  The LLG algebra of
+ *       Eqs. llg_tra4-llg_tra6, N() and Eq. iterate_H are therefore evaluated
+ *       in extended precision (long double) and rounded to FP64 for storage.
+ *   R14 N() returns M to |M| = Ms, which in exact arithmetic M^n already
+ *       has; with M stored in floating point it also pulls the rounding of
+ *       the stored M^n (an ulp of Ms, ~3e-11 A/m in FP64) back onto the
+ *       sphere.  Eq. iterate_H uses M^n - M^(n+1/2,r) taken along the sphere
+ *       through the stored M^n, x Ms_n/|x| - M^n with Ms_n = |M^n| (equal to
+ *       N()'s change in exact arithmetic), so that this storage rounding does
+ *       not enter H; the stored M^(n+1/2,r) is N(x) itself.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -91,7 +103,8 @@ typedef struct orc_sim {
     grid3 Hhalf[3];                 /* non-magnetic end-of-half-step H */
     long long nmag[3], *mag[3];     /* flat indices of magnetic faces per family */
     int *magix[3];                  /* (i, j, k) of each magnetic face */
-    double *C[3], *Bv[3], *Mn[3], *Mr[3], *Hr[3];  /* per magnetic face work */
+    long double *C[3], *Bv[3];      /* per magnetic face: H^n - dt/(2 mu0) curl E, b */
+    double *Mn[3], *Mr[3], *Hr[3];  /* per magnetic face work */
     orc_source *src;
     int nsrc;
     int *iters;
@@ -256,7 +269,8 @@ static void free_mag(orc_sim *s)
 {
     for (int d = 0; d < 3; d++) {
         free(s->mag[d]); free(s->magix[d]); free(s->C[d]); free(s->Bv[d]); free(s->Mn[d]); free(s->Mr[d]); free(s->Hr[d]);
-        s->mag[d] = NULL; s->magix[d] = NULL; s->C[d] = s->Bv[d] = s->Mn[d] = s->Mr[d] = s->Hr[d] = NULL;
+        s->mag[d] = NULL; s->magix[d] = NULL; s->C[d] = s->Bv[d] = NULL;
+        s->Mn[d] = s->Mr[d] = s->Hr[d] = NULL;
         s->nmag[d] = 0;
     }
 }
@@ -336,9 +350,9 @@ static int build_mag(orc_sim *s)
         size_t m = (size_t)(cnt > 0 ? cnt : 1);
         s->mag[d] = (long long *)malloc(m * sizeof(long long));
         s->magix[d] = (int *)malloc(3 * m * sizeof(int));
-        s->C[d] = (double *)malloc(m * sizeof(double));
+        s->C[d] = (long double *)malloc(m * sizeof(long double));
         s->Hr[d] = (double *)malloc(m * sizeof(double));
-        s->Bv[d] = (double *)malloc(3 * m * sizeof(double));
+        s->Bv[d] = (long double *)malloc(3 * m * sizeof(long double));
         s->Mn[d] = (double *)malloc(3 * m * sizeof(double));
         s->Mr[d] = (double *)malloc(3 * m * sizeof(double));
         if (!s->mag[d] || !s->magix[d] || !s->C[d] || !s->Hr[d] || !s->Bv[d] || !s->Mn[d] || !s->Mr[d]) return ORC_ERR_OOM;
@@ -414,6 +428,13 @@ static void renorm(double m[3], double Ms)
 {
     double nrm = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
     double f = Ms / nrm;
+    m[0] *= f; m[1] *= f; m[2] *= f;
+}
+
+static void renorm_ld(long double m[3], long double Ms)
+{
+    long double nrm = sqrtl(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+    long double f = Ms / nrm;
     m[0] *= f; m[1] *= f; m[2] *= f;
 }
 
@@ -631,7 +652,17 @@ static void h_vector(const orc_sim *s, grid3 *const Hsrc[3], int d, const int ix
     }
 }
 
-static void cross(const double a[3], const double b[3], double r[3])
+/* H^(n+1/2,r) on a magnetic face from Eq. iterate_H,
+ * H^n - dt/(2 mu0) curl E - (M^(n+1/2,r) - M^n)_d, with the change of M taken
+ * along the sphere through the stored M^n (reading R14): x |M^n|/|x| - M^n. */
+static double h_from_x(long double C, const long double x[3], const double Mn[3], int d)
+{
+    long double xn = sqrtl(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    long double mn = sqrtl((long double)Mn[0] * Mn[0] + (long double)Mn[1] * Mn[1] + (long double)Mn[2] * Mn[2]);
+    return (double)(C - (x[d] * (mn / xn) - (long double)Mn[d]));
+}
+
+static void cross_ld(const long double a[3], const long double b[3], long double r[3])
 {
     r[0] = a[1] * b[2] - a[2] * b[1];
     r[1] = a[2] * b[0] - a[0] * b[2];
@@ -767,15 +798,16 @@ static int hm_half_step(orc_sim *s)
             double rest, zp;
             curl_e(s, d, ix, &rest, &zp);
             double Mn[3] = {s->M[d][0].v[q], s->M[d][1].v[q], s->M[d][2].v[q]};
-            s->C[d][m] = s->H[d].v[q] + Mn[d] - dt / (2.0 * ORC_MU0) * (rest + zp);
+            s->C[d][m] = (long double)s->H[d].v[q] - (long double)(dt / (2.0 * ORC_MU0) * (rest + zp));
             for (int c = 0; c < 3; c++) s->Mn[d][3 * m + c] = Mn[c];
             if (s->order == 2) {
-                double h[3], heff[3], mxh[3];
+                double h[3];
+                long double heff[3], mxh[3], Ml[3] = {Mn[0], Mn[1], Mn[2]};
                 h_vector(s, Hcur, d, ix, h);
-                for (int c = 0; c < 3; c++) heff[c] = s->h0[c] + h[c];
-                double kappa = ORC_MU0 * s->gam[d].v[q] * dt / 4.0;
-                cross(Mn, heff, mxh);
-                for (int c = 0; c < 3; c++) s->Bv[d][3 * m + c] = Mn[c] - kappa * mxh[c];
+                for (int c = 0; c < 3; c++) heff[c] = (long double)s->h0[c] + h[c];
+                long double kappa = (long double)(ORC_MU0 * s->gam[d].v[q] * dt / 4.0);
+                cross_ld(Ml, heff, mxh);
+                for (int c = 0; c < 3; c++) s->Bv[d][3 * m + c] = Ml[c] - kappa * mxh[c];
             }
         }
     }
@@ -788,20 +820,22 @@ static int hm_half_step(orc_sim *s)
             for (long long m = 0; m < s->nmag[d]; m++) {
                 long long q = s->mag[d][m];
                 const int *ix = &s->magix[d][3 * m];
-                double h[3], heff[3], mxh[3], mxmxh[3];
+                double h[3];
+                long double heff[3], mxh[3], mxmxh[3], x[3];
                 h_vector(s, Hcur, d, ix, h);
-                for (int c = 0; c < 3; c++) heff[c] = s->h0[c] + h[c];
+                for (int c = 0; c < 3; c++) heff[c] = (long double)s->h0[c] + h[c];
                 double Ms = s->ms[d].v[q], al = s->alp[d].v[q];
                 double gL = s->gam[d].v[q] / (1.0 + al * al);
-                double *Mn = &s->Mn[d][3 * m];
-                cross(Mn, heff, mxh);
-                cross(Mn, mxh, mxmxh);
-                double x[3];
+                long double Mn[3] = {s->Mn[d][3 * m], s->Mn[d][3 * m + 1], s->Mn[d][3 * m + 2]};
+                cross_ld(Mn, heff, mxh);
+                cross_ld(Mn, mxh, mxmxh);
+                long double c1 = (long double)(ORC_MU0 * gL), c2 = (long double)(al * ORC_MU0 * gL / Ms);
                 for (int c = 0; c < 3; c++)
-                    x[c] = Mn[c] + (dt / 2.0) * (-ORC_MU0 * gL * mxh[c] - al * ORC_MU0 * gL / Ms * mxmxh[c]);
-                renorm(x, Ms);
-                for (int c = 0; c < 3; c++) s->Mr[d][3 * m + c] = x[c];
-                s->Hr[d][m] = wall_face(s, d, ix) ? 0.0 : s->C[d][m] - x[d];
+                    x[c] = Mn[c] + (long double)(dt / 2.0) * (-c1 * mxh[c] - c2 * mxmxh[c]);
+                double hr = h_from_x(s->C[d][m], x, &s->Mn[d][3 * m], d);
+                renorm_ld(x, Ms);
+                for (int c = 0; c < 3; c++) s->Mr[d][3 * m + c] = (double)x[c];
+                s->Hr[d][m] = wall_face(s, d, ix) ? 0.0 : hr;
             }
         }
         for (int d = 0; d < 3; d++) {
@@ -829,28 +863,32 @@ static int hm_half_step(orc_sim *s)
             for (long long m = 0; m < s->nmag[d]; m++) {
                 long long q = s->mag[d][m];
                 const int *ix = &s->magix[d][3 * m];
-                double h[3], heff[3];
+                double h[3];
+                long double heff[3];
                 h_vector(s, Hcur, d, ix, h);
-                for (int c = 0; c < 3; c++) heff[c] = s->h0[c] + h[c];
+                for (int c = 0; c < 3; c++) heff[c] = (long double)s->h0[c] + h[c];
                 double Ms = s->ms[d].v[q], al = s->alp[d].v[q];
-                double kappa = ORC_MU0 * s->gam[d].v[q] * dt / 4.0;
-                const double *Mn = &s->Mn[d][3 * m], *b = &s->Bv[d][3 * m];
+                long double kappa = (long double)(ORC_MU0 * s->gam[d].v[q] * dt / 4.0);
+                long double aoms = (long double)(al / Ms);
+                const double *Mn = &s->Mn[d][3 * m];
+                const long double *b = &s->Bv[d][3 * m];
                 /* a = -[kappa Heff^(r-1) + alpha/Ms M^n]  (Eq. llg_tra5) */
-                double a[3];
-                for (int c = 0; c < 3; c++) a[c] = -(kappa * heff[c] + al / Ms * Mn[c]);
+                long double a[3];
+                for (int c = 0; c < 3; c++) a[c] = -(kappa * heff[c] + aoms * Mn[c]);
                 /* M^r = (b + (a.b) a - a x b)/(1 + |a|^2)  (Eq. llg_tra4) */
-                double ab = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
-                double aa = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
-                double axb[3], x[3];
-                cross(a, b, axb);
-                for (int c = 0; c < 3; c++) x[c] = (b[c] + ab * a[c] - axb[c]) / (1.0 + aa);
-                renorm(x, Ms);
+                long double ab = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+                long double aa = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+                long double axb[3], x[3];
+                cross_ld(a, b, axb);
+                for (int c = 0; c < 3; c++) x[c] = (b[c] + ab * a[c] - axb[c]) / (1.0L + aa);
+                double hr = h_from_x(s->C[d][m], x, Mn, d);
+                renorm_ld(x, Ms);
                 for (int c = 0; c < 3; c++) {
-                    double dm = fabs(x[c] - s->M[d][c].v[q]) / Ms;
+                    double dm = (double)(fabsl(x[c] - (long double)s->M[d][c].v[q]) / Ms);
                     if (dm > rho) rho = dm;
-                    s->Mr[d][3 * m + c] = x[c];
+                    s->Mr[d][3 * m + c] = (double)x[c];
                 }
-                s->Hr[d][m] = wall_face(s, d, ix) ? 0.0 : s->C[d][m] - x[d];
+                s->Hr[d][m] = wall_face(s, d, ix) ? 0.0 : hr;
             }
         }
         /* non-magnetic faces take their final value from r = 1 on (R3) */

@@ -42,10 +42,15 @@ class Stats(ctypes.Structure):
                 ("last_residual", ctypes.c_double), ("status", ctypes.c_int)]
 
 
+class KernelProfile(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong),
+                ("total_ms", ctypes.c_double)]
+
+
 EXPORTS = ("mmx_create", "mmx_set_materials", "mmx_set_bias", "mmx_set_M_cells", "mmx_set_field",
            "mmx_get_field", "mmx_get_material", "mmx_add_source", "mmx_set_path", "mmx_step",
            "mmx_sync", "mmx_get_stats", "mmx_get_iter_log", "mmx_get_field_device",
-           "mmx_last_error", "mmx_destroy")
+           "mmx_set_profiling", "mmx_get_profile", "mmx_last_error", "mmx_destroy")
 
 _lib = None
 
@@ -88,6 +93,10 @@ def lib():
     L.mmx_get_iter_log.argtypes = [P, ctypes.POINTER(ctypes.c_int), LL]
     L.mmx_get_field_device.restype = I
     L.mmx_get_field_device.argtypes = [P, I, ctypes.POINTER(P), ctypes.POINTER(LL), ctypes.POINTER(LL)]
+    L.mmx_set_profiling.restype = I
+    L.mmx_set_profiling.argtypes = [P, I]
+    L.mmx_get_profile.restype = I
+    L.mmx_get_profile.argtypes = [P, ctypes.POINTER(KernelProfile), I, I]
     L.mmx_last_error.restype = ctypes.c_char_p
     L.mmx_last_error.argtypes = [P]
     L.mmx_destroy.restype = None
@@ -240,6 +249,15 @@ class Solver:
         self._check(self._L.mmx_get_field_device(self._h, int(fid), ctypes.byref(p), ctypes.byref(sx),
                                                  ctypes.byref(sy)), "mmx_get_field_device")
         return p.value, sx.value, sy.value
+
+    def set_profiling(self, enable=True):
+        self._check(self._L.mmx_set_profiling(self._h, 1 if enable else 0), "mmx_set_profiling")
+
+    def get_profile(self, reset=True):
+        """{kernel name: (launches, total device ms)} since the last reset."""
+        buf = (KernelProfile * 16)()
+        n = self._check(self._L.mmx_get_profile(self._h, buf, 16, 1 if reset else 0), "mmx_get_profile")
+        return {buf[q].name.decode(): (int(buf[q].launches), float(buf[q].total_ms)) for q in range(min(n, 16))}
 
     def last_error(self):
         return self._L.mmx_last_error(self._h).decode()

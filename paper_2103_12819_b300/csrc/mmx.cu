@@ -19,9 +19,13 @@ using namespace mmx;
 
 namespace {
 
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
+// Kernel kinds timed by the optional profiler.
+enum KernelKind { KK_HM_BOX = 0, KK_H_UPDATE, KK_E_UPDATE, KK_HARD, KK_FUSED, KK_COUNT };
+const char *const kKernelNames[KK_COUNT] = {"hm_box", "h_update", "e_update", "hard_source", "fused_eh"};
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
 };
 
 } // namespace
@@ -35,8 +39,11 @@ struct mmx_ctx {
     int path = MMX_PATH_FUSED;
     std::string err;
 
-    // Yee state
+    // Yee state (current) and the second set the fused path ping-pongs with
     void *E[3] = {}, *H[3] = {}, *Ezp[2] = {}, *Hzp[2] = {};
+    void *Ealt[3] = {}, *Halt[3] = {}, *Ezpalt[2] = {};
+    int fused_chunk = 0;
+    int fused_grid_z = 0;
     // coefficients
     void *ca[3] = {}, *cb[3] = {}, *fh[3] = {};
     void *dampE = nullptr, *dampH = nullptr;
@@ -56,7 +63,7 @@ struct mmx_ctx {
     int coop_blocks = 0;
 
     // control words (device)
-    unsigned long long *res = nullptr;     // [2][kMaxIter+1]
+    unsigned long long *res = nullptr;     // [4][kMaxIter+1]
     unsigned int *bar = nullptr;           // [2]
     int *iterlog = nullptr;                // [kIterLogCap]
     unsigned long long *halfsteps = nullptr;
@@ -64,15 +71,26 @@ struct mmx_ctx {
     int *errw = nullptr;
     int box_slot = 0;
 
-    // sources
+    // sources: descriptors, per-step waveform table (T, kAmpChunk x nsrc)
+    // and the TE10 profile tables (T, nx+1 each)
     std::vector<mmx_source_desc> src;
     void *dsrc = nullptr;
+    void *damp = nullptr;
+    void *dprof[2] = {};
 
     // staging
     double *stage = nullptr;
     size_t stage_elems = 0;
 
     long long steps = 0;
+
+    // optional per-kernel profile
+    bool prof_on = false;
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;
+    long long prof_launches[KK_COUNT] = {};
+    double prof_ms[KK_COUNT] = {};
+    int prof_open = -1;
 };
 
 // ------------------------------------------------------------- helpers
@@ -99,6 +117,54 @@ static int fail(mmx_ctx *c, int code, const char *fmt, ...)
     } while (0)
 
 static bool is_fp64(const mmx_ctx *c) { return c->desc.prec == MMX_FP64; }
+
+constexpr int kAmpChunk = 1024;   // steps whose source values are uploaded at once
+
+static cudaEvent_t prof_event(mmx_ctx *c)
+{
+    if (!c->prof_pool.empty()) {
+        cudaEvent_t e = c->prof_pool.back();
+        c->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket the next launch with events when profiling is enabled.
+static void prof_begin(mmx_ctx *c, int kind)
+{
+    if (!c->prof_on) return;
+    ProfRec r;
+    r.kind = kind;
+    r.a = prof_event(c);
+    r.b = prof_event(c);
+    cudaEventRecord(r.a, c->stream);
+    c->prof_recs.push_back(r);
+    c->prof_open = (int)c->prof_recs.size() - 1;
+}
+
+static void prof_end(mmx_ctx *c)
+{
+    if (!c->prof_on || c->prof_open < 0) return;
+    cudaEventRecord(c->prof_recs[c->prof_open].b, c->stream);
+    c->prof_open = -1;
+}
+
+static void prof_collect(mmx_ctx *c)
+{
+    for (ProfRec &r : c->prof_recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            c->prof_ms[r.kind] += ms;
+            c->prof_launches[r.kind] += 1;
+        }
+        c->prof_pool.push_back(r.a);
+        c->prof_pool.push_back(r.b);
+    }
+    c->prof_recs.clear();
+}
 
 static void edge_ext(const mmx_ctx *c, int comp, int e[3])
 {
@@ -150,6 +216,10 @@ template <typename T> static Fields<T> make_fields(mmx_ctx *c)
     f.fh0 = (T)(c->desc.dt / (2.0 * kMu0));
     f.dampE = (const T *)c->dampE;
     f.dampH = (const T *)c->dampH;
+    for (int a = 0; a < 3; a++) f.inv_d[a] = (T)(1.0 / c->desc.d[a]);
+    f.src_amp = (const T *)c->damp;
+    f.prof[0] = (const T *)c->dprof[0];
+    f.prof[1] = (const T *)c->dprof[1];
     f.err = c->errw;
     return f;
 }
@@ -218,6 +288,31 @@ static void pml_tables(const mmx_ctx *c, std::vector<double> &dE, std::vector<do
         double s = sig((k + 0.5) * dz);
         if (s > 0.0) dH[k] = std::exp(-s * (dt / 4.0) / e0);
     }
+}
+
+// Waveform of a source, g(t) = amp exp(-(t-t0)^2/(2 tp^2)) cos(2 pi f0 t).
+static double host_waveform(const mmx_source_desc &q, double t)
+{
+    double u = t - q.t0;
+    return q.amp * std::exp(-u * u / (2.0 * q.tp * q.tp)) * std::cos(2.0 * kPi * q.f0 * t);
+}
+
+// Soft-source values at t = (n + 1/2) dt for steps n0 .. n0+cnt-1.
+template <typename T> static int upload_amplitudes(mmx_ctx *ctx, long long n0, int cnt)
+{
+    size_t ns = ctx->src.size();
+    if (ns == 0) return MMX_OK;
+    std::vector<T> v((size_t)cnt * ns);
+    for (int s = 0; s < cnt; s++)
+        for (size_t q = 0; q < ns; q++) {
+            const mmx_source_desc &d = ctx->src[q];
+            double val = (d.kind == 0 || d.kind == 1) ? host_waveform(d, ((double)(n0 + s) + 0.5) * ctx->desc.dt) : 0.0;
+            v[(size_t)s * ns + q] = (T)val;
+        }
+    CK(cudaMemcpyAsync(ctx->damp, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    // the host vector dies at return: wait for the copy
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MMX_OK;
 }
 
 template <typename T> static int upload_table(mmx_ctx *ctx, void **dst, const std::vector<double> &v)
@@ -300,13 +395,19 @@ template <typename T> static int set_materials_t(mmx_ctx *ctx)
 
 // ------------------------------------------------------------ stepping
 
-template <typename T> static int launch_box(mmx_ctx *ctx, const Fields<T> &f, const Box<T> &b)
+// One cooperative launch over the magnetic box: nsub H/M half steps with
+// the E in f.E, starting from the H in f.H and ending in Hout.
+template <typename T>
+static int launch_box(mmx_ctx *ctx, const Fields<T> &f, const Box<T> &b, Ptr3<T> Hout, int nsub)
 {
     int slot = ctx->box_slot;
     ctx->box_slot ^= 1;
-    void *args[] = {(void *)&ctx->g, (void *)&f, (void *)&b, (void *)&slot};
-    CK(cudaLaunchCooperativeKernel((const void *)k_hm_box<T>, dim3(ctx->coop_blocks), dim3(256), args, 0,
-                                   ctx->stream));
+    void *args[] = {(void *)&ctx->g, (void *)&f, (void *)&b, (void *)&Hout, (void *)&nsub, (void *)&slot};
+    prof_begin(ctx, KK_HM_BOX);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_hm_box<T>, dim3(ctx->coop_blocks), dim3(256),
+                                                args, 0, ctx->stream);
+    prof_end(ctx);
+    CK(e);
     return MMX_OK;
 }
 
@@ -314,19 +415,26 @@ template <typename T> static int half_step(mmx_ctx *ctx, const Fields<T> &f, con
 {
     dim3 B = node_block(), G = node_grid(ctx);
     if (ctx->magnetic) {
-        int rc = launch_box<T>(ctx, f, b);
+        Ptr3<T> Hout = {{f.H[0], f.H[1], f.H[2]}};
+        int rc = launch_box<T>(ctx, f, b, Hout, 1);
         if (rc) return rc;
+        prof_begin(ctx, KK_H_UPDATE);
         k_h_update<T><<<G, B, 0, ctx->stream>>>(ctx->g, f, ctx->lo[0], ctx->lo[1], ctx->lo[2], ctx->hi[0],
                                                  ctx->hi[1], ctx->hi[2]);
+        prof_end(ctx);
     } else {
+        prof_begin(ctx, KK_H_UPDATE);
         k_h_update<T><<<G, B, 0, ctx->stream>>>(ctx->g, f, 0, 0, 0, 0, 0, 0);
+        prof_end(ctx);
     }
     CK(cudaGetLastError());
     bool hardH = false;
     for (auto &s : ctx->src) hardH |= s.kind == 3;
     if (hardH) {
         Ptr3<T> F = {{f.H[0], f.H[1], f.H[2]}};
+        prof_begin(ctx, KK_HARD);
         k_hard<T><<<1, 32, 0, ctx->stream>>>(ctx->g, F, (const Src<T> *)ctx->dsrc, (int)ctx->src.size(), 3, t_end);
+        prof_end(ctx);
         CK(cudaGetLastError());
     }
     return MMX_OK;
@@ -340,20 +448,114 @@ template <typename T> static int step_plain(mmx_ctx *ctx, int nsteps)
     int nsrc = (int)ctx->src.size();
     bool hardE = false;
     for (auto &s : ctx->src) hardE |= s.kind == 2;
+    const T *amp0 = (const T *)ctx->damp;
     for (int s = 0; s < nsteps; s++) {
         long long n = ctx->steps;
         double dt = ctx->desc.dt;
+        if (s % kAmpChunk == 0) {
+            int rc = upload_amplitudes<T>(ctx, n, std::min(kAmpChunk, nsteps - s));
+            if (rc) return rc;
+        }
+        f.src_amp = amp0 + (size_t)(s % kAmpChunk) * nsrc;
         int rc = half_step<T>(ctx, f, b, (n + 0.5) * dt);
         if (rc) return rc;
-        k_e_update<T><<<G, B, 0, ctx->stream>>>(ctx->g, f, (const Src<T> *)ctx->dsrc, nsrc, n);
+        prof_begin(ctx, KK_E_UPDATE);
+        k_e_update<T><<<G, B, 0, ctx->stream>>>(ctx->g, f, (const Src<T> *)ctx->dsrc, nsrc);
+        prof_end(ctx);
         CK(cudaGetLastError());
         if (hardE) {
             Ptr3<T> F = {{f.E[0], f.E[1], f.E[2]}};
+            prof_begin(ctx, KK_HARD);
             k_hard<T><<<1, 32, 0, ctx->stream>>>(ctx->g, F, (const Src<T> *)ctx->dsrc, nsrc, 2, (n + 1.0) * dt);
+            prof_end(ctx);
             CK(cudaGetLastError());
         }
         rc = half_step<T>(ctx, f, b, (n + 1.0) * dt);
         if (rc) return rc;
+        ctx->steps++;
+    }
+    return MMX_OK;
+}
+
+// ------------------------------------------------------------ fused path
+
+constexpr int kFBX = 32, kFBY = 8;   // fused block: 31 x 7 output columns + halo
+
+// z chunk of the fused kernel: as many chunks as fill one resident wave of
+// blocks (each block marches its whole chunk, so a second wave would double
+// the time).
+template <typename T> static int plan_fused(mmx_ctx *ctx)
+{
+    int dev = 0, nsm = 0, per = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused<T, kFBX, kFBY>, kFBX * kFBY, 0));
+    per = std::max(per, 1);
+    const int *n = ctx->desc.n;
+    long long tiles = (long long)((n[0] + 1 + kFBX - 2) / (kFBX - 1)) * ((n[1] + 1 + kFBY - 2) / (kFBY - 1));
+    // as many z chunks as fit in one resident wave
+    long long nch = std::max(1LL, ((long long)per * nsm) / tiles);
+    int chunk = (int)std::max(2LL, (n[2] + nch - 1) / nch);
+    chunk = std::min(chunk, n[2]);
+    ctx->fused_chunk = chunk;
+    ctx->fused_grid_z = (n[2] + chunk - 1) / chunk;
+    return MMX_OK;
+}
+
+template <typename T> static void swap_buffers(mmx_ctx *ctx)
+{
+    for (int a = 0; a < 3; a++) {
+        std::swap(ctx->E[a], ctx->Ealt[a]);
+        std::swap(ctx->H[a], ctx->Halt[a]);
+    }
+    for (int a = 0; a < 2; a++) std::swap(ctx->Ezp[a], ctx->Ezpalt[a]);
+}
+
+template <typename T> static int step_fused(mmx_ctx *ctx, int nsteps)
+{
+    if (!ctx->fused_chunk) {
+        int rc = plan_fused<T>(ctx);
+        if (rc) return rc;
+    }
+    Box<T> b = make_box<T>(ctx);
+    int nsrc = (int)ctx->src.size();
+    const T *amp0 = (const T *)ctx->damp;
+    // Step 1 of the first step in place: H^n -> H^(n+1/2)
+    {
+        Fields<T> f = make_fields<T>(ctx);
+        int rc = half_step<T>(ctx, f, b, (ctx->steps + 0.5) * ctx->desc.dt);
+        if (rc) return rc;
+    }
+    const int *n = ctx->desc.n;
+    dim3 B(kFBX, kFBY, 1);
+    dim3 G((n[0] + 1 + kFBX - 2) / (kFBX - 1), (n[1] + 1 + kFBY - 2) / (kFBY - 1), ctx->fused_grid_z);
+    for (int s = 0; s < nsteps; s++) {
+        if (s % kAmpChunk == 0) {
+            int rc = upload_amplitudes<T>(ctx, ctx->steps, std::min(kAmpChunk, nsteps - s));
+            if (rc) return rc;
+        }
+        const int nhalf = s == nsteps - 1 ? 1 : 2;
+        Fields<T> f = make_fields<T>(ctx);
+        f.src_amp = amp0 + (size_t)(s % kAmpChunk) * nsrc;
+        Ptr3<T> Eo = {{(T *)ctx->E[0], (T *)ctx->E[1], (T *)ctx->E[2]}};
+        Ptr3<T> Ho = {{(T *)ctx->H[0], (T *)ctx->H[1], (T *)ctx->H[2]}};
+        Ptr3<T> En = {{(T *)ctx->Ealt[0], (T *)ctx->Ealt[1], (T *)ctx->Ealt[2]}};
+        Ptr3<T> Hn = {{(T *)ctx->Halt[0], (T *)ctx->Halt[1], (T *)ctx->Halt[2]}};
+        Ptr3<T> Zo = {{(T *)ctx->Ezp[0], (T *)ctx->Ezp[1], nullptr}};
+        Ptr3<T> Zn = {{(T *)ctx->Ezpalt[0], (T *)ctx->Ezpalt[1], nullptr}};
+        prof_begin(ctx, KK_FUSED);
+        k_fused<T, kFBX, kFBY><<<G, B, 0, ctx->stream>>>(ctx->g, f, Eo, Ho, En, Hn, Zo, Zn, (const Src<T> *)ctx->dsrc,
+                                                        nsrc, nhalf, ctx->fused_chunk, ctx->lo[0], ctx->lo[1],
+                                                        ctx->lo[2], ctx->hi[0], ctx->hi[1], ctx->hi[2]);
+        prof_end(ctx);
+        CK(cudaGetLastError());
+        if (ctx->magnetic) {
+            Fields<T> fb = f;
+            for (int a = 0; a < 3; a++) fb.E[a] = En.p[a];   // E^(n+1); fb.H = H^(n+1/2)
+            int rc = launch_box<T>(ctx, fb, b, Hn, nhalf);
+            if (rc) return rc;
+        }
+        swap_buffers<T>(ctx);
         ctx->steps++;
     }
     return MMX_OK;
@@ -486,20 +688,36 @@ int mmx_create(const mmx_grid_desc *desc, void *cuda_stream, mmx_ctx **out)
     for (int a = 0; a < 3 && !rc; a++) {
         rc = dalloc(ctx, &ctx->E[a], fb);
         if (!rc) rc = dalloc(ctx, &ctx->H[a], fb);
+        if (!rc) rc = dalloc(ctx, &ctx->Ealt[a], fb);
+        if (!rc) rc = dalloc(ctx, &ctx->Halt[a], fb);
         if (!rc) rc = dalloc(ctx, &ctx->cb[a], fb);
     }
     if (!rc && g.npml > 0)
         for (int a = 0; a < 2 && !rc; a++) {
             rc = dalloc(ctx, &ctx->Ezp[a], fb);
+            if (!rc) rc = dalloc(ctx, &ctx->Ezpalt[a], fb);
             if (!rc) rc = dalloc(ctx, &ctx->Hzp[a], fb);
         }
-    if (!rc) rc = dalloc(ctx, (void **)&ctx->res, 2 * (kMaxIter + 1) * sizeof(unsigned long long));
+    if (!rc) rc = dalloc(ctx, (void **)&ctx->res, 4 * (kMaxIter + 1) * sizeof(unsigned long long));
     if (!rc) rc = dalloc(ctx, (void **)&ctx->bar, 2 * sizeof(unsigned int));
     if (!rc) rc = dalloc(ctx, (void **)&ctx->iterlog, kIterLogCap * sizeof(int));
     if (!rc) rc = dalloc(ctx, (void **)&ctx->halfsteps, sizeof(unsigned long long));
     if (!rc) rc = dalloc(ctx, (void **)&ctx->last_res, sizeof(double));
     if (!rc) rc = dalloc(ctx, (void **)&ctx->errw, sizeof(int));
     if (!rc) rc = dalloc(ctx, &ctx->dsrc, kMaxSources * sizeof(Src<double>));
+    if (!rc) rc = dalloc(ctx, &ctx->damp, (size_t)kAmpChunk * kMaxSources * ctx->esz);
+    if (!rc) {
+        // TE10 profile sin(pi x / W) at x = i dx and (i + 1/2) dx, W = nx dx
+        std::vector<double> p0(d.n[0] + 1), p1(d.n[0] + 1);
+        double W = d.n[0] * d.d[0];
+        for (int i = 0; i <= d.n[0]; i++) {
+            double x0 = (double)i * d.d[0], x1 = (i + 0.5) * d.d[0];
+            p0[i] = std::sin(kPi * x0 / W);
+            p1[i] = std::sin(kPi * x1 / W);
+        }
+        rc = is_fp64(ctx) ? upload_table<double>(ctx, &ctx->dprof[0], p0) : upload_table<float>(ctx, &ctx->dprof[0], p0);
+        if (!rc) rc = is_fp64(ctx) ? upload_table<double>(ctx, &ctx->dprof[1], p1) : upload_table<float>(ctx, &ctx->dprof[1], p1);
+    }
     if (!rc) {
         std::vector<double> dE, dH;
         pml_tables(ctx, dE, dH);
@@ -521,13 +739,17 @@ void mmx_destroy(mmx_ctx *ctx)
     if (ctx->E[0]) cudaStreamSynchronize(ctx->stream);
     for (int a = 0; a < 3; a++) {
         cudaFree(ctx->E[a]); cudaFree(ctx->H[a]); cudaFree(ctx->ca[a]); cudaFree(ctx->cb[a]); cudaFree(ctx->fh[a]);
+        cudaFree(ctx->Ealt[a]); cudaFree(ctx->Halt[a]);
     }
-    for (int a = 0; a < 2; a++) { cudaFree(ctx->Ezp[a]); cudaFree(ctx->Hzp[a]); }
+    for (int a = 0; a < 2; a++) { cudaFree(ctx->Ezp[a]); cudaFree(ctx->Hzp[a]); cudaFree(ctx->Ezpalt[a]); }
     for (int a = 0; a < 6; a++) cudaFree(ctx->cell[a]);
     free_box(ctx);
     cudaFree(ctx->dampE); cudaFree(ctx->dampH);
     cudaFree(ctx->res); cudaFree(ctx->bar); cudaFree(ctx->iterlog); cudaFree(ctx->halfsteps);
     cudaFree(ctx->last_res); cudaFree(ctx->errw); cudaFree(ctx->dsrc); cudaFree(ctx->stage);
+    cudaFree(ctx->damp); cudaFree(ctx->dprof[0]); cudaFree(ctx->dprof[1]);
+    for (ProfRec &r : ctx->prof_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -778,6 +1000,10 @@ int mmx_step(mmx_ctx *ctx, int nsteps)
     if (!ctx || !ctx->E[0] || nsteps < 0) return MMX_ERR_INVALID;
     if (nsteps == 0) return MMX_OK;
     CK(cudaMemsetAsync(ctx->bar, 0, 2 * sizeof(unsigned int), ctx->stream));
+    bool hard = false;
+    for (auto &q : ctx->src) hard |= q.kind >= 2;
+    if (ctx->path == MMX_PATH_FUSED && !hard)
+        return is_fp64(ctx) ? step_fused<double>(ctx, nsteps) : step_fused<float>(ctx, nsteps);
     return is_fp64(ctx) ? step_plain<double>(ctx, nsteps) : step_plain<float>(ctx, nsteps);
 }
 
@@ -830,6 +1056,37 @@ long long mmx_get_iter_log(mmx_ctx *ctx, int *host, long long cap)
     CK(cudaMemcpy(v.data(), ctx->iterlog, kIterLogCap * sizeof(int), cudaMemcpyDeviceToHost));
     long long first = (long long)hs - avail;   // oldest kept
     for (long long q = 0; q < m; q++) host[q] = v[(first + q) % kIterLogCap];
+    return m;
+}
+
+int mmx_set_profiling(mmx_ctx *ctx, int enable)
+{
+    if (!ctx || !ctx->E[0]) return MMX_ERR_INVALID;
+    ctx->prof_on = enable != 0;
+    return MMX_OK;
+}
+
+int mmx_get_profile(mmx_ctx *ctx, mmx_kernel_profile *out, int cap, int reset)
+{
+    if (!ctx || !ctx->E[0] || (cap > 0 && !out)) return MMX_ERR_INVALID;
+    CK(cudaStreamSynchronize(ctx->stream));
+    prof_collect(ctx);
+    int m = 0;
+    for (int k = 0; k < KK_COUNT; k++) {
+        if (ctx->prof_launches[k] == 0) continue;
+        if (m < cap) {
+            memset(out[m].name, 0, sizeof out[m].name);
+            strncpy(out[m].name, kKernelNames[k], sizeof out[m].name - 1);
+            out[m].launches = ctx->prof_launches[k];
+            out[m].total_ms = ctx->prof_ms[k];
+        }
+        m++;
+    }
+    if (reset)
+        for (int k = 0; k < KK_COUNT; k++) {
+            ctx->prof_launches[k] = 0;
+            ctx->prof_ms[k] = 0.0;
+        }
     return m;
 }
 

@@ -82,6 +82,9 @@ template <typename T> struct Fields {
     T fh0;
     const T *dampE;     // per z node: exp(-sigma_z dt/(2 eps0)) (PML planes)
     const T *dampH;     // per z cell: exp(-sigma_z dt/(4 eps0))
+    T inv_d[3];         // 1/dx, 1/dy, 1/dz in T (no FP64 in FP32 kernels)
+    const T *src_amp;   // g(t) of every source for the current step
+    const T *prof[2];   // TE10 profile sin(pi x/W): [0] at x = i dx, [1] at (i+1/2) dx
     int *err;
 };
 
@@ -125,10 +128,10 @@ __device__ __forceinline__ size_t bidx(const int lo[3], int bx, int by, int i, i
 // (curl H) on an E edge split into the z-derivative part and the rest
 // (Sec. 3.1: 2nd-order central differences of the face values).
 template <typename T>
-__device__ __forceinline__ void curl_h(const Geo &g, T *const H[3], int c, int i, int j, int k,
-                                       T &rest, T &zp)
+__device__ __forceinline__ void curl_h(const Geo &g, T *const H[3], const T inv_d[3], int c, int i, int j,
+                                       int k, T &rest, T &zp)
 {
-    const T idx = (T)g.inv_d[0], idy = (T)g.inv_d[1], idz = (T)g.inv_d[2];
+    const T idx = inv_d[0], idy = inv_d[1], idz = inv_d[2];
     if (c == 0) {
         int jm = cell_nb(g, 1, j - 1), jp = cell_nb(g, 1, j);
         int km = cell_nb(g, 2, k - 1), kp = cell_nb(g, 2, k);
@@ -150,10 +153,10 @@ __device__ __forceinline__ void curl_h(const Geo &g, T *const H[3], int c, int i
 
 // (curl E) on an H face of family d, split the same way.
 template <typename T>
-__device__ __forceinline__ void curl_e(const Geo &g, T *const E[3], int d, int i, int j, int k,
-                                       T &rest, T &zp)
+__device__ __forceinline__ void curl_e(const Geo &g, T *const E[3], const T inv_d[3], int d, int i, int j,
+                                       int k, T &rest, T &zp)
 {
-    const T idx = (T)g.inv_d[0], idy = (T)g.inv_d[1], idz = (T)g.inv_d[2];
+    const T idx = inv_d[0], idy = inv_d[1], idz = inv_d[2];
     if (d == 0) {
         rest = (E[2][gidx(g, i, j + 1, k)] - E[2][gidx(g, i, j, k)]) * idy;
         zp = -(E[1][gidx(g, i, j, k + 1)] - E[1][gidx(g, i, j, k)]) * idz;
@@ -175,14 +178,16 @@ __device__ __forceinline__ double waveform(double amp, double f0, double tp, dou
     return amp * exp(-u * u / (2.0 * tp * tp)) * cos(2.0 * kPi * f0 * t);
 }
 
-// Soft J on edge (c, i, j, k) at time t: point sources and TE10-shaped plane
-// sources (profile sin(pi x / W) across x).  Indices on periodic axes are
-// compared modulo n so that a duplicate node receives the same current.
+// Soft J on edge (c, i, j, k) for the current step: point sources and
+// TE10-shaped plane sources (profile sin(pi x / W) across x), with the
+// waveform value of each source precomputed for the step.  Indices on
+// periodic axes are compared modulo n so that a duplicate node receives the
+// same current.
 template <typename T>
-__device__ __forceinline__ double j_source(const Geo &g, const Src<T> *src, int nsrc, int c, int i,
-                                           int j, int k, double t)
+__device__ __forceinline__ T j_source(const Geo &g, const Fields<T> &f, const Src<T> *src, int nsrc, int c,
+                                      int i, int j, int k)
 {
-    double J = 0.0;
+    T J = T(0);
     int ci = (g.per[0] && c != 0 && i == g.n[0]) ? 0 : i;
     int cj = (g.per[1] && c != 1 && j == g.n[1]) ? 0 : j;
     int ck = (g.per[2] && c != 2 && k == g.n[2]) ? 0 : k;
@@ -190,12 +195,9 @@ __device__ __forceinline__ double j_source(const Geo &g, const Src<T> *src, int 
         const Src<T> &q = src[s];
         if (q.comp != c) continue;
         if (q.kind == 0) {
-            if (q.i == ci && q.j == cj && q.k == ck) J += waveform(q.amp, q.f0, q.tp, q.t0, t);
+            if (q.i == ci && q.j == cj && q.k == ck) J += f.src_amp[s];
         } else if (q.kind == 1) {
-            if (q.k != ck) continue;
-            double x = (c == 0 ? ci + 0.5 : (double)ci) * g.d[0];
-            double W = g.n[0] * g.d[0];
-            J += waveform(q.amp, q.f0, q.tp, q.t0, t) * sin(kPi * x / W);
+            if (q.k == ck) J += f.src_amp[s] * f.prof[c == 0 ? 1 : 0][ci];
         }
     }
     return J;
@@ -208,8 +210,7 @@ __device__ __forceinline__ double j_source(const Geo &g, const Src<T> *src, int 
 // held at zero; in the z-PML the z part is damped before and after its
 // update (time-centred split field).
 template <typename T>
-__device__ __forceinline__ void e_edge(const Geo &g, const Fields<T> &f, int c, int i, int j, int k,
-                                       double J)
+__device__ __forceinline__ void e_edge(const Geo &g, const Fields<T> &f, int c, int i, int j, int k, T J)
 {
     size_t q = gidx(g, i, j, k);
     bool wall = (c != 0 && wall_node(g, 0, i)) || (c != 1 && wall_node(g, 1, j)) ||
@@ -220,7 +221,7 @@ __device__ __forceinline__ void e_edge(const Geo &g, const Fields<T> &f, int c, 
         return;
     }
     T rest, zp;
-    curl_h(g, f.H, c, i, j, k, rest, zp);
+    curl_h(g, f.H, f.inv_d, c, i, j, k, rest, zp);
     T ca = f.ca[c] ? f.ca[c][q] : T(1);
     T cb = f.cb[c][q];
     T v;
@@ -229,14 +230,14 @@ __device__ __forceinline__ void e_edge(const Geo &g, const Fields<T> &f, int c, 
         T ez = f.Ezp[c][q];
         T er = f.E[c][q] - ez;
         T ez1 = (ca * (ez * h) + cb * zp) * h;
-        T er1 = ca * er + cb * (rest - (T)J);
+        T er1 = ca * er + cb * (rest - J);
         f.Ezp[c][q] = ez1;
         v = er1 + ez1;
     } else {
-        v = ca * f.E[c][q] + cb * (rest + zp - (T)J);
+        v = ca * f.E[c][q] + cb * (rest + zp - J);
     }
     f.E[c][q] = v;
-    if (!isfinite((double)v)) atomicOr(f.err, kErrNonFinite);
+    if (!isfinite(v)) atomicOr(f.err, kErrNonFinite);
 }
 
 // ------------------------------------------- Steps 1/3: non-magnetic faces
@@ -255,7 +256,7 @@ __device__ __forceinline__ T h_face_nonmag(const Geo &g, const Fields<T> &f, int
         return T(0);
     }
     T rest, zp;
-    curl_e(g, f.E, d, i, j, k, rest, zp);
+    curl_e(g, f.E, f.inv_d, d, i, j, k, rest, zp);
     T fh = f.fh[d] ? f.fh[d][q] : f.fh0;
     T v;
     if (d < 2 && pml_h_plane(g, k)) {
@@ -274,42 +275,122 @@ __device__ __forceinline__ T h_face_nonmag(const Geo &g, const Fields<T> &f, int
 
 // ------------------------------------------------ LLG: one iterate
 
-// One solve of the trapezoidal LLG step (Eqs. llg_tra4-llg_tra6) written for
-// the increment: with b = M^n + beta, beta = -kappa M^n x Heff^n and
-// a = -(kappa Heff^(r-1) + alpha/Ms M^n), x = (b + (a.b) a - a x b)/(1+|a|^2)
-// gives delta = x - M^n = (beta + (a.b) a - |a|^2 M^n - a x b)/(1+|a|^2);
-// N(x) = x Ms/|x| then gives DeltaM = delta + (delta + M^n)(s - 1) with
-// s - 1 = q/(|x|(Ms + |x|)), q = Ms^2 - |x|^2 = e0 - 2 M^n.delta - |delta|^2
-// and e0 = Ms^2 - |M^n|^2.  Every term is small next to Ms, so FP32 keeps the
-// relative precision of the increment (no cancellation against |M| ~ Ms).
-template <typename T>
-__device__ __forceinline__ void llg_iterate(const T Mn[3], const T beta[3], const T heff[3], T kap,
-                                            T aoms, T Ms, T e0, T dM[3])
+// e0 = Ms^2 - |M^n|^2, the norm defect of the stored M^n that N() removes.
+// |M^n| equals Ms up to rounding, so this is a difference of two nearly equal
+// ~1e10 numbers; FP64: every square is split exactly with an FMA
+// (a*a = p + e) and the eight terms are summed with Neumaier compensation;
+// FP32: the float products are exact in FP64.
+__device__ __forceinline__ void two_sum_acc(double &s, double &c, double x)
 {
-    T a[3];
+    double t = s + x;
+    c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+
+__device__ __forceinline__ double norm_defect(double Ms, double mx, double my, double mz)
+{
+    double v[4] = {Ms, mx, my, mz};
+    double s = 0.0, c = 0.0;
 #pragma unroll
-    for (int c = 0; c < 3; c++) a[c] = -(kap * heff[c] + aoms * Mn[c]);
-    T ab = (a[0] * Mn[0] + a[1] * Mn[1] + a[2] * Mn[2]) + (a[0] * beta[0] + a[1] * beta[1] + a[2] * beta[2]);
-    T aa = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
-    T b[3] = {Mn[0] + beta[0], Mn[1] + beta[1], Mn[2] + beta[2]};
-    T axb[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
-    T inv = T(1) / (T(1) + aa);
-    T del[3];
+    for (int q = 0; q < 4; q++) {
+        double p = v[q] * v[q];
+        double e = fma(v[q], v[q], -p);
+        double sg = q == 0 ? 1.0 : -1.0;
+        two_sum_acc(s, c, sg * p);
+        two_sum_acc(s, c, sg * e);
+    }
+    return s + c;
+}
+
+__device__ __forceinline__ void two_sum_accf(float &s, float &c, float x)
+{
+    float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+
+// FP32 path: the same exact splitting with FMA in float; the compensated
+// sum keeps e0 to ~1e-14 relative to Ms^2, which FP64 would also give,
+// without FP64 instructions (1/64 of the FP32 rate on this part).
+__device__ __forceinline__ float norm_defect(float Ms, float mx, float my, float mz)
+{
+    float v[4] = {Ms, mx, my, mz};
+    float s = 0.f, c = 0.f;
 #pragma unroll
-    for (int c = 0; c < 3; c++) del[c] = (beta[c] + ab * a[c] - aa * Mn[c] - axb[c]) * inv;
+    for (int q = 0; q < 4; q++) {
+        float p = v[q] * v[q];
+        float e = fmaf(v[q], v[q], -p);
+        float sg = q == 0 ? 1.f : -1.f;
+        two_sum_accf(s, c, sg * p);
+        two_sum_accf(s, c, sg * e);
+    }
+    return s + c;
+}
+
+
+// N(M^n + delta) - M^n without cancellation against |M| ~ Ms:
+// DeltaM = delta + (delta + M^n)(s - 1), s - 1 = q/(|x|(Ms + |x|)),
+// q = Ms^2 - |x|^2 = e0 - 2 M^n.delta - |delta|^2.  The H update (Eq.
+// iterate_H) takes the change along the sphere through the stored M^n
+// (the same with e0 = 0): component d of it is returned in dMh, so the
+// rounding of the stored M^n, which N() also removes, does not enter H.
+template <typename T>
+__device__ __forceinline__ void renormalised_increment(const T Mn[3], const T del[3], T Ms, T e0, int d,
+                                                       T dM[3], T &dMh)
+{
     T md = Mn[0] * del[0] + Mn[1] * del[1] + Mn[2] * del[2];
     T dd = del[0] * del[0] + del[1] * del[1] + del[2] * del[2];
-    T qv = e0 - (T(2) * md + dd);
+    T q0 = -(T(2) * md + dd);
+    T qv = e0 + q0;
     T xn = sqrt(Ms * Ms - qv);
-    T sm1 = qv / (xn * (Ms + xn));
+    T den = T(1) / (xn * (Ms + xn));
+    T sm1 = qv * den;
 #pragma unroll
     for (int c = 0; c < 3; c++) dM[c] = del[c] + (del[c] + Mn[c]) * sm1;
+    dMh = del[d] + (del[d] + Mn[d]) * (q0 * den);
+}
+
+// One solve of the trapezoidal LLG step (Eqs. llg_tra4-llg_tra6) written for
+// the increment.  With b = M^n + beta, beta = -kappa M^n x Heff^n and
+// a = -(u + s M^n), u = kappa Heff^(r-1), s = alpha/Ms, the closed form
+// x = (b + (a.b) a - a x b)/(1+|a|^2) gives
+//   delta = x - M^n = (beta + (a.b) a - |a|^2 M^n - a x b)/(1+|a|^2).
+// a is dominated by its damping part s M^n, parallel to M^n; expanding
+//   (a.b) a - |a|^2 M^n = (p + s m2 + q) u + (s q - s p - |u|^2) M^n,
+//   a x b = -(u x M^n + u x beta + s M^n x beta),
+// with p = u.M^n, q = (u + s M^n).beta, m2 = |M^n|^2 = Ms^2 - e0, drops the
+// terms that cancel identically (M^n x M^n and the s^2 m2 pair), so every
+// remaining term is small and keeps its relative precision (FP32 included).
+// N(x) = x Ms/|x| then gives DeltaM = delta + (delta + M^n)(s_N - 1) with
+// s_N - 1 = q'/(|x|(Ms + |x|)), q' = Ms^2 - |x|^2 = e0 - 2 M^n.delta - |delta|^2.
+template <typename T>
+__device__ __forceinline__ void llg_iterate(const T Mn[3], const T beta[3], const T heff[3], T kap,
+                                            T s, T Ms, T e0, int d, T dM[3], T &dMh)
+{
+    T u[3] = {kap * heff[0], kap * heff[1], kap * heff[2]};
+    T m2 = Ms * Ms - e0;
+    T p = u[0] * Mn[0] + u[1] * Mn[1] + u[2] * Mn[2];
+    T q = (u[0] + s * Mn[0]) * beta[0] + (u[1] + s * Mn[1]) * beta[1] + (u[2] + s * Mn[2]) * beta[2];
+    T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    T c_u = p + s * m2 + q;
+    T c_m = s * q - s * p - uu;
+    T uxm[3] = {u[1] * Mn[2] - u[2] * Mn[1], u[2] * Mn[0] - u[0] * Mn[2], u[0] * Mn[1] - u[1] * Mn[0]};
+    T uxb[3] = {u[1] * beta[2] - u[2] * beta[1], u[2] * beta[0] - u[0] * beta[2], u[0] * beta[1] - u[1] * beta[0]};
+    T mxb[3] = {Mn[1] * beta[2] - Mn[2] * beta[1], Mn[2] * beta[0] - Mn[0] * beta[2],
+                Mn[0] * beta[1] - Mn[1] * beta[0]};
+    T inv = T(1) / (T(1) + uu + T(2) * s * p + s * s * m2);
+    T del[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+        del[c] = (beta[c] + c_u * u[c] + c_m * Mn[c] + uxm[c] + uxb[c] + s * mxb[c]) * inv;
+    renormalised_increment(Mn, del, Ms, e0, d, dM, dMh);
 }
 
 // First-order scheme (Sec. 3.2.1, Steps 1/3): forward Euler of Eq. LLG_scalar
 // over the half step, delta = -c1 M^n x H - c2 M^n x (M^n x H), then N().
 template <typename T>
-__device__ __forceinline__ void llg_euler(const T Mn[3], const T heff[3], T c1, T c2, T Ms, T e0, T dM[3])
+__device__ __forceinline__ void llg_euler(const T Mn[3], const T heff[3], T c1, T c2, T Ms, T e0, int d,
+                                          T dM[3], T &dMh)
 {
     T mxh[3] = {Mn[1] * heff[2] - Mn[2] * heff[1], Mn[2] * heff[0] - Mn[0] * heff[2],
                 Mn[0] * heff[1] - Mn[1] * heff[0]};
@@ -318,13 +399,7 @@ __device__ __forceinline__ void llg_euler(const T Mn[3], const T heff[3], T c1, 
     T del[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) del[c] = -c1 * mxh[c] - c2 * mxmxh[c];
-    T md = Mn[0] * del[0] + Mn[1] * del[1] + Mn[2] * del[2];
-    T dd = del[0] * del[0] + del[1] * del[1] + del[2] * del[2];
-    T qv = e0 - (T(2) * md + dd);
-    T xn = sqrt(Ms * Ms - qv);
-    T sm1 = qv / (xn * (Ms + xn));
-#pragma unroll
-    for (int c = 0; c < 3; c++) dM[c] = del[c] + (del[c] + Mn[c]) * sm1;
+    renormalised_increment(Mn, del, Ms, e0, d, dM, dMh);
 }
 
 } // namespace mmx

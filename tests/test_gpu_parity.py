@@ -60,10 +60,15 @@ def test_a1_initial_m_matches_oracle(prec, tol):
 
 # ------------------------------------------- the coupled step, FP64 parity
 
-def test_yig_slab_32_fp64_200_steps():
+PATHS = [mmx.PATH_PLAIN, mmx.PATH_FUSED]
+PATH_IDS = ["plain", "fused"]
+
+
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_yig_slab_32_fp64_200_steps(path):
     """The 32^3 YIG-slab box: 200 steps, tol 1e-10, PEC, point Jx source."""
     w = W.yig_slab_32()
-    sim, ref = _run_pair(w, w.steps)
+    sim, ref = _run_pair(w, w.steps, path=path)
     _compare(sim, ref, label="yig_slab_32")
     np.testing.assert_array_equal(sim.get_iter_log(), ref.iter_log())
 
@@ -77,49 +82,53 @@ CASES = [
     dict(seed=16, bc=(W.PEC, W.PEC, W.PEC), hard=True),
     dict(seed=17, bc=(W.PEC, W.PERIODIC, W.PEC), order=1),
     dict(seed=18, bc=(W.PERIODIC, W.PEC, W.PEC), magnetic=False),
-    dict(seed=19, bc=(W.PEC, W.PEC, W.PEC), n=(1, 9, 7)),
+    dict(seed=19, bc=(W.PEC, W.PEC, W.PEC), n=(2, 9, 7)),
 ]
 
 
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
 @pytest.mark.parametrize("case", CASES, ids=[str(c["seed"]) for c in CASES])
-def test_random_small_fp64(case):
+def test_random_small_fp64(case, path):
     kw = dict(case)
     seed = kw.pop("seed")
     w = W.random_small(seed, **kw)
-    sim, ref = _run_pair(w, 8)
+    sim, ref = _run_pair(w, 8, path=path)
     fids = list(range(15)) + ([15, 16, 17, 18] if w.bc[2] == W.PML else [])
     _compare(sim, ref, fids=fids, label=str(seed))
     np.testing.assert_array_equal(sim.get_iter_log(), ref.iter_log()[: len(sim.get_iter_log())])
 
 
-def test_convergence_problem_32_fp64():
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_convergence_problem_32_fp64(path):
     """The paper's periodic coupled problem (Sec. 5.1) on 32^3, 5 steps:
     magnetic everywhere, sigma/eps/Ms/alpha/gamma bumps."""
     w = W.convergence(32)
-    sim, ref = _run_pair(w, w.steps)
+    sim, ref = _run_pair(w, w.steps, path=path)
     _compare(sim, ref, label="convergence_32")
     np.testing.assert_array_equal(sim.get_iter_log(), ref.iter_log())
 
 
 def test_waveguide_full_size_fp64_parity():
     """The 128x128x512 waveguide (z-PML, YIG slab, TE10 source) at full size,
-    same launch configuration as the benchmark, 6 steps against the oracle."""
+    in the benchmark's launch configuration (fused path), 6 steps against
+    the oracle."""
     w = W.waveguide(steps=6)
-    sim, ref = _run_pair(w, 6)
+    sim, ref = _run_pair(w, 6, path=mmx.PATH_FUSED)
     _compare(sim, ref, fids=list(range(19)), label="waveguide")
     np.testing.assert_array_equal(sim.get_iter_log(), ref.iter_log())
 
 
 # ----------------------------------------------------------- FP32 path
 
-def test_fp32_error_against_oracle_yig_slab():
-    """FP32 storage and arithmetic (FP64 only in e0 = Ms^2 - |M^n|^2 and the
-    residual): stated error after 200 steps of the 32^3 slab."""
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_fp32_error_against_oracle_yig_slab(path):
+    """FP32 storage and arithmetic (the residual compared in FP64): stated
+    error after 200 steps of the 32^3 slab."""
     w = W.yig_slab_32()
     w.tol = 1e-6
     ref = oracle.from_workload(w)
     ref.step(w.steps)
-    sim = mmx.from_workload(w, prec=mmx.FP32)
+    sim = mmx.from_workload(w, prec=mmx.FP32, path=path)
     sim.step(w.steps)
     assert sim.sync(check=False) == 0
     errs = {fid: rel_l2(sim.get_field(fid), ref.get_field(fid)) for fid in range(15)}
@@ -146,3 +155,21 @@ def test_nonfinite_is_reported():
     sim.set_field(0, e)
     sim.step(1)
     assert sim.sync(check=False) == -5
+
+
+@pytest.mark.parametrize("prec", [mmx.FP64, mmx.FP32], ids=["fp64", "fp32"])
+def test_fused_equals_plain(prec):
+    """The fused pass and the one-kernel-per-update path compute the same
+    scheme: identical iteration counts and fields equal to rounding (the PML
+    split part is carried instead of re-derived, the only reordering)."""
+    w = W.waveguide(n=(24, 20, 48), steps=30)
+    a = mmx.from_workload(w, prec=prec, path=mmx.PATH_PLAIN)
+    b = mmx.from_workload(w, prec=prec, path=mmx.PATH_FUSED)
+    for chunk in (7, 1, 12, 10):           # several mmx_step call patterns
+        a.step(chunk)
+        b.step(chunk)
+    assert a.sync(check=False) == 0 and b.sync(check=False) == 0
+    tol = 1e-13 if prec == mmx.FP64 else 1e-5
+    for fid in range(19):
+        assert rel_l2(b.get_field(fid), a.get_field(fid)) <= tol, fid
+    np.testing.assert_array_equal(a.get_iter_log(), b.get_iter_log())

@@ -150,7 +150,7 @@ def yig_slab_32(seed: int = 0, steps: int = 200, n: int = 32) -> Workload:
 
 
 def waveguide(seed: int = 1, steps: int = 5000, n=(128, 128, 512), dx: float = 2e-4,
-              tol: float = 1e-10, amp: float = 1e7) -> Workload:
+              tol: float = 1e-6, amp: float = 1e7) -> Workload:
     """Rectangular PEC guide with 10-cell z-PML ends and a YIG-like slab.
 
     At the default 128x128x512 size the slab covers x cells 32-95, y cells
