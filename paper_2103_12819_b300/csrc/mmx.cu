@@ -489,7 +489,7 @@ template <typename T> static int plan_fused(mmx_ctx *ctx)
     int dev = 0, nsm = 0, per = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused<T, kFBX, kFBY>, kFBX * kFBY, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused<T, kFBX, kFBY, 2, true, true>, kFBX * kFBY, 0));
     per = std::max(per, 1);
     const int *n = ctx->desc.n;
     long long tiles = (long long)((n[0] + 1 + kFBX - 2) / (kFBX - 1)) * ((n[1] + 1 + kFBY - 2) / (kFBY - 1));
@@ -509,6 +509,32 @@ template <typename T> static void swap_buffers(mmx_ctx *ctx)
         std::swap(ctx->H[a], ctx->Halt[a]);
     }
     for (int a = 0; a < 2; a++) std::swap(ctx->Ezp[a], ctx->Ezpalt[a]);
+}
+
+template <typename T, int NH, bool PMLK, bool GEN>
+static void launch_fused_v(mmx_ctx *ctx, dim3 G, dim3 B, const Fields<T> &f, Ptr3<T> Eo, Ptr3<T> Ho, Ptr3<T> En,
+                           Ptr3<T> Hn, Ptr3<T> Zo, Ptr3<T> Zn, int nsrc)
+{
+    k_fused<T, kFBX, kFBY, NH, PMLK, GEN><<<G, B, 0, ctx->stream>>>(
+        ctx->g, f, Eo, Ho, En, Hn, Zo, Zn, (const Src<T> *)ctx->dsrc, nsrc, ctx->fused_chunk, ctx->lo[0],
+        ctx->lo[1], ctx->lo[2], ctx->hi[0], ctx->hi[1], ctx->hi[2]);
+}
+
+// Pick the compile-time variant of the fused kernel.
+template <typename T>
+static void launch_fused(mmx_ctx *ctx, dim3 G, dim3 B, const Fields<T> &f, Ptr3<T> Eo, Ptr3<T> Ho, Ptr3<T> En,
+                         Ptr3<T> Hn, Ptr3<T> Zo, Ptr3<T> Zn, int nsrc, int nhalf)
+{
+    const bool pml = ctx->g.npml > 0, gen = ctx->any_sigma || ctx->any_mu;
+#define MMX_FUSED_CASE(NHV, PV, GV)                                                                  \
+    if (nhalf == NHV && pml == PV && gen == GV) {                                                    \
+        launch_fused_v<T, NHV, PV, GV>(ctx, G, B, f, Eo, Ho, En, Hn, Zo, Zn, nsrc);                  \
+        return;                                                                                      \
+    }
+    MMX_FUSED_CASE(2, true, false) MMX_FUSED_CASE(2, false, false) MMX_FUSED_CASE(2, true, true)
+    MMX_FUSED_CASE(2, false, true) MMX_FUSED_CASE(1, true, false) MMX_FUSED_CASE(1, false, false)
+    MMX_FUSED_CASE(1, true, true) MMX_FUSED_CASE(1, false, true)
+#undef MMX_FUSED_CASE
 }
 
 template <typename T> static int step_fused(mmx_ctx *ctx, int nsteps)
@@ -544,9 +570,7 @@ template <typename T> static int step_fused(mmx_ctx *ctx, int nsteps)
         Ptr3<T> Zo = {{(T *)ctx->Ezp[0], (T *)ctx->Ezp[1], nullptr}};
         Ptr3<T> Zn = {{(T *)ctx->Ezpalt[0], (T *)ctx->Ezpalt[1], nullptr}};
         prof_begin(ctx, KK_FUSED);
-        k_fused<T, kFBX, kFBY><<<G, B, 0, ctx->stream>>>(ctx->g, f, Eo, Ho, En, Hn, Zo, Zn, (const Src<T> *)ctx->dsrc,
-                                                        nsrc, nhalf, ctx->fused_chunk, ctx->lo[0], ctx->lo[1],
-                                                        ctx->lo[2], ctx->hi[0], ctx->hi[1], ctx->hi[2]);
+        launch_fused<T>(ctx, G, B, f, Eo, Ho, En, Hn, Zo, Zn, nsrc, nhalf);
         prof_end(ctx);
         CK(cudaGetLastError());
         if (ctx->magnetic) {
@@ -1099,5 +1123,6 @@ int mmx_get_field_device(mmx_ctx *ctx, int id, void **ptr, long long *sx, long l
     *sy = (long long)ctx->g.X * ctx->g.Y;
     return MMX_OK;
 }
+
 
 } // extern "C"

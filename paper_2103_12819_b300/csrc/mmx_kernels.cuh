@@ -590,16 +590,6 @@ __global__ void __launch_bounds__(256) k_hm_box(const __grid_constant__ Geo g,
 
 // ========================================================== fused pass
 
-// Values of one column at one z plane that the fused pass loads ahead.
-template <typename T> struct ColPlane {
-    T hx, hy, hz;          // H^(n+1/2): Hx, Hy of layer k, Hz of plane k
-    T hy_m, hz_m;          // column i-1 (loaded by tx == 0)
-    T hx_jm, hz_jm;        // row j-1 (loaded by ty == 0)
-    T eo[3];               // E^n of Ex, Ey (plane k), Ez (layer k)
-    T cb[3], ca[3];        // E coefficients
-    T zo[2];               // PML z parts of Ex, Ey (old buffer)
-};
-
 // One pass per time step over the whole grid: E^(n+1) on every edge from
 // (E^n, H^(n+1/2)) and, on every face outside the magnetic box, H from
 // H^(n+1/2) by nhalf half steps of -fh curl E^(n+1) (two for H^(n+3/2):
@@ -613,18 +603,25 @@ template <typename T> struct ColPlane {
 // a z chunk [k0, k1).  At plane k it stages H^(n+1/2) of layer/plane k (with
 // a one-cell low-side halo) in shared memory, computes E^(n+1) at plane k
 // for tile + halo, then H at plane k (Hz) and layer k-1 (Hx, Hy) for the
-// tile; the next plane's column values are loaded into registers before the
-// first barrier so their latency overlaps this plane's work.  The chunk's
-// last iteration k = k1 recomputes the next chunk's E plane without writing.
-template <typename T, int BX, int BY>
-__global__ void __launch_bounds__(BX *BY) k_fused(const __grid_constant__ Geo g, const __grid_constant__ Fields<T> f,
+// tile.  The next plane's column values are loaded into registers before
+// the first barrier so their latency overlaps this plane's work; the shared
+// tiles are double-buffered (two barriers per plane).  Everything that does
+// not depend on k (offsets, wall and box flags, sources) is set up once per
+// column, and offsets are 32-bit (a grid of up to 2^31 padded elements).
+// The chunk's last iteration k = k1 recomputes the next chunk's E plane
+// without writing it.
+// Compile-time variants: NH half steps of H (1 or 2), PMLK a z-PML is
+// present, GEN per-edge ca / per-face fh arrays exist (sigma or mu_r varies).
+template <typename T, int BX, int BY, int NH, bool PMLK, bool GEN>
+__global__ void __launch_bounds__(BX *BY, sizeof(T) == 4 ? 4 : 2) k_fused(const __grid_constant__ Geo g, const __grid_constant__ Fields<T> f,
                                                  Ptr3<T> Eo, Ptr3<T> Ho, Ptr3<T> En, Ptr3<T> Hn, Ptr3<T> Zo,
-                                                 Ptr3<T> Zn, const Src<T> *__restrict__ src, int nsrc, int nhalf,
+                                                 Ptr3<T> Zn, const Src<T> *__restrict__ src, int nsrc,
                                                  int chunk, int blo0, int blo1, int blo2, int bhi0, int bhi1,
                                                  int bhi2)
 {
-    __shared__ T sH[3][BY + 1][BX + 1];
-    __shared__ T sE[2][BY][BX];
+    constexpr int nhalf = NH;
+    __shared__ T sH[2][3][BY + 1][BX + 1];
+    __shared__ T sE[2][2][BY][BX];
     __shared__ T sEz[2][BY][BX];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int i = blockIdx.x * (BX - 1) + tx;
@@ -633,215 +630,248 @@ __global__ void __launch_bounds__(BX *BY) k_fused(const __grid_constant__ Geo g,
     const int k0 = blockIdx.z * chunk;
     const int k1 = min(k0 + chunk, nz);
     const bool last_chunk = k1 == nz;
-    const int kend = k1;                     // inclusive
     const bool halo = tx == BX - 1 || ty == BY - 1;
-    const bool col = i <= nx && j <= ny;     // a node column of the grid
+    const bool col = i <= nx && j <= ny;
     const T idx = f.inv_d[0], idy = f.inv_d[1], idz = f.inv_d[2];
-    // wrapped cell-centred indices of this column (-1: outside a wall)
+    const unsigned XY = (unsigned)g.X * (unsigned)g.Y;
+
+    // ---- per-column set-up
     const int ci = cell_nb(g, 0, i), cj = cell_nb(g, 1, j);
     const int cim = cell_nb(g, 0, i - 1), cjm = cell_nb(g, 1, j - 1);
-    const bool has_ex = i < nx, has_ey = j < ny;
+    const unsigned qc = (unsigned)i + (unsigned)g.X * (unsigned)j;          // this column
+    const bool hx_ok = col && cj >= 0, hy_ok = col && ci >= 0, hz_ok = col && ci >= 0 && cj >= 0;
+    const unsigned ohx = (unsigned)i + (unsigned)g.X * (unsigned)max(cj, 0);
+    const unsigned ohy = (unsigned)max(ci, 0) + (unsigned)g.X * (unsigned)j;
+    const unsigned ohz = (unsigned)max(ci, 0) + (unsigned)g.X * (unsigned)max(cj, 0);
+    const bool hym_ok = col && tx == 0 && cim >= 0, hzm_ok = hym_ok && cj >= 0;
+    const unsigned ohym = (unsigned)max(cim, 0) + (unsigned)g.X * (unsigned)j;
+    const unsigned ohzm = (unsigned)max(cim, 0) + (unsigned)g.X * (unsigned)max(cj, 0);
+    const bool hxj_ok = col && ty == 0 && cjm >= 0, hzj_ok = hxj_ok && ci >= 0;
+    const unsigned ohxj = (unsigned)i + (unsigned)g.X * (unsigned)max(cjm, 0);
+    const unsigned ohzj = (unsigned)max(ci, 0) + (unsigned)g.X * (unsigned)max(cjm, 0);
+    const bool wx = wall_node(g, 0, i), wy = wall_node(g, 1, j);
+    const bool ex_on = col && i < nx && !wy;          // Ex edge exists and is not on a y wall
+    const bool ey_on = col && j < ny && !wx;
+    const bool ez_on = col && !wx && !wy;
+    const bool ex_has = col && i < nx, ey_has = col && j < ny;
+    const bool tile = col && !halo;
+    const bool hz_on = tile && i < nx && j < ny && !(i >= blo0 && i < bhi0 && j >= blo1 && j < bhi1);
+    const bool hz_box = tile && i < nx && j < ny && (i >= blo0 && i < bhi0 && j >= blo1 && j < bhi1);
+    const bool hx_on = tile && j < ny, hy_on = tile && i < nx;
+    const bool xy_box = i >= blo0 && i < bhi0 && j >= blo1 && j < bhi1;
+    const bool hx_wall = wx, hy_wall = wy;
+    // z range of the soft sources touching this column (empty: klo > khi)
+    int src_klo = 1 << 30, src_khi = -1;
+    if (col)
+        for (int s = 0; s < nsrc; s++) {
+            const Src<T> &q = src[s];
+            if (q.kind == 1 || (q.kind == 0 && q.i == ((g.per[0] && q.comp != 0 && i == nx) ? 0 : i) &&
+                                q.j == ((g.per[1] && q.comp != 1 && j == ny) ? 0 : j))) {
+                src_klo = min(src_klo, q.k);
+                src_khi = max(src_khi, q.k);
+                if (g.per[2] && q.k == 0) src_khi = max(src_khi, nz);
+            }
+        }
+    const T fh0 = f.fh0;
 
-    auto loadH = [&](int c, int ii, int jj, int kk) -> T {
-        if (ii < 0 || jj < 0 || kk < 0) return T(0);
-        return Ho.p[c][gidx(g, ii, jj, kk)];
-    };
-    auto fetch = [&](int k, ColPlane<T> &v) {
+    // ---- next-plane register set
+    T nhx, nhy, nhz, nhym, nhzm, nhxj, nhzj, neo0, neo1, neo2, ncb0, ncb1, ncb2, nca0, nca1, nca2, nz0, nz1;
+    auto fetch = [&](int k) {
         const int ck = cell_nb(g, 2, k);
-        v.hx = v.hy = v.hz = v.hy_m = v.hz_m = v.hx_jm = v.hz_jm = T(0);
-        v.eo[0] = v.eo[1] = v.eo[2] = T(0);
-        v.cb[0] = v.cb[1] = v.cb[2] = T(0);
-        v.ca[0] = v.ca[1] = v.ca[2] = T(1);
-        v.zo[0] = v.zo[1] = T(0);
-        if (!col || k > kend) return;
-        v.hx = loadH(0, i, cj, ck);
-        v.hy = loadH(1, ci, j, ck);
-        v.hz = loadH(2, ci, cj, k);
-        if (tx == 0) {
-            v.hy_m = loadH(1, cim, j, ck);
-            v.hz_m = loadH(2, cim, cj, k);
+        const bool kin = k <= k1;
+        const unsigned kz = (unsigned)max(ck, 0) * XY, kn = (unsigned)k * XY;
+        const bool ckok = ck >= 0 && kin;
+        nhx = (hx_ok && ckok) ? Ho.p[0][ohx + kz] : T(0);
+        nhy = (hy_ok && ckok) ? Ho.p[1][ohy + kz] : T(0);
+        nhz = (hz_ok && kin) ? Ho.p[2][ohz + kn] : T(0);
+        nhym = (hym_ok && ckok) ? Ho.p[1][ohym + kz] : T(0);
+        nhzm = (hzm_ok && kin) ? Ho.p[2][ohzm + kn] : T(0);
+        nhxj = (hxj_ok && ckok) ? Ho.p[0][ohxj + kz] : T(0);
+        nhzj = (hzj_ok && kin) ? Ho.p[2][ohzj + kn] : T(0);
+        const unsigned q = qc + kn;
+        const bool ok = col && kin;
+        neo0 = (ok && ex_has) ? Eo.p[0][q] : T(0);
+        neo1 = (ok && ey_has) ? Eo.p[1][q] : T(0);
+        neo2 = (ok && k < nz) ? Eo.p[2][q] : T(0);
+        ncb0 = (ok && ex_has) ? f.cb[0][q] : T(0);
+        ncb1 = (ok && ey_has) ? f.cb[1][q] : T(0);
+        ncb2 = (ok && k < nz) ? f.cb[2][q] : T(0);
+        if (GEN) {
+            nca0 = (f.ca[0] && ok && ex_has) ? f.ca[0][q] : T(1);
+            nca1 = (f.ca[1] && ok && ey_has) ? f.ca[1][q] : T(1);
+            nca2 = (f.ca[2] && ok && k < nz) ? f.ca[2][q] : T(1);
+        } else {
+            nca0 = nca1 = nca2 = T(1);
         }
-        if (ty == 0) {
-            v.hx_jm = loadH(0, i, cjm, ck);
-            v.hz_jm = loadH(2, ci, cjm, k);
-        }
-        const size_t q = gidx(g, i, j, k);
-        if (has_ex) { v.eo[0] = Eo.p[0][q]; v.cb[0] = f.cb[0][q]; if (f.ca[0]) v.ca[0] = f.ca[0][q]; }
-        if (has_ey) { v.eo[1] = Eo.p[1][q]; v.cb[1] = f.cb[1][q]; if (f.ca[1]) v.ca[1] = f.ca[1][q]; }
-        if (k < nz) { v.eo[2] = Eo.p[2][q]; v.cb[2] = f.cb[2][q]; if (f.ca[2]) v.ca[2] = f.ca[2][q]; }
-        if (pml_e_plane(g, k)) {
-            if (has_ex) v.zo[0] = Zo.p[0][q];
-            if (has_ey) v.zo[1] = Zo.p[1][q];
+        if (PMLK) {
+            const bool pz = ok && pml_e_plane(g, k);
+            nz0 = (pz && ex_has) ? Zo.p[0][q] : T(0);
+            nz1 = (pz && ey_has) ? Zo.p[1][q] : T(0);
+        } else {
+            nz0 = nz1 = T(0);
         }
     };
 
-    // H of layer k0-1 in this column (for E at plane k0)
     T hx_prev = T(0), hy_prev = T(0), ex_prev = T(0), ey_prev = T(0);
-    if (col) {
-        int ckm = cell_nb(g, 2, k0 - 1);
-        hx_prev = loadH(0, i, cj, ckm);
-        hy_prev = loadH(1, ci, j, ckm);
+    {
+        const int ckm = cell_nb(g, 2, k0 - 1);
+        const unsigned kz = (unsigned)max(ckm, 0) * XY;
+        hx_prev = (hx_ok && ckm >= 0) ? Ho.p[0][ohx + kz] : T(0);
+        hy_prev = (hy_ok && ckm >= 0) ? Ho.p[1][ohy + kz] : T(0);
     }
-    ColPlane<T> cur, nxt;
-    fetch(k0, cur);
-    int zb = 0;
-    for (int k = k0; k <= kend; k++) {
-        // ---- stage H^(n+1/2) of plane k
-        sH[0][ty + 1][tx + 1] = cur.hx;
-        sH[1][ty + 1][tx + 1] = cur.hy;
-        sH[2][ty + 1][tx + 1] = cur.hz;
+    fetch(k0);
+    T acc = T(0);        // sum of everything written: NaN/Inf propagate into it
+    int b = 0;
+    for (int k = k0; k <= k1; k++, b ^= 1) {
+        // ---- stage H^(n+1/2) of plane k; take this plane's registers
+        const T hx = nhx, hy = nhy, hz = nhz;
+        const T eo0 = neo0, eo1 = neo1, eo2 = neo2, cb0 = ncb0, cb1 = ncb1, cb2 = ncb2;
+        const T ca0 = nca0, ca1 = nca1, ca2 = nca2, zo0 = nz0, zo1 = nz1;
+        sH[b][0][ty + 1][tx + 1] = hx;
+        sH[b][1][ty + 1][tx + 1] = hy;
+        sH[b][2][ty + 1][tx + 1] = hz;
         if (tx == 0) {
-            sH[1][ty + 1][0] = cur.hy_m;
-            sH[2][ty + 1][0] = cur.hz_m;
+            sH[b][1][ty + 1][0] = nhym;
+            sH[b][2][ty + 1][0] = nhzm;
         }
         if (ty == 0) {
-            sH[0][0][tx + 1] = cur.hx_jm;
-            sH[2][0][tx + 1] = cur.hz_jm;
+            sH[b][0][0][tx + 1] = nhxj;
+            sH[b][2][0][tx + 1] = nhzj;
         }
-        // ---- issue the next plane's loads (consumed next iteration)
-        fetch(k + 1, nxt);
+        fetch(k + 1);
         __syncthreads();
 
         // ---- E^(n+1) at plane k (Ex, Ey) and layer k (Ez)
         const bool own_plane = k < k1 || last_chunk;
+        const bool wz = wall_node(g, 2, k);
+        const bool pml = PMLK && pml_e_plane(g, k);
+        const unsigned q = qc + (unsigned)k * XY;
+        T J0 = T(0), J1 = T(0), J2 = T(0);
+        if (k >= src_klo && k <= src_khi) {
+            J0 = j_source(g, f, src, nsrc, 0, i, j, k);
+            J1 = j_source(g, f, src, nsrc, 1, i, j, k);
+            J2 = j_source(g, f, src, nsrc, 2, i, j, k);
+        }
         T ex = T(0), ey = T(0), ez = T(0);
-        if (col) {
-            const size_t q = gidx(g, i, j, k);
-            const bool wx = wall_node(g, 0, i), wy = wall_node(g, 1, j), wz = wall_node(g, 2, k);
-            const bool pml = pml_e_plane(g, k);
-            if (has_ex && !wy && !wz) {
-                T rest = (sH[2][ty + 1][tx + 1] - sH[2][ty][tx + 1]) * idy;
-                T zp = -(sH[1][ty + 1][tx + 1] - hy_prev) * idz;
-                T J = nsrc ? j_source(g, f, src, nsrc, 0, i, j, k) : T(0);
-                if (pml) {
-                    T h = f.dampE[k];
-                    T ez1 = (cur.ca[0] * (cur.zo[0] * h) + cur.cb[0] * zp) * h;
-                    ex = cur.ca[0] * (cur.eo[0] - cur.zo[0]) + cur.cb[0] * (rest - J) + ez1;
-                    if (!halo && own_plane) Zn.p[0][q] = ez1;
-                } else {
-                    ex = cur.ca[0] * cur.eo[0] + cur.cb[0] * (rest + zp - J);
-                }
-            } else if (pml && has_ex && !halo && own_plane) {
-                Zn.p[0][q] = T(0);
-            }
-            if (has_ey && !wx && !wz) {
-                T zp = (sH[0][ty + 1][tx + 1] - hx_prev) * idz;
-                T rest = -(sH[2][ty + 1][tx + 1] - sH[2][ty + 1][tx]) * idx;
-                T J = nsrc ? j_source(g, f, src, nsrc, 1, i, j, k) : T(0);
-                if (pml) {
-                    T h = f.dampE[k];
-                    T ez1 = (cur.ca[1] * (cur.zo[1] * h) + cur.cb[1] * zp) * h;
-                    ey = cur.ca[1] * (cur.eo[1] - cur.zo[1]) + cur.cb[1] * (rest - J) + ez1;
-                    if (!halo && own_plane) Zn.p[1][q] = ez1;
-                } else {
-                    ey = cur.ca[1] * cur.eo[1] + cur.cb[1] * (rest + zp - J);
-                }
-            } else if (pml && has_ey && !halo && own_plane) {
-                Zn.p[1][q] = T(0);
-            }
-            if (k < nz && !wx && !wy) {
-                T rest = (sH[1][ty + 1][tx + 1] - sH[1][ty + 1][tx]) * idx
-                       - (sH[0][ty + 1][tx + 1] - sH[0][ty][tx + 1]) * idy;
-                T J = nsrc ? j_source(g, f, src, nsrc, 2, i, j, k) : T(0);
-                ez = cur.ca[2] * cur.eo[2] + cur.cb[2] * (rest - J);
-            }
-            if (!halo && own_plane) {
-                if (has_ex) En.p[0][q] = ex;
-                if (has_ey) En.p[1][q] = ey;
-                if (k < nz) En.p[2][q] = ez;
-                if (!(isfinite(ex) && isfinite(ey) && isfinite(ez))) atomicOr(f.err, kErrNonFinite);
+        T zn0 = T(0), zn1 = T(0);
+        if (ex_on && !wz) {
+            const T rest = (hz - sH[b][2][ty][tx + 1]) * idy;
+            const T zp = -(hy - hy_prev) * idz;
+            if (pml) {
+                const T h = f.dampE[k];
+                zn0 = (ca0 * (zo0 * h) + cb0 * zp) * h;
+                ex = ca0 * (eo0 - zo0) + cb0 * (rest - J0) + zn0;
+            } else {
+                ex = ca0 * eo0 + cb0 * (rest + zp - J0);
             }
         }
-        sE[0][ty][tx] = ex;
-        sE[1][ty][tx] = ey;
-        sEz[zb][ty][tx] = ez;
+        if (ey_on && !wz) {
+            const T zp = (hx - hx_prev) * idz;
+            const T rest = -(hz - sH[b][2][ty + 1][tx]) * idx;
+            if (pml) {
+                const T h = f.dampE[k];
+                zn1 = (ca1 * (zo1 * h) + cb1 * zp) * h;
+                ey = ca1 * (eo1 - zo1) + cb1 * (rest - J1) + zn1;
+            } else {
+                ey = ca1 * eo1 + cb1 * (rest + zp - J1);
+            }
+        }
+        if (ez_on && k < nz) {
+            const T rest = (hy - sH[b][1][ty + 1][tx]) * idx - (hx - sH[b][0][ty][tx + 1]) * idy;
+            ez = ca2 * eo2 + cb2 * (rest - J2);
+        }
+        if (tile && own_plane) {
+            if (ex_has) En.p[0][q] = ex;
+            if (ey_has) En.p[1][q] = ey;
+            if (k < nz) En.p[2][q] = ez;
+            if (pml) {
+                if (ex_has) Zn.p[0][q] = zn0;
+                if (ey_has) Zn.p[1][q] = zn1;
+            }
+            acc += ex + ey + ez;
+        }
+        sE[b][0][ty][tx] = ex;
+        sE[b][1][ty][tx] = ey;
+        sEz[b][ty][tx] = ez;
         __syncthreads();
 
         // ---- H for the tile: Hz at plane k, Hx and Hy at layer k-1
-        if (col && !halo) {
-            if (own_plane && has_ex && has_ey) {
-                const bool inbox = i >= blo0 && i < bhi0 && j >= blo1 && j < bhi1 && k >= blo2 && k < bhi2;
-                if (!inbox) {
-                    const size_t q = gidx(g, i, j, k);
-                    T v = T(0);
-                    if (!wall_node(g, 2, k)) {
-                        T cz = (sE[1][ty][tx + 1] - sE[1][ty][tx]) * idx - (sE[0][ty + 1][tx] - sE[0][ty][tx]) * idy;
-                        T fh = f.fh[2] ? f.fh[2][q] : f.fh0;
-                        v = sH[2][ty + 1][tx + 1] - fh * cz;
-                        if (nhalf == 2) v = v - fh * cz;
-                    }
-                    Hn.p[2][q] = v;
-                    if (!isfinite(v)) atomicOr(f.err, kErrNonFinite);
-                }
+        if (own_plane && (hz_on || (hz_box && !(k >= blo2 && k < bhi2)))) {
+            T v = T(0);
+            if (!wz) {
+                const T cz = (sE[b][1][ty][tx + 1] - ey) * idx - (sE[b][0][ty + 1][tx] - ex) * idy;
+                const T fh = (GEN && f.fh[2]) ? f.fh[2][q] : fh0;
+                v = hz - fh * cz;
+                if (nhalf == 2) v = v - fh * cz;
             }
-            if (k > k0) {
-                const int kl = k - 1;
-                const size_t q = gidx(g, i, j, kl);
-                const bool inbox = i >= blo0 && i < bhi0 && j >= blo1 && j < bhi1 && kl >= blo2 && kl < bhi2;
-                const bool pml = pml_h_plane(g, kl);
-                if (has_ey && !inbox) {      // Hx (i, j+1/2, k-1/2)
-                    T v = T(0);
-                    if (!wall_node(g, 0, i)) {
-                        T rest = (sEz[zb ^ 1][ty + 1][tx] - sEz[zb ^ 1][ty][tx]) * idy;
-                        T zp = -(sE[1][ty][tx] - ey_prev) * idz;
-                        T fh = f.fh[0] ? f.fh[0][q] : f.fh0;
-                        if (pml) {
-                            T h = f.dampH[kl];
-                            T hzp = f.Hzp[0][q];
-                            T hr = hx_prev - hzp;
-                            for (int s = 0; s < nhalf; s++) {
-                                hzp = (hzp * h - fh * zp) * h;
-                                hr = hr - fh * rest;
-                            }
-                            f.Hzp[0][q] = hzp;
-                            v = hr + hzp;
-                        } else {
-                            v = hx_prev - fh * (rest + zp);
-                            if (nhalf == 2) v = v - fh * (rest + zp);
+            Hn.p[2][q] = v;
+            acc += v;
+        }
+        if (k > k0) {
+            const int kl = k - 1;
+            const unsigned ql = q - XY;
+            const bool inbox = xy_box && kl >= blo2 && kl < bhi2;
+            const bool hp = PMLK && pml_h_plane(g, kl);
+            const int pb = b ^ 1;
+            if (hx_on && !inbox) {      // Hx (i, j+1/2, k-1/2)
+                T v = T(0);
+                if (!hx_wall) {
+                    const T rest = (sEz[pb][ty + 1][tx] - sEz[pb][ty][tx]) * idy;
+                    const T zp = -(ey - ey_prev) * idz;
+                    const T fh = (GEN && f.fh[0]) ? f.fh[0][ql] : fh0;
+                    if (hp) {
+                        const T h = f.dampH[kl];
+                        T hzp = f.Hzp[0][ql];
+                        T hr = hx_prev - hzp;
+                        for (int s = 0; s < nhalf; s++) {
+                            hzp = (hzp * h - fh * zp) * h;
+                            hr = hr - fh * rest;
                         }
-                    } else if (pml) {
-                        f.Hzp[0][q] = T(0);
+                        f.Hzp[0][ql] = hzp;
+                        v = hr + hzp;
+                    } else {
+                        v = hx_prev - fh * (rest + zp);
+                        if (nhalf == 2) v = v - fh * (rest + zp);
                     }
-                    Hn.p[0][q] = v;
-                    if (!isfinite(v)) atomicOr(f.err, kErrNonFinite);
+                } else if (hp) {
+                    f.Hzp[0][ql] = T(0);
                 }
-                if (has_ex && !inbox) {      // Hy (i+1/2, j, k-1/2)
-                    T v = T(0);
-                    if (!wall_node(g, 1, j)) {
-                        T zp = (sE[0][ty][tx] - ex_prev) * idz;
-                        T rest = -(sEz[zb ^ 1][ty][tx + 1] - sEz[zb ^ 1][ty][tx]) * idx;
-                        T fh = f.fh[1] ? f.fh[1][q] : f.fh0;
-                        if (pml) {
-                            T h = f.dampH[kl];
-                            T hzp = f.Hzp[1][q];
-                            T hr = hy_prev - hzp;
-                            for (int s = 0; s < nhalf; s++) {
-                                hzp = (hzp * h - fh * zp) * h;
-                                hr = hr - fh * rest;
-                            }
-                            f.Hzp[1][q] = hzp;
-                            v = hr + hzp;
-                        } else {
-                            v = hy_prev - fh * (rest + zp);
-                            if (nhalf == 2) v = v - fh * (rest + zp);
+                Hn.p[0][ql] = v;
+                acc += v;
+            }
+            if (hy_on && !inbox) {      // Hy (i+1/2, j, k-1/2)
+                T v = T(0);
+                if (!hy_wall) {
+                    const T zp = (ex - ex_prev) * idz;
+                    const T rest = -(sEz[pb][ty][tx + 1] - sEz[pb][ty][tx]) * idx;
+                    const T fh = (GEN && f.fh[1]) ? f.fh[1][ql] : fh0;
+                    if (hp) {
+                        const T h = f.dampH[kl];
+                        T hzp = f.Hzp[1][ql];
+                        T hr = hy_prev - hzp;
+                        for (int s = 0; s < nhalf; s++) {
+                            hzp = (hzp * h - fh * zp) * h;
+                            hr = hr - fh * rest;
                         }
-                    } else if (pml) {
-                        f.Hzp[1][q] = T(0);
+                        f.Hzp[1][ql] = hzp;
+                        v = hr + hzp;
+                    } else {
+                        v = hy_prev - fh * (rest + zp);
+                        if (nhalf == 2) v = v - fh * (rest + zp);
                     }
-                    Hn.p[1][q] = v;
-                    if (!isfinite(v)) atomicOr(f.err, kErrNonFinite);
+                } else if (hp) {
+                    f.Hzp[1][ql] = T(0);
                 }
+                Hn.p[1][ql] = v;
+                acc += v;
             }
         }
-        // ---- roll the column registers and the Ez buffers
-        hx_prev = cur.hx;
-        hy_prev = cur.hy;
+        hx_prev = hx;
+        hy_prev = hy;
         ex_prev = ex;
         ey_prev = ey;
-        zb ^= 1;
-        cur = nxt;
-        __syncthreads();
     }
+    if (!isfinite(acc)) atomicOr(f.err, kErrNonFinite);
 }
 
 } // namespace mmx
