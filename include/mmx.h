@@ -205,6 +205,28 @@ typedef struct {
 MMX_API int mmx_set_profiling(mmx_ctx *ctx, int enable);
 MMX_API int mmx_get_profile(mmx_ctx *ctx, mmx_kernel_profile *out, int cap, int reset);
 
+/* Edge or face mean of a cell-centred array with no memory allocation, for
+ * callers that cannot call cudaMalloc: code whose device memory is all owned
+ * by its own arena or pool, or that runs where an allocation (which may
+ * synchronise the device) is not acceptable.  The paper has no counterpart;
+ * the computation is the one mmx_get_material reads back (Sec. 3.1 means).
+ *   desc       only n[3] and bc[3] are used.
+ *   location   0-2: mean over the edges of Ex, Ey, Ez (up to 4 cells);
+ *              3-5: mean over the x, y, z faces (2 cells).
+ *   cell       device array, nx*ny*nz doubles, x fastest (read).
+ *   out        device array of n doubles, the edge/face extent (written).
+ *   cuda_stream  cudaStream_t of the two kernel launches (NULL = default).
+ * The padded intermediate lives in a fixed 8 MiB device array inside the
+ * library (1,048,576 doubles; every GPU that loads the library holds it until
+ * exit): grids with (round_up(nx+1, 8))(ny+1)(nz+1) > 1,048,576 return
+ * MMX_ERR_INVALID, as do bad arguments; MMX_ERR_CUDA reports a failed launch.
+ * The first call on a device looks up that array's device address, so make it
+ * before any stream capture.  All calls share the array: calls whose kernels
+ * overlap on the GPU (other streams, other threads) race.  Asynchronous: the
+ * result is ready when the stream has finished. */
+MMX_API int mmx_material_average_noalloc(const mmx_grid_desc *desc, int location, const double *cell,
+                                         double *out, long long n, void *cuda_stream);
+
 /* Message of the last error on this context (never NULL). */
 MMX_API const char *mmx_last_error(const mmx_ctx *ctx);
 

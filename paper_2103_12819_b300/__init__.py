@@ -50,7 +50,8 @@ class KernelProfile(ctypes.Structure):
 EXPORTS = ("mmx_create", "mmx_set_materials", "mmx_set_bias", "mmx_set_M_cells", "mmx_set_field",
            "mmx_get_field", "mmx_get_material", "mmx_add_source", "mmx_set_path", "mmx_step",
            "mmx_sync", "mmx_get_stats", "mmx_get_iter_log", "mmx_get_field_device",
-           "mmx_set_profiling", "mmx_get_profile", "mmx_last_error", "mmx_destroy")
+           "mmx_set_profiling", "mmx_get_profile", "mmx_material_average_noalloc", "mmx_last_error",
+           "mmx_destroy")
 
 _lib = None
 
@@ -97,6 +98,8 @@ def lib():
     L.mmx_set_profiling.argtypes = [P, I]
     L.mmx_get_profile.restype = I
     L.mmx_get_profile.argtypes = [P, ctypes.POINTER(KernelProfile), I, I]
+    L.mmx_material_average_noalloc.restype = I
+    L.mmx_material_average_noalloc.argtypes = [ctypes.POINTER(GridDesc), I, P, P, LL, P]
     L.mmx_last_error.restype = ctypes.c_char_p
     L.mmx_last_error.argtypes = [P]
     L.mmx_destroy.restype = None
@@ -261,6 +264,18 @@ class Solver:
 
     def last_error(self):
         return self._L.mmx_last_error(self._h).decode()
+
+
+def material_average_noalloc(n, bc, location, cell_ptr, out_ptr, count, stream=None) -> int:
+    """Call ``mmx_material_average_noalloc`` on device pointers (ints);
+    returns the status code (0 = OK)."""
+    desc = GridDesc()
+    for a in range(3):
+        desc.n[a] = int(n[a])
+        desc.bc[a] = int(bc[a])
+    return lib().mmx_material_average_noalloc(ctypes.byref(desc), int(location), ctypes.c_void_p(cell_ptr),
+                                              ctypes.c_void_p(out_ptr), int(count),
+                                              ctypes.c_void_p(stream or 0))
 
 
 def from_workload(w, prec=FP64, stream=None, with_sources=True, path=PATH_FUSED) -> Solver:

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1126,3 +1127,72 @@ int mmx_get_field_device(mmx_ctx *ctx, int id, void **ptr, long long *sx, long l
 
 
 } // extern "C"
+
+// ====================================================== no-allocation entry
+
+// Scratch of mmx_material_average_noalloc: the padded intermediate of the
+// edge/face mean lives in this file-scope device array, so that the entry
+// point allocates nothing.  Every GPU that loads the library holds it until
+// the process exits.  In host code the name is only a stand-in: its device
+// address is looked up once per device with cudaGetSymbolAddress.
+constexpr size_t kNoAllocMaxElems = (size_t)1 << 20;   // 1,048,576 doubles = 8 MiB
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxElems];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_dev_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (set up on the
+// first call for that device).
+int noalloc_scratch(double **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MMX_ERR_CUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return MMX_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_dev_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MMX_ERR_CUDA;
+        g_noalloc_dev_ptr[dev] = (double *)p;
+    }
+    *out = g_noalloc_dev_ptr[dev];
+    return MMX_OK;
+}
+} // namespace
+
+extern "C" int mmx_material_average_noalloc(const mmx_grid_desc *desc, int location, const double *cell,
+                                            double *out, long long n, void *cuda_stream)
+{
+    if (!desc || !cell || !out || location < 0 || location > 5) return MMX_ERR_INVALID;
+    Geo g;
+    memset(&g, 0, sizeof g);
+    for (int a = 0; a < 3; a++) {
+        if (desc->n[a] < 1 || desc->bc[a] < 0 || desc->bc[a] > 2) return MMX_ERR_INVALID;
+        g.n[a] = desc->n[a];
+        g.per[a] = desc->bc[a] == MMX_BC_PERIODIC;
+    }
+    long long X = ((long long)desc->n[0] + 1 + 7) / 8 * 8;
+    long long padded = X * (desc->n[1] + 1LL) * (desc->n[2] + 1LL);
+    if (padded > (long long)kNoAllocMaxElems) return MMX_ERR_INVALID;   // grid too large for the scratch
+    g.X = (int)X;
+    g.Y = desc->n[1] + 1;
+    const int c = location % 3, kind = location < 3 ? 0 : 1;
+    int e[3];
+    for (int a = 0; a < 3; a++) e[a] = desc->n[a] + (kind == 0 ? (a == c ? 0 : 1) : (a == c ? 1 : 0));
+    if (n != (long long)e[0] * e[1] * e[2]) return MMX_ERR_INVALID;
+    double *scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    dim3 B(32, 8, 1), G((desc->n[0] + 1 + 31) / 32, (desc->n[1] + 1 + 7) / 8, desc->n[2] + 1);
+    // every scratch element the gather reads is written by k_mean first, so
+    // nothing has to be cleared between calls
+    k_mean<<<G, B, 0, st>>>(g, cell, kind, c, scratch);
+    if (cudaGetLastError() != cudaSuccess) return MMX_ERR_CUDA;
+    Box<double> nobox;
+    memset(&nobox, 0, sizeof nobox);
+    k_copy_field<double><<<(int)((n + 255) / 256), 256, 0, st>>>(g, scratch, nobox, 0, e[0], e[1], e[2], out, 0);
+    if (cudaGetLastError() != cudaSuccess) return MMX_ERR_CUDA;
+    return MMX_OK;
+}
