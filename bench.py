@@ -132,6 +132,27 @@ def alg_bytes_per_cell(kernel, w, esz):
     return None
 
 
+def replica_layout(env=None):
+    """(world, rank, local_rank) from the torchrun environment; 1 GPU if unset."""
+    env = os.environ if env is None else env
+    return (int(env.get("WORLD_SIZE", "1")), int(env.get("RANK", "0")), int(env.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(torch, ms, dist, device):
+    """The slowest rank's time: every replica must finish before the job has."""
+    if dist is None:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(cells_per_rank, world, K, ms):
+    """Cell-updates per second of the whole job: all ranks' cells x K steps
+    over the slowest rank's time (weak scaling, one replica per GPU)."""
+    return cells_per_rank * world * K / (ms * 1e-3)
+
+
 def time_steps(torch, sim, stream, K, dist=None):
     if dist is not None:
         dist.barrier()
@@ -142,12 +163,9 @@ def time_steps(torch, sim, stream, K, dist=None):
     sim.step(K)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
     if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    return ms
+        dist.barrier()
+    return max_over_ranks(torch, e0.elapsed_time(e1), dist, "cuda")
 
 
 def run_path(torch, mmx, w, prec, path, K, W, stream, dist=None, profile=True):
@@ -210,7 +228,7 @@ def e2e_leg(torch, mmx, w, prec, path, K, stream):
         sim.set_field(fid, host[fid].numpy())
     sim.step(K)
     for fid in fids:
-        out[fid].numpy()[:] = sim.get_field(fid)
+        sim.get_field(fid, out=out[fid].numpy())
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     nbytes = sum(8 * sim.field_size(f) for f in fids)
@@ -242,7 +260,7 @@ def cpu_baseline(w, budget_s=15.0):
 
 def reference_arm(args):
     import workloads
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = replica_layout()
     if rank != 0:
         return 0
     w = workloads.waveguide()
@@ -263,9 +281,7 @@ def ours_arm(args):
     import torch
     import paper_2103_12819_b300 as mmx
     import workloads
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = replica_layout()
     dist = None
     if world > 1:
         import torch.distributed as dist_mod
@@ -298,8 +314,7 @@ def ours_arm(args):
         sim32.close()
         sim64.close()
         e2e = e2e_leg(torch, mmx, w, mmx.FP32, path, K, stream)
-    cells_total = w.ncells * world
-    value = cells_total * K / (ms32 * 1e-3)
+    value = whole_job_rate(w.ncells, world, K, ms32)
     mag_frac = float(np.count_nonzero(w.Ms > 0)) / w.ncells
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -313,9 +328,9 @@ def ours_arm(args):
         "clocks": clocks,
         "gpu_launches": int(round(lps * K)) if lps else None,
         "e2e": e2e,
-        "fp64": {"value": cells_total * K / (ms64 * 1e-3), "ms_per_step": ms64 / K, "roofline": roof64,
+        "fp64": {"value": whole_job_rate(w.ncells, world, K, ms64), "ms_per_step": ms64 / K, "roofline": roof64,
                  "iters_min": stats64["iters_min"], "iters_max": stats64["iters_max"]},
-        "plain_fp64": {"value": cells_total * K / (msp * 1e-3), "ms_per_step": msp / K},
+        "plain_fp64": {"value": whole_job_rate(w.ncells, world, K, msp), "ms_per_step": msp / K},
         "fp32_vs_fp64_rel_l2_after_steps": {"steps": W + 2 * K, "max": max(errs.values()),
                                             "per_field": {str(k): float("%.3e" % v) for k, v in errs.items()}},
         "iters": {"min": stats32["iters_min"], "max": stats32["iters_max"]},

@@ -124,7 +124,10 @@ MMX_API int mmx_create(const mmx_grid_desc *desc, void *cuda_stream, mmx_ctx **o
  * doubles or NULL for the default (eps_r 1, sigma 0, mu_r 1, Ms 0, alpha 0,
  * |gamma| 0).  A face is magnetic iff its averaged Ms > 0; magnetic faces
  * restart at M = Ms zhat.  Ms must be 0 in the PML slabs (the paper's PML is
- * non-magnetic).  Synchronises the context stream. */
+ * non-magnetic); every cell's Ms is 0 or in [1e-20, 1e20] A/m, eps_r and mu_r
+ * > 0, sigma, alpha and |gamma| >= 0, else MMX_ERR_INVALID.  The magnetic box
+ * must hold fewer than 2^30 faces per family.  Synchronises the context
+ * stream. */
 MMX_API int mmx_set_materials(mmx_ctx *ctx, const double *eps_r, const double *sigma,
                       const double *mu_r, const double *Ms, const double *alpha,
                       const double *gamma_abs);

@@ -204,8 +204,14 @@ class Solver:
         a = _c64(values)
         self._check(self._L.mmx_set_field(self._h, int(fid), _dp(a), a.size), "mmx_set_field")
 
-    def get_field(self, fid, check=True):
-        out = np.empty(self.field_size(fid), dtype=np.float64)
+    def get_field(self, fid, check=True, out=None):
+        """Field `fid` as float64 values in the order of its extent (x fastest);
+        `out`, if given, is a C-contiguous float64 array of that size (pinned
+        host memory makes the device->host copy direct)."""
+        if out is None:
+            out = np.empty(self.field_size(fid), dtype=np.float64)
+        elif out.dtype != np.float64 or not out.flags.c_contiguous or out.size != self.field_size(fid):
+            raise ValueError("out must be a C-contiguous float64 array of %d values" % self.field_size(fid))
         rc = self._L.mmx_get_field(self._h, int(fid), _dp(out), out.size)
         if check:
             self._check(rc, "mmx_get_field")

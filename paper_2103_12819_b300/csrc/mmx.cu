@@ -61,6 +61,8 @@ struct mmx_ctx {
     std::vector<void *> box_allocs;
     void *bM[9] = {}, *bbeta[9] = {}, *bdM[2][9] = {}, *bCp[3] = {}, *be0[3] = {}, *bHit[2][3] = {};
     void *bms[3] = {}, *bk1[3] = {}, *bk2[3] = {};
+    int4 *dmag = nullptr, *dnon = nullptr;
+    int nmag = 0, nnon = 0;
     int coop_blocks = 0;
 
     // control words (device)
@@ -257,6 +259,10 @@ template <typename T> static Box<T> make_box(mmx_ctx *c)
     b.halfsteps = c->halfsteps;
     b.last_res = c->last_res;
     b.err = c->errw;
+    b.mag = c->dmag;
+    b.nonmag = c->dnon;
+    b.nmag = c->nmag;
+    b.nnon = c->nnon;
     return b;
 }
 
@@ -343,6 +349,59 @@ static void free_box(mmx_ctx *c)
     c->box_allocs.clear();
     c->magnetic = false;
     c->nb = 0;
+    c->dmag = c->dnon = nullptr;
+    c->nmag = c->nnon = 0;
+}
+
+// Work lists of the box kernel: every valid face of the box, split into
+// magnetic faces (an adjacent cell has Ms > 0, i.e. Ms_face > 0) and the rest;
+// entries {box index | family << 30, i, j, k}.
+static int build_box_lists(mmx_ctx *ctx, const double *Ms)
+{
+    const int *n = ctx->desc.n;
+    std::vector<int4> mag, non;
+    auto cell_ms = [&](int i, int j, int k) {
+        return Ms[(size_t)i + (size_t)n[0] * ((size_t)j + (size_t)n[1] * k)];
+    };
+    for (int d = 0; d < 3; d++)
+        for (int k = ctx->lo[2]; k < ctx->hi[2]; k++)
+            for (int j = ctx->lo[1]; j < ctx->hi[1]; j++)
+                for (int i = ctx->lo[0]; i < ctx->hi[0]; i++) {
+                    int ix[3] = {i, j, k};
+                    bool valid = true;
+                    for (int a = 0; a < 3; a++)
+                        if (ix[a] > n[a] || (a != d && ix[a] >= n[a])) valid = false;
+                    if (!valid) continue;
+                    bool magnetic = false;
+                    for (int o = -1; o <= 0; o++) {
+                        int cc[3] = {i, j, k};
+                        int v = ix[d] + o;
+                        if (v < 0 || v >= n[d]) {
+                            if (!ctx->g.per[d]) continue;
+                            v = (v + n[d]) % n[d];
+                        }
+                        cc[d] = v;
+                        if (cell_ms(cc[0], cc[1], cc[2]) > 0) magnetic = true;
+                    }
+                    unsigned l = (unsigned)(i - ctx->lo[0]) +
+                                 (unsigned)ctx->bx * ((unsigned)(j - ctx->lo[1]) + (unsigned)ctx->by * (unsigned)(k - ctx->lo[2]));
+                    int4 e = make_int4((int)(l | ((unsigned)d << 30)), i, j, k);
+                    (magnetic ? mag : non).push_back(e);
+                }
+    ctx->nmag = (int)mag.size();
+    ctx->nnon = (int)non.size();
+    void *pm = nullptr, *pn = nullptr;
+    int rc = dalloc(ctx, &pm, std::max<size_t>(1, mag.size()) * sizeof(int4));
+    if (rc) return rc;
+    ctx->box_allocs.push_back(pm);
+    rc = dalloc(ctx, &pn, std::max<size_t>(1, non.size()) * sizeof(int4));
+    if (rc) return rc;
+    ctx->box_allocs.push_back(pn);
+    if (!mag.empty()) CK(cudaMemcpy(pm, mag.data(), mag.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    if (!non.empty()) CK(cudaMemcpy(pn, non.data(), non.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    ctx->dmag = (int4 *)pm;
+    ctx->dnon = (int4 *)pn;
+    return MMX_OK;
 }
 
 static int box_alloc(mmx_ctx *ctx, void **p)
@@ -359,7 +418,7 @@ template <typename T> static int compute_coop(mmx_ctx *ctx)
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hm_box<T>, 256, 0));
     if (per < 1) return fail(ctx, MMX_ERR_CUDA, "H/M kernel cannot be resident");
-    long long need = (3 * ctx->nb + 255) / 256;
+    long long need = (std::max(ctx->nmag, ctx->nnon) + 255) / 256;
     long long cap = (long long)per * nsm;
     ctx->coop_blocks = (int)std::max(1LL, std::min(need, cap));
     return MMX_OK;
@@ -795,7 +854,8 @@ int mmx_set_materials(mmx_ctx *ctx, const double *eps_r, const double *sigma, co
         if (eps_r && !(eps_r[q] > 0)) return fail(ctx, MMX_ERR_INVALID, "eps_r must be > 0");
         if (mu_r && !(mu_r[q] > 0)) return fail(ctx, MMX_ERR_INVALID, "mu_r must be > 0");
         if (sigma && !(sigma[q] >= 0)) return fail(ctx, MMX_ERR_INVALID, "sigma must be >= 0");
-        if (Ms && !(Ms[q] >= 0)) return fail(ctx, MMX_ERR_INVALID, "Ms must be >= 0");
+        if (Ms && !(Ms[q] == 0 || (Ms[q] >= 1e-20 && Ms[q] <= 1e20)))
+            return fail(ctx, MMX_ERR_INVALID, "Ms must be 0 or in [1e-20, 1e20] A/m");
         if (alpha && !(alpha[q] >= 0)) return fail(ctx, MMX_ERR_INVALID, "alpha must be >= 0");
         if (gamma_abs && !(gamma_abs[q] >= 0)) return fail(ctx, MMX_ERR_INVALID, "gamma must be >= 0");
     }
@@ -871,6 +931,9 @@ int mmx_set_materials(mmx_ctx *ctx, const double *eps_r, const double *sigma, co
             if (!rc) rc = box_alloc(ctx, &ctx->bk1[a]);
             if (!rc) rc = box_alloc(ctx, &ctx->bk2[a]);
         }
+        if (!rc && (ctx->nb >= (1LL << 30) || (long long)ctx->g.X * ctx->g.Y * (ctx->desc.n[2] + 1LL) >= (1LL << 32)))
+            rc = fail(ctx, MMX_ERR_INVALID, "magnetic box or grid too large for 32-bit box indexing");
+        if (!rc) rc = build_box_lists(ctx, Ms);
         if (rc) {
             free_box(ctx);
             return rc;

@@ -116,11 +116,27 @@ template <typename T> struct Box {
     unsigned long long *halfsteps;
     double *last_res;
     int *err;
+    // work lists: {box index | family << 30, i, j, k} of the magnetic faces
+    // and of the other (non-magnetic) faces of the box
+    const int4 *mag;
+    const int4 *nonmag;
+    int nmag, nnon;
 };
 
 __device__ __forceinline__ size_t bidx(const int lo[3], int bx, int by, int i, int j, int k)
 {
     return (size_t)(i - lo[0]) + (size_t)bx * ((size_t)(j - lo[1]) + (size_t)by * (size_t)(k - lo[2]));
+}
+
+// 32-bit forms for the box kernel (box and grid below 2^32 elements)
+__device__ __forceinline__ unsigned bidx32(const int lo[3], int bx, int by, int i, int j, int k)
+{
+    return (unsigned)(i - lo[0]) + (unsigned)bx * ((unsigned)(j - lo[1]) + (unsigned)by * (unsigned)(k - lo[2]));
+}
+
+__device__ __forceinline__ unsigned gidx32(const Geo &g, int i, int j, int k)
+{
+    return (unsigned)i + (unsigned)g.X * ((unsigned)j + (unsigned)g.Y * (unsigned)k);
 }
 
 // ---------------------------------------------------------------- curls

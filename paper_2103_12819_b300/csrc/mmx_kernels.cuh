@@ -372,49 +372,46 @@ __device__ __forceinline__ bool residual_below(const unsigned long long *slot, d
 
 struct FaceOf {
     int d, i, j, k;
-    long long l;
+    unsigned l;
 };
 
-template <typename T>
-__device__ __forceinline__ bool box_face(const Geo &g, const Box<T> &b, long long t, FaceOf &fo)
+__device__ __forceinline__ FaceOf face_of(int4 e)
 {
-    fo.d = (int)(t / b.nb);
-    fo.l = t - (long long)fo.d * b.nb;
-    int bi = (int)(fo.l % b.bx);
-    int bj = (int)((fo.l / b.bx) % b.by);
-    int bk = (int)(fo.l / ((long long)b.bx * b.by));
-    fo.i = b.lo[0] + bi;
-    fo.j = b.lo[1] + bj;
-    fo.k = b.lo[2] + bk;
-    if (fo.i > g.n[0] || fo.j > g.n[1] || fo.k > g.n[2]) return false;
-    return face_valid(g, fo.d, fo.i, fo.j, fo.k);
+    FaceOf fo;
+    fo.l = (unsigned)e.x & 0x3fffffffu;
+    fo.d = (int)((unsigned)e.x >> 30);
+    fo.i = e.y;
+    fo.j = e.z;
+    fo.k = e.w;
+    return fo;
 }
 
-// H vector at face (d; i, j, k): own normal value and the four-point means of
-// the two transverse families (Sec. 3.1), from the padded global H (mode 0)
-// or from box-local iterates (mode 1).
-template <typename T>
+// H vector at a face of family D (i, j, k): own normal value and the
+// four-point means of the two transverse families (Sec. 3.1), from the padded
+// global H (mode 0) or from box-local iterates (mode 1).  The family is a
+// template argument so that every index below is in registers.
+template <int D, typename T>
 __device__ __forceinline__ void h_vector(const Geo &g, const Box<T> &b, T *const Hg[3], T *const Hb[3],
-                                         int mode, int d, int i, int j, int k, T h[3])
+                                         int mode, int i, int j, int k, T h[3])
 {
-    int ix[3] = {i, j, k};
-    h[d] = mode == 0 ? Hg[d][gidx(g, i, j, k)] : Hb[d][bidx(b.lo, b.bx, b.by, i, j, k)];
+    const int ix[3] = {i, j, k};
+    h[D] = mode == 0 ? Hg[D][gidx32(g, i, j, k)] : Hb[D][bidx32(b.lo, b.bx, b.by, i, j, k)];
 #pragma unroll
     for (int t = 0; t < 3; t++) {
-        if (t == d) continue;
+        if (t == D) continue;
         T sum = T(0);
         int cnt = 0;
 #pragma unroll
         for (int od = -1; od <= 0; od++) {
-            int nd = cell_nb(g, d, ix[d] + od);
+            int nd = cell_nb(g, D, ix[D] + od);
             if (nd < 0) continue;
 #pragma unroll
             for (int ot = 0; ot <= 1; ot++) {
                 int q[3] = {ix[0], ix[1], ix[2]};
-                q[d] = nd;
+                q[D] = nd;
                 q[t] = ix[t] + ot;
-                sum += mode == 0 ? Hg[t][gidx(g, q[0], q[1], q[2])]
-                                 : Hb[t][bidx(b.lo, b.bx, b.by, q[0], q[1], q[2])];
+                sum += mode == 0 ? Hg[t][gidx32(g, q[0], q[1], q[2])]
+                                 : Hb[t][bidx32(b.lo, b.bx, b.by, q[0], q[1], q[2])];
                 cnt++;
             }
         }
@@ -422,73 +419,144 @@ __device__ __forceinline__ void h_vector(const Geo &g, const Box<T> &b, T *const
     }
 }
 
+// First iterate on one magnetic face of family D: forms
+// Cp = H^n - dt/(2 mu0) curl E, beta = -kappa M^n x H_eff^n, e0 and
+// DeltaM^1 from H^n; returns max_c |DeltaM^1_c| / Ms.
+template <int D, typename T>
+__device__ __forceinline__ T mag_first(const Geo &g, const Fields<T> &f, const Box<T> &b, T *const Hin[3],
+                                       const FaceOf &fo, const T h0[3])
+{
+    const unsigned l = fo.l;
+    const T Ms = b.ms[D][l];
+    T rest, zp;
+    curl_e(g, f.E, f.inv_d, D, fo.i, fo.j, fo.k, rest, zp);
+    const T cp = Hin[D][gidx32(g, fo.i, fo.j, fo.k)] - b.cfar * (rest + zp);
+    const T Mn[3] = {b.M[3 * D][l], b.M[3 * D + 1][l], b.M[3 * D + 2][l]};
+    const T e0 = norm_defect(Ms, Mn[0], Mn[1], Mn[2]);
+    T h[3], heff[3];
+    h_vector<D>(g, b, Hin, Hin, 0, fo.i, fo.j, fo.k, h);
+#pragma unroll
+    for (int c = 0; c < 3; c++) heff[c] = h0[c] + h[c];
+    T dM[3], dMh;
+    const T k1 = b.k1[D][l], k2 = b.k2[D][l];
+    if (b.order == 2) {
+        const T beta[3] = {-k1 * (Mn[1] * heff[2] - Mn[2] * heff[1]), -k1 * (Mn[2] * heff[0] - Mn[0] * heff[2]),
+                           -k1 * (Mn[0] * heff[1] - Mn[1] * heff[0])};
+        llg_iterate(Mn, beta, heff, k1, k2, Ms, e0, D, dM, dMh);
+#pragma unroll
+        for (int c = 0; c < 3; c++) b.beta[3 * D + c][l] = beta[c];
+    } else {
+        llg_euler(Mn, heff, k1, k2, Ms, e0, D, dM, dMh);
+    }
+    b.Cp[D][l] = cp;
+    b.e0[D][l] = e0;
+    const bool wall = wall_node(g, D, D == 0 ? fo.i : D == 1 ? fo.j : fo.k);
+    b.Hit[1][D][l] = wall ? T(0) : cp - dMh;
+    T amax = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        b.dM[1][3 * D + c][l] = dM[c];
+        amax = max(amax, abs(dM[c]));
+    }
+    return amax / Ms;
+}
+
+// Phase 0 on a non-magnetic face of family D: its final H in both iterate
+// buffers.
+template <int D, typename T>
+__device__ __forceinline__ void non_first(const Geo &g, const Fields<T> &f, const Box<T> &b, T *const Hin[3],
+                                          const FaceOf &fo)
+{
+    const T v = h_face_nonmag(g, f, D, fo.i, fo.j, fo.k, Hin[D]);
+    b.Hit[0][D][fo.l] = v;
+    b.Hit[1][D][fo.l] = v;
+}
+
+// Iterate r >= 2 on one magnetic face of family D from the neighbours'
+// iterate r-1 (buffers pr -> cr); returns max_c |DeltaM^r_c - DeltaM^(r-1)_c| / Ms.
+template <int D, typename T>
+__device__ __forceinline__ T mag_next(const Geo &g, const Box<T> &b, const FaceOf &fo, T *const Hprev[3],
+                                      int pr, int cr, const T h0[3])
+{
+    const unsigned l = fo.l;
+    const T Ms = b.ms[D][l];
+    const T Mn[3] = {b.M[3 * D][l], b.M[3 * D + 1][l], b.M[3 * D + 2][l]};
+    const T beta[3] = {b.beta[3 * D][l], b.beta[3 * D + 1][l], b.beta[3 * D + 2][l]};
+    const T prev[3] = {b.dM[pr][3 * D][l], b.dM[pr][3 * D + 1][l], b.dM[pr][3 * D + 2][l]};
+    const T k1 = b.k1[D][l], k2 = b.k2[D][l], e0 = b.e0[D][l], cp = b.Cp[D][l];
+    T h[3], heff[3];
+    h_vector<D>(g, b, Hprev, Hprev, 1, fo.i, fo.j, fo.k, h);
+#pragma unroll
+    for (int c = 0; c < 3; c++) heff[c] = h0[c] + h[c];
+    T dM[3], dMh;
+    llg_iterate(Mn, beta, heff, k1, k2, Ms, e0, D, dM, dMh);
+    const bool wall = wall_node(g, D, D == 0 ? fo.i : D == 1 ? fo.j : fo.k);
+    b.Hit[cr][D][l] = wall ? T(0) : cp - dMh;
+    T amax = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        b.dM[cr][3 * D + c][l] = dM[c];
+        amax = max(amax, abs(dM[c] - prev[c]));
+    }
+    return amax / Ms;
+}
+
+// Final H and M^(n+1/2) on one magnetic face of family D; returns false if a
+// written value is not finite.
+template <int D, typename T>
+__device__ __forceinline__ bool mag_store(const Geo &g, const Box<T> &b, const FaceOf &fo, T *const Hout[3],
+                                          int fr)
+{
+    const unsigned l = fo.l;
+    const T v = b.Hit[fr][D][l];
+    Hout[D][gidx32(g, fo.i, fo.j, fo.k)] = v;
+    bool ok = isfinite(v);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const T m = b.M[3 * D + c][l] + b.dM[fr][3 * D + c][l];
+        b.M[3 * D + c][l] = m;
+        ok &= isfinite(m);
+    }
+    return ok;
+}
+
 // One H/M half step on every face of the magnetic box (Sec. 3.2.2 Step 1 or
 // Step 3) with the E in f.E, from H^n in Hin to H^(n+1/2) in Hout (the same
-// array for the in-place plain path).  Phase 0 forms Cp = H^n - dt/(2 mu0)
-// curl E, beta, e0 and the first iterate on magnetic faces and the final H
-// on non-magnetic ones; each further iteration r updates every magnetic face
-// from the neighbours' iterate r-1 (Jacobi), reduces
-// max |DeltaM^r - DeltaM^(r-1)|/Ms into res[r] (warp shuffle, block max, one
-// atomicMax on the FP64 bit pattern per block) and meets at a bounded grid
-// barrier; all blocks then read res[r] and stop together at the first r with
-// res[r] < tol (or at max_iter, latching kErrNotConverged).  Returns false
-// if a barrier timed out.
+// arrays for the in-place plain path).  Work comes from two lists built when
+// the materials are set, each ordered by family: the magnetic faces and the
+// other faces of the box.  Phase 0 gives non-magnetic faces their final H and
+// forms the first iterate on magnetic faces; each further iteration r
+// updates every magnetic face from the neighbours' iterate r-1 (Jacobi),
+// reduces max |DeltaM^r - DeltaM^(r-1)|/Ms into res[r] (warp shuffle, block
+// max, one atomicMax on the FP64 bit pattern per block) and meets at a
+// bounded grid barrier; all blocks then read res[r] and stop together at the
+// first r with res[r] < tol (or at max_iter, latching kErrNotConverged).
+// Returns false if a barrier timed out.
 template <typename T>
-__device__ bool hm_half_step(const Geo &g, const Fields<T> &f, const Box<T> &b, const T *Hin, T *const Hout[3],
-                             unsigned long long *res)
+__device__ bool hm_half_step(const Geo &g, const Fields<T> &f, const Box<T> &b, T *const Hin[3],
+                             T *const Hout[3], unsigned long long *res)
 {
-    const long long F = 3 * b.nb;
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    const int stride = gridDim.x * blockDim.x;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
     const T h0[3] = {(T)b.h0[0], (T)b.h0[1], (T)b.h0[2]};
-    T *const Hb0[3] = {b.Hit[0][0], b.Hit[0][1], b.Hit[0][2]};
-    T *const Hg[3] = {const_cast<T *>(Hin) , nullptr, nullptr};
-    (void)Hg;
 
     // ---- phase 0: r = 1
+    for (int t = t0; t < b.nnon; t += stride) {
+        const FaceOf fo = face_of(b.nonmag[t]);
+        if (fo.d == 0)
+            non_first<0>(g, f, b, Hin, fo);
+        else if (fo.d == 1)
+            non_first<1>(g, f, b, Hin, fo);
+        else
+            non_first<2>(g, f, b, Hin, fo);
+    }
     T rmax = T(0);
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < F; t += stride) {
-        FaceOf fo;
-        if (!box_face(g, b, t, fo)) continue;
-        const int d = fo.d;
-        const long long l = fo.l;
-        T Ms = b.ms[d][l];
-        if (!(Ms > T(0))) {
-            T v = h_face_nonmag(g, f, d, fo.i, fo.j, fo.k, f.H[d]);
-            b.Hit[0][d][l] = v;
-            b.Hit[1][d][l] = v;
-            continue;
-        }
-        T rest, zp;
-        curl_e(g, f.E, f.inv_d, d, fo.i, fo.j, fo.k, rest, zp);
-        size_t q = gidx(g, fo.i, fo.j, fo.k);
-        T cp = f.H[d][q] - b.cfar * (rest + zp);
-        T Mn[3] = {b.M[3 * d][l], b.M[3 * d + 1][l], b.M[3 * d + 2][l]};
-        T e0 = norm_defect(Ms, Mn[0], Mn[1], Mn[2]);
-        T h[3], heff[3];
-        h_vector(g, b, f.H, Hb0, 0, d, fo.i, fo.j, fo.k, h);
-#pragma unroll
-        for (int c = 0; c < 3; c++) heff[c] = h0[c] + h[c];
-        T dM[3], dMh;
-        T k1 = b.k1[d][l], k2 = b.k2[d][l];
-        if (b.order == 2) {
-            T beta[3] = {-k1 * (Mn[1] * heff[2] - Mn[2] * heff[1]), -k1 * (Mn[2] * heff[0] - Mn[0] * heff[2]),
-                         -k1 * (Mn[0] * heff[1] - Mn[1] * heff[0])};
-            llg_iterate(Mn, beta, heff, k1, k2, Ms, e0, d, dM, dMh);
-            for (int c = 0; c < 3; c++) b.beta[3 * d + c][l] = beta[c];
-        } else {
-            llg_euler(Mn, heff, k1, k2, Ms, e0, d, dM, dMh);
-        }
-        b.Cp[d][l] = cp;
-        b.e0[d][l] = e0;
-        bool wall = wall_node(g, d, d == 0 ? fo.i : d == 1 ? fo.j : fo.k);
-        b.Hit[1][d][l] = wall ? T(0) : cp - dMh;
-        T amax = T(0);
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            b.dM[1][3 * d + c][l] = dM[c];
-            amax = max(amax, abs(dM[c]));
-        }
-        rmax = max(rmax, amax / Ms);
+    for (int t = t0; t < b.nmag; t += stride) {
+        const FaceOf fo = face_of(b.mag[t]);
+        T rv = fo.d == 0   ? mag_first<0>(g, f, b, Hin, fo, h0)
+               : fo.d == 1 ? mag_first<1>(g, f, b, Hin, fo, h0)
+                           : mag_first<2>(g, f, b, Hin, fo, h0);
+        rmax = max(rmax, rv);
     }
     rmax = block_max(rmax);
     publish_residual(&res[1], rmax);
@@ -501,31 +569,12 @@ __device__ bool hm_half_step(const Geo &g, const Fields<T> &f, const Box<T> &b, 
         const int pr = (r - 1) & 1, cr = r & 1;
         T *const Hprev[3] = {b.Hit[pr][0], b.Hit[pr][1], b.Hit[pr][2]};
         rmax = T(0);
-        for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < F; t += stride) {
-            FaceOf fo;
-            if (!box_face(g, b, t, fo)) continue;
-            const int d = fo.d;
-            const long long l = fo.l;
-            T Ms = b.ms[d][l];
-            if (!(Ms > T(0))) continue;
-            T Mn[3] = {b.M[3 * d][l], b.M[3 * d + 1][l], b.M[3 * d + 2][l]};
-            T beta[3] = {b.beta[3 * d][l], b.beta[3 * d + 1][l], b.beta[3 * d + 2][l]};
-            T h[3], heff[3];
-            h_vector(g, b, f.H, Hprev, 1, d, fo.i, fo.j, fo.k, h);
-#pragma unroll
-            for (int c = 0; c < 3; c++) heff[c] = h0[c] + h[c];
-            T dM[3], dMh;
-            llg_iterate(Mn, beta, heff, b.k1[d][l], b.k2[d][l], Ms, b.e0[d][l], d, dM, dMh);
-            bool wall = wall_node(g, d, d == 0 ? fo.i : d == 1 ? fo.j : fo.k);
-            b.Hit[cr][d][l] = wall ? T(0) : b.Cp[d][l] - dMh;
-            T amax = T(0);
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                T prev = b.dM[pr][3 * d + c][l];
-                b.dM[cr][3 * d + c][l] = dM[c];
-                amax = max(amax, abs(dM[c] - prev));
-            }
-            rmax = max(rmax, amax / Ms);
+        for (int t = t0; t < b.nmag; t += stride) {
+            const FaceOf fo = face_of(b.mag[t]);
+            T rv = fo.d == 0   ? mag_next<0>(g, b, fo, Hprev, pr, cr, h0)
+                   : fo.d == 1 ? mag_next<1>(g, b, fo, Hprev, pr, cr, h0)
+                               : mag_next<2>(g, b, fo, Hprev, pr, cr, h0);
+            rmax = max(rmax, rv);
         }
         rmax = block_max(rmax);
         publish_residual(&res[r], rmax);
@@ -535,24 +584,21 @@ __device__ bool hm_half_step(const Geo &g, const Fields<T> &f, const Box<T> &b, 
 
     // ---- write back H (all box faces) and M (magnetic faces)
     const int fr = r & 1;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < F; t += stride) {
-        FaceOf fo;
-        if (!box_face(g, b, t, fo)) continue;
-        const int d = fo.d;
-        const long long l = fo.l;
-        T v = b.Hit[fr][d][l];
-        Hout[d][gidx(g, fo.i, fo.j, fo.k)] = v;
-        bool bad = !isfinite(v);
-        if (b.ms[d][l] > T(0)) {
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                T m = b.M[3 * d + c][l] + b.dM[fr][3 * d + c][l];
-                b.M[3 * d + c][l] = m;
-                bad |= !isfinite(m);
-            }
-        }
-        if (bad) atomicOr(b.err, kErrNonFinite);
+    bool ok = true;
+    for (int t = t0; t < b.nnon; t += stride) {
+        const FaceOf fo = face_of(b.nonmag[t]);
+        const T v = b.Hit[fr][fo.d][fo.l];
+        T *const Ho = fo.d == 0 ? Hout[0] : fo.d == 1 ? Hout[1] : Hout[2];
+        Ho[gidx32(g, fo.i, fo.j, fo.k)] = v;
+        ok &= isfinite(v);
     }
+    for (int t = t0; t < b.nmag; t += stride) {
+        const FaceOf fo = face_of(b.mag[t]);
+        ok &= fo.d == 0   ? mag_store<0>(g, b, fo, Hout, fr)
+              : fo.d == 1 ? mag_store<1>(g, b, fo, Hout, fr)
+                          : mag_store<2>(g, b, fo, Hout, fr);
+    }
+    if (!ok) atomicOr(b.err, kErrNonFinite);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (!conv && b.order == 2) atomicOr(b.err, kErrNotConverged);
         unsigned long long hs = *b.halfsteps;
@@ -571,20 +617,18 @@ __device__ bool hm_half_step(const Geo &g, const Fields<T> &f, const Box<T> &b, 
 template <typename T>
 __global__ void __launch_bounds__(256) k_hm_box(const __grid_constant__ Geo g,
                                                 const __grid_constant__ Fields<T> f,
-                                                const __grid_constant__ Box<T> b, Ptr3<T> Hout, int nsub,
-                                                int slot)
+                                                const __grid_constant__ Box<T> b,
+                                                const __grid_constant__ Ptr3<T> Hout, int nsub, int slot)
 {
     const int W = kMaxIter + 1;
     if (blockIdx.x == 0) {
         unsigned long long *other = b.res + 2 * (1 - slot) * W;
         for (int r = threadIdx.x; r < 2 * W; r += blockDim.x) other[r] = 0ull;
     }
-    if (!hm_half_step(g, f, b, f.H[0], Hout.p, b.res + 2 * slot * W)) return;
+    if (!hm_half_step(g, f, b, f.H, Hout.p, b.res + 2 * slot * W)) return;
     if (nsub == 2) {
         if (!grid_barrier(b.bar, b.err)) return;
-        Fields<T> f2 = f;
-        for (int a = 0; a < 3; a++) f2.H[a] = Hout.p[a];
-        hm_half_step(g, f2, b, f2.H[0], Hout.p, b.res + (2 * slot + 1) * W);
+        hm_half_step(g, f, b, Hout.p, Hout.p, b.res + (2 * slot + 1) * W);
     }
 }
 
