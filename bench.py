@@ -126,7 +126,7 @@ def alg_bytes_per_cell(kernel, w, esz):
     a fused E+H+H pass reads E, H, eps_r and writes E, H (13 words); the H/M
     box kernel reads E, H, M, Ms, alpha, gamma and writes H, M on its faces
     (per magnetic cell 6 + 9 + 3 read, 3 + 9 written)."""
-    words = {"e_update": 10, "h_update": 9, "fused_eh": 13}.get(kernel)
+    words = {"e_update": 10, "h_update": 9, "fused_eh": 13, "fused_eh_vec": 13}.get(kernel)
     if words is not None:
         return words * esz
     return None

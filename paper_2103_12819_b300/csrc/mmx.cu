@@ -14,15 +14,16 @@
 #include <vector>
 
 #include "mmx.h"
-#include "mmx_kernels.cuh"
+#include "mmx_fused.cuh"
 
 using namespace mmx;
 
 namespace {
 
 // Kernel kinds timed by the optional profiler.
-enum KernelKind { KK_HM_BOX = 0, KK_H_UPDATE, KK_E_UPDATE, KK_HARD, KK_FUSED, KK_COUNT };
-const char *const kKernelNames[KK_COUNT] = {"hm_box", "h_update", "e_update", "hard_source", "fused_eh"};
+enum KernelKind { KK_HM_BOX = 0, KK_H_UPDATE, KK_E_UPDATE, KK_HARD, KK_FUSED, KK_FUSED_VEC, KK_ZERO_WALLS, KK_COUNT };
+const char *const kKernelNames[KK_COUNT] = {"hm_box",   "h_update",     "e_update",  "hard_source",
+                                            "fused_eh", "fused_eh_vec", "zero_walls"};
 
 struct ProfRec {
     int kind;
@@ -45,6 +46,11 @@ struct mmx_ctx {
     void *Ealt[3] = {}, *Halt[3] = {}, *Ezpalt[2] = {};
     int fused_chunk = 0;
     int fused_grid_z = 0;
+    // vectorised fused kernel: plan (0 chunk = not planned) and wall state
+    int vec_chunk = 0;
+    dim3 vec_grid;
+    int vec_xstride = 0;
+    bool walls_dirty = false;
     // coefficients
     void *ca[3] = {}, *cb[3] = {}, *fh[3] = {};
     void *dampE = nullptr, *dampH = nullptr;
@@ -597,8 +603,124 @@ static void launch_fused(mmx_ctx *ctx, dim3 G, dim3 B, const Fields<T> &f, Ptr3<
 #undef MMX_FUSED_CASE
 }
 
+// ------------------------------------------- vectorised fused kernel (PEC x, y)
+
+constexpr int kVBY = 8;   // rows per CTA (+1 halo warp)
+
+// The vectorised kernel covers grids with PEC x and y walls whose magnetic
+// box stays clear of the PML layers (it writes box faces for the box kernel
+// to overwrite, which the in-place PML split parts would not survive).
+static bool vec_usable(const mmx_ctx *ctx)
+{
+    if (ctx->g.per[0] || ctx->g.per[1]) return false;
+    if (ctx->magnetic && ctx->g.npml > 0 &&
+        (ctx->lo[2] < ctx->g.npml + 1 || ctx->hi[2] > ctx->desc.n[2] - ctx->g.npml - 1))
+        return false;
+    return true;
+}
+
+// Opt every variant in to its dynamic shared memory (above the 48 KB default).
+template <typename T, int NH, bool PMLK, bool GEN> static cudaError_t set_vec_smem_v()
+{
+    return cudaFuncSetAttribute(k_fused_vec<T, kVBY, NH, PMLK, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)VecLayout<T, kVBY, GEN>::bytes);
+}
+
+template <typename T> static cudaError_t set_vec_smem()
+{
+    cudaError_t e = cudaSuccess;
+    cudaError_t r[8] = {set_vec_smem_v<T, 1, false, false>(), set_vec_smem_v<T, 1, false, true>(),
+                        set_vec_smem_v<T, 1, true, false>(),  set_vec_smem_v<T, 1, true, true>(),
+                        set_vec_smem_v<T, 2, false, false>(), set_vec_smem_v<T, 2, false, true>(),
+                        set_vec_smem_v<T, 2, true, false>(),  set_vec_smem_v<T, 2, true, true>()};
+    for (cudaError_t x : r)
+        if (x != cudaSuccess) e = x;
+    return e;
+}
+
+template <typename T> static int plan_vec(mmx_ctx *ctx)
+{
+    constexpr int W = 32 * Lanes<T>::V;
+    int dev = 0, nsm = 0, per = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CK(set_vec_smem<T>());
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused_vec<T, kVBY, 2, true, false>,
+                                                     32 * (kVBY + 1), VecLayout<T, kVBY, false>::bytes));
+    per = std::max(per, 1);
+    const int *n = ctx->desc.n;
+    const int xs = W - Lanes<T>::V;
+    const int ntx = n[0] <= W ? 1 : 1 + (n[0] - W + xs - 1) / xs;
+    const int nty = (n[1] + kVBY - 1) / kVBY;
+    long long nch = std::max(1LL, ((long long)per * nsm) / ((long long)ntx * nty));
+    int chunk = (int)std::max(2LL, (n[2] + nch - 1) / nch);
+    chunk = std::min(chunk, n[2]);
+    ctx->vec_chunk = chunk;
+    ctx->vec_xstride = xs;
+    ctx->vec_grid = dim3(ntx, nty, (n[2] + chunk - 1) / chunk);
+    return MMX_OK;
+}
+
+template <typename T> static int zero_walls(mmx_ctx *ctx)
+{
+    WallList<T> L;
+    L.n = 0;
+    for (int a = 0; a < 3; a++) {
+        L.p[L.n++] = (T *)ctx->E[a];
+        L.p[L.n++] = (T *)ctx->Ealt[a];
+        L.p[L.n++] = (T *)ctx->H[a];
+        L.p[L.n++] = (T *)ctx->Halt[a];
+    }
+    for (int a = 0; a < 2; a++) {
+        if (ctx->Ezp[a]) L.p[L.n++] = (T *)ctx->Ezp[a];
+        if (ctx->Ezpalt[a]) L.p[L.n++] = (T *)ctx->Ezpalt[a];
+    }
+    dim3 G((ctx->g.X + ctx->g.Y + 255) / 256, ctx->desc.n[2] + 1);
+    prof_begin(ctx, KK_ZERO_WALLS);
+    k_zero_walls<T><<<G, 256, 0, ctx->stream>>>(ctx->g, L);
+    if (ctx->Hzp[0]) {
+        WallList<T> P;
+        P.n = 0;
+        for (int a = 0; a < 2; a++) P.p[P.n++] = (T *)ctx->Hzp[a];
+        k_zero_walls<T><<<G, 256, 0, ctx->stream>>>(ctx->g, P);
+    }
+    prof_end(ctx);
+    CK(cudaGetLastError());
+    return MMX_OK;
+}
+
+template <typename T, int NH, bool PMLK, bool GEN>
+static void launch_vec_v(mmx_ctx *ctx, const Fields<T> &f, const FusedIO<T> &io, int nsrc)
+{
+    k_fused_vec<T, kVBY, NH, PMLK, GEN><<<ctx->vec_grid, dim3(32, kVBY + 1), VecLayout<T, kVBY, GEN>::bytes,
+                                          ctx->stream>>>(
+        ctx->g, f, io, (const Src<T> *)ctx->dsrc, nsrc, ctx->vec_chunk, ctx->vec_xstride);
+}
+
+template <typename T>
+static void launch_vec(mmx_ctx *ctx, const Fields<T> &f, const FusedIO<T> &io, int nsrc, int nhalf)
+{
+    const bool pml = ctx->g.npml > 0, gen = ctx->any_sigma || ctx->any_mu;
+#define MMX_VEC_CASE(NHV, PV, GV)                                                                    \
+    if (nhalf == NHV && pml == PV && gen == GV) {                                                    \
+        launch_vec_v<T, NHV, PV, GV>(ctx, f, io, nsrc);                                              \
+        return;                                                                                      \
+    }
+    MMX_VEC_CASE(2, true, false) MMX_VEC_CASE(2, false, false) MMX_VEC_CASE(2, true, true)
+    MMX_VEC_CASE(2, false, true) MMX_VEC_CASE(1, true, false) MMX_VEC_CASE(1, false, false)
+    MMX_VEC_CASE(1, true, true) MMX_VEC_CASE(1, false, true)
+#undef MMX_VEC_CASE
+}
+
 template <typename T> static int step_fused(mmx_ctx *ctx, int nsteps)
 {
+    const bool vec = vec_usable(ctx);
+    if (vec) {
+        if (!ctx->vec_chunk) {
+            int rc = plan_vec<T>(ctx);
+            if (rc) return rc;
+        }
+    }
     if (!ctx->fused_chunk) {
         int rc = plan_fused<T>(ctx);
         if (rc) return rc;
@@ -611,6 +733,14 @@ template <typename T> static int step_fused(mmx_ctx *ctx, int nsteps)
         Fields<T> f = make_fields<T>(ctx);
         int rc = half_step<T>(ctx, f, b, (ctx->steps + 0.5) * ctx->desc.dt);
         if (rc) return rc;
+    }
+    // Wall values set through mmx_set_field have been used by that half step
+    // (as the per-update path uses them); from here on they are zero, which
+    // the vectorised kernel relies on for the x = nx column and y = ny row.
+    if (vec && ctx->walls_dirty) {
+        int rc = zero_walls<T>(ctx);
+        if (rc) return rc;
+        ctx->walls_dirty = false;
     }
     const int *n = ctx->desc.n;
     dim3 B(kFBX, kFBY, 1);
@@ -629,8 +759,23 @@ template <typename T> static int step_fused(mmx_ctx *ctx, int nsteps)
         Ptr3<T> Hn = {{(T *)ctx->Halt[0], (T *)ctx->Halt[1], (T *)ctx->Halt[2]}};
         Ptr3<T> Zo = {{(T *)ctx->Ezp[0], (T *)ctx->Ezp[1], nullptr}};
         Ptr3<T> Zn = {{(T *)ctx->Ezpalt[0], (T *)ctx->Ezpalt[1], nullptr}};
-        prof_begin(ctx, KK_FUSED);
-        launch_fused<T>(ctx, G, B, f, Eo, Ho, En, Hn, Zo, Zn, nsrc, nhalf);
+        prof_begin(ctx, vec ? KK_FUSED_VEC : KK_FUSED);
+        if (vec) {
+            FusedIO<T> io;
+            for (int a = 0; a < 3; a++) {
+                io.Eo[a] = Eo.p[a];
+                io.Ho[a] = Ho.p[a];
+                io.En[a] = En.p[a];
+                io.Hn[a] = Hn.p[a];
+            }
+            for (int a = 0; a < 2; a++) {
+                io.Zo[a] = Zo.p[a];
+                io.Zn[a] = Zn.p[a];
+            }
+            launch_vec<T>(ctx, f, io, nsrc, nhalf);
+        } else {
+            launch_fused<T>(ctx, G, B, f, Eo, Ho, En, Hn, Zo, Zn, nsrc, nhalf);
+        }
         prof_end(ctx);
         CK(cudaGetLastError());
         if (ctx->magnetic) {
@@ -991,6 +1136,7 @@ int mmx_set_field(mmx_ctx *ctx, int id, const double *host, long long n)
     int e[3];
     if (!field_ext(ctx, id, e)) return fail(ctx, MMX_ERR_INVALID, "bad field id %d", id);
     if (n != (long long)e[0] * e[1] * e[2]) return fail(ctx, MMX_ERR_INVALID, "field %d needs %lld values", id, (long long)e[0] * e[1] * e[2]);
+    ctx->walls_dirty = true;
     return is_fp64(ctx) ? copy_field_t<double>(ctx, id, const_cast<double *>(host), n, 1)
                         : copy_field_t<float>(ctx, id, const_cast<double *>(host), n, 1);
 }

@@ -1,0 +1,502 @@
+// mmx_fused.cuh -- the vectorised one-pass E/H kernel of the coupled
+// Maxwell-LLG step (arXiv 2103.12819, Sec. 3.2.2 Steps 2 and 3 with the next
+// step's Step 1 folded in), for grids whose x and y boundaries are PEC walls.
+//
+// Work decomposition.  A CTA owns a strip of W = 32 V columns (V = 16 bytes /
+// sizeof(T): 4 floats or 2 doubles per lane, moved with one 16-byte load or
+// store) by BY rows, and marches its z chunk plane by plane.  Lane L of warp
+// w holds columns x0 + V L ... x0 + V L + V-1 of row y0 + w.  Neighbours
+// along x come from warp shuffles; neighbours along y from double-buffered
+// shared-memory rows.  Warp BY is a halo warp: it computes E^(n+1) of row
+// y0 + BY, which the H update of row y0 + BY - 1 needs, and stores nothing.
+// A strip narrower than the grid (nx > W) likewise treats lane 31 as a halo
+// lane and the strips overlap by V columns.
+//
+// Per plane k of the chunk: H^(n+1/2) of plane k is staged for the warp
+// below; E^(n+1) of plane k (Ex, Ey at node k; Ez at layer k+1/2) is formed
+// and staged for the warp above; the next plane is prefetched into
+// registers; then Hz at plane k and Hx, Hy at layer k-1/2 take NH half steps
+// (Steps 3 and the next step's 1, both with E^(n+1)).  Faces of the magnetic
+// box are written here too and overwritten by the H/M box kernel, which runs
+// after this one from the old H buffer.  Walls: Ey, Ez at x = 0, Ex, Ez at
+// y = 0 and every component at z walls are written as zero; the wall column
+// x = nx and wall row y = ny are never written (the host keeps them zero).
+#pragma once
+#include "mmx_kernels.cuh"
+
+namespace mmx {
+
+template <typename T> struct FusedIO {
+    const T *Eo[3];
+    const T *Ho[3];
+    T *En[3];
+    T *Hn[3];
+    const T *Zo[2];     // PML split part of Ex, Ey (old)
+    T *Zn[2];           // (new)
+};
+
+template <typename T> struct Lanes;
+template <> struct Lanes<float> { static constexpr int V = 4; };
+template <> struct Lanes<double> { static constexpr int V = 2; };
+
+// 16-byte vector loads (read-only path) and stores.
+__device__ __forceinline__ void vload(float (&r)[4], const float *p)
+{
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+}
+__device__ __forceinline__ void vload(double (&r)[2], const double *p)
+{
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    r[0] = v.x; r[1] = v.y;
+}
+// coherent load for arrays this kernel also writes (the PML split H)
+__device__ __forceinline__ void vload_rw(float (&r)[4], const float *p)
+{
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+}
+__device__ __forceinline__ void vload_rw(double (&r)[2], const double *p)
+{
+    const double2 v = *reinterpret_cast<const double2 *>(p);
+    r[0] = v.x; r[1] = v.y;
+}
+// shared-memory 16-byte load
+__device__ __forceinline__ void sload(float (&r)[4], const float *p)
+{
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+}
+__device__ __forceinline__ void sload(double (&r)[2], const double *p)
+{
+    const double2 v = *reinterpret_cast<const double2 *>(p);
+    r[0] = v.x; r[1] = v.y;
+}
+__device__ __forceinline__ void vstore(float *p, const float (&r)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(r[0], r[1], r[2], r[3]);
+}
+__device__ __forceinline__ void vstore(double *p, const double (&r)[2])
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(r[0], r[1]);
+}
+
+template <typename T, int V> __device__ __forceinline__ void vzero(T (&r)[V])
+{
+#pragma unroll
+    for (int e = 0; e < V; e++) r[e] = T(0);
+}
+template <typename T, int V> __device__ __forceinline__ void vfill(T (&r)[V], T x)
+{
+#pragma unroll
+    for (int e = 0; e < V; e++) r[e] = x;
+}
+template <typename T, int V> __device__ __forceinline__ void vcopy(T (&d)[V], const T (&s)[V])
+{
+#pragma unroll
+    for (int e = 0; e < V; e++) d[e] = s[e];
+}
+
+// Asynchronous global -> shared copies (cp.async): 16 bytes, or one element
+// for the halo column; a false predicate zero-fills the destination and
+// reads nothing (the source operand is then the array base, always valid).
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp16(void *dst, const void *src, const void *base, bool on)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)),
+                 "l"(on ? src : base), "r"(on ? 16 : 0)
+                 : "memory");
+}
+template <typename T> __device__ __forceinline__ void cp1(T *dst, const T *src, const T *base, bool on)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_u32(dst)), "l"(on ? src : base),
+                 "n"(sizeof(T)), "r"(on ? (int)sizeof(T) : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_wait_all()
+{
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Shared-memory layout of the vectorised kernel (elements of T):
+//   stage [2][NF][R][W]  per plane: Hx, Hy (layer k+1/2), Hz (node k), Ex, Ey,
+//                        Ez, cbx, cby, cbz [, cax, cay, caz] of rows y0..y0+BY
+//   up    [2][2][W]      Hx, Hz of row y0-1
+//   left  [2][2][RP]     Hy, Hz of column x0-1, one per row
+//   sEx, sEz [2][R][W]   E^(n+1) exchanged between rows
+template <typename T, int BY, bool GEN> struct VecLayout {
+    static constexpr int V = Lanes<T>::V;
+    static constexpr int W = 32 * V;
+    static constexpr int R = BY + 1;
+    static constexpr int RP = (R + 3) / 4 * 4;
+    static constexpr int NF = GEN ? 12 : 9;
+    static constexpr int stage = 0;
+    static constexpr int up = stage + 2 * NF * R * W;
+    static constexpr int left = up + 2 * 2 * W;
+    static constexpr int ex = left + 2 * 2 * RP;
+    static constexpr int ez = ex + 2 * R * W;
+    static constexpr int total = ez + 2 * R * W;
+    static constexpr size_t bytes = (size_t)total * sizeof(T);
+};
+
+template <typename T, int BY, int NH, bool PMLK, bool GEN>
+__global__ void __launch_bounds__(32 * (BY + 1), 2)
+    k_fused_vec(const __grid_constant__ Geo g, const __grid_constant__ Fields<T> f,
+                const __grid_constant__ FusedIO<T> io, const Src<T> *__restrict__ src, int nsrc, int chunk,
+                int xstride)
+{
+    using L = VecLayout<T, BY, GEN>;
+    constexpr int V = L::V, W = L::W, R = L::R, RP = L::RP, NF = L::NF;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *const sm = reinterpret_cast<T *>(smem_raw);
+    auto S = [&](int st, int fld, int row) -> T * { return sm + L::stage + ((st * NF + fld) * R + row) * W; };
+    auto U = [&](int st, int fld) -> T * { return sm + L::up + (st * 2 + fld) * W; };
+    auto Lf = [&](int st, int fld) -> T * { return sm + L::left + (st * 2 + fld) * RP; };
+    auto SEx = [&](int bb, int row) -> T * { return sm + L::ex + (bb * R + row) * W; };
+    auto SEz = [&](int bb, int row) -> T * { return sm + L::ez + (bb * R + row) * W; };
+
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int x0 = blockIdx.x * xstride;
+    const int i0 = x0 + V * lane;
+    const int col = V * lane;
+    const int j = blockIdx.y * BY + w;
+    const int k0 = blockIdx.z * chunk;
+    const int k1 = min(k0 + chunk, nz);
+    const bool last_chunk = k1 == nz;
+    const bool lane_on = j < ny && i0 < nx;
+    const bool up_on = w == 0 && j > 0 && j <= ny && i0 < nx;
+    const bool left_on = lane == 0 && x0 > 0 && j < ny;
+    const bool store = lane_on && w < BY && (lane < 31 || x0 + W >= nx);
+    const unsigned XY = (unsigned)g.X * (unsigned)g.Y;
+    const unsigned rb = (unsigned)i0 + (unsigned)g.X * (unsigned)j;
+    const unsigned rbu = rb - (unsigned)g.X;
+    const unsigned rbl = (unsigned)(x0 - 1) + (unsigned)g.X * (unsigned)j;
+    const T idx = f.inv_d[0], idy = f.inv_d[1], idz = f.inv_d[2];
+    const T fh0 = f.fh0;
+    const bool wy = j == 0;
+    bool cin[V], xw[V];
+#pragma unroll
+    for (int e = 0; e < V; e++) {
+        cin[e] = i0 + e < nx;
+        xw[e] = i0 + e == 0;
+    }
+    // z range of the soft sources touching this lane's columns
+    int src_klo = 1 << 30, src_khi = -1;
+    if (lane_on)
+        for (int s = 0; s < nsrc; s++) {
+            const Src<T> &q = src[s];
+            if (q.kind == 1 || (q.kind == 0 && q.j == j && q.i >= i0 && q.i < i0 + V)) {
+                src_klo = min(src_klo, q.k);
+                src_khi = max(src_khi, q.k);
+                if (g.per[2] && q.k == 0) src_khi = max(src_khi, nz);
+            }
+        }
+
+    // copies of everything plane k needs into stage st
+    auto issue = [&](int k, int st) {
+        const int ck = cell_nb(g, 2, k);
+        const unsigned kn = (unsigned)k * XY, kc = (unsigned)max(ck, 0) * XY;
+        const bool lay = ck >= 0;
+        cp16(S(st, 0, w) + col, io.Ho[0] + rb + kc, io.Ho[0], lane_on && lay);
+        cp16(S(st, 1, w) + col, io.Ho[1] + rb + kc, io.Ho[1], lane_on && lay);
+        cp16(S(st, 2, w) + col, io.Ho[2] + rb + kn, io.Ho[2], lane_on);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            cp16(S(st, 3 + c, w) + col, io.Eo[c] + rb + kn, io.Eo[c], lane_on);
+            cp16(S(st, 6 + c, w) + col, f.cb[c] + rb + kn, f.cb[c], lane_on);
+            if (GEN && f.ca[c]) cp16(S(st, 9 + c, w) + col, f.ca[c] + rb + kn, f.ca[c], lane_on);
+        }
+        if (w == 0) {
+            cp16(U(st, 0) + col, io.Ho[0] + rbu + kc, io.Ho[0], up_on && lay);
+            cp16(U(st, 1) + col, io.Ho[2] + rbu + kn, io.Ho[2], up_on);
+        }
+        if (lane == 0) {
+            cp1(Lf(st, 0) + w, io.Ho[1] + rbl + kc, io.Ho[1], left_on && lay);
+            cp1(Lf(st, 1) + w, io.Ho[2] + rbl + kn, io.Ho[2], left_on);
+        }
+        cp_commit();
+    };
+
+    T hxp[V], hyp[V];                 // Hx, Hy at layer k-1/2
+    T exq[V], eyq[V], ezq[V];         // E^(n+1) of plane k-1 (Ez: layer k-1/2)
+    vzero<T, V>(exq);
+    vzero<T, V>(eyq);
+    vzero<T, V>(ezq);
+    {
+        const int ckm = cell_nb(g, 2, k0 - 1);
+        if (lane_on && ckm >= 0) {
+            vload(hxp, io.Ho[0] + rb + (unsigned)ckm * XY);
+            vload(hyp, io.Ho[1] + rb + (unsigned)ckm * XY);
+        } else {
+            vzero<T, V>(hxp);
+            vzero<T, V>(hyp);
+        }
+    }
+    issue(k0, 0);
+    T acc = T(0);
+    int b = 0;
+    for (int k = k0; k <= k1; k++, b ^= 1) {
+        const int st = b;
+        cp_wait_all();
+        __syncthreads();          // plane k staged; every thread is done with plane k-1
+        if (k < k1) issue(k + 1, st ^ 1);
+
+        T hx[V], hy[V], hz[V], hzu[V], hxu[V];
+        sload(hx, S(st, 0, w) + col);
+        sload(hy, S(st, 1, w) + col);
+        sload(hz, S(st, 2, w) + col);
+        if (w == 0) {
+            sload(hxu, U(st, 0) + col);
+            sload(hzu, U(st, 1) + col);
+        } else {
+            sload(hxu, S(st, 0, w - 1) + col);
+            sload(hzu, S(st, 2, w - 1) + col);
+        }
+        // column i-1 of element 0: previous lane's last element, or the halo
+        T hzl = __shfl_up_sync(0xffffffffu, hz[V - 1], 1);
+        T hyl = __shfl_up_sync(0xffffffffu, hy[V - 1], 1);
+        if (lane == 0) {
+            hyl = Lf(st, 0)[w];
+            hzl = Lf(st, 1)[w];
+        }
+
+        // ---- E^(n+1) at plane k
+        const bool own_plane = k < k1 || last_chunk;
+        const bool wz = wall_node(g, 2, k);
+        const bool pml = PMLK && pml_e_plane(g, k);
+        const unsigned q = rb + (unsigned)k * XY;
+        T ex[V], ey[V], ez[V], zn0[V], zn1[V];
+        {
+            T eo[3][V], cb[3][V], ca[3][V];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                sload(eo[c], S(st, 3 + c, w) + col);
+                sload(cb[c], S(st, 6 + c, w) + col);
+                if (GEN && f.ca[c])
+                    sload(ca[c], S(st, 9 + c, w) + col);
+                else
+                    vfill<T, V>(ca[c], T(1));
+            }
+            T zo0[V], zo1[V];
+            if (pml && lane_on) {
+                vload(zo0, io.Zo[0] + q);
+                vload(zo1, io.Zo[1] + q);
+            } else {
+                vzero<T, V>(zo0);
+                vzero<T, V>(zo1);
+            }
+            const T hdamp = pml ? f.dampE[k] : T(1);
+            const bool src_here = k >= src_klo && k <= src_khi;
+#pragma unroll
+            for (int e = 0; e < V; e++) {
+                T J0 = T(0), J1 = T(0), J2 = T(0);
+                if (src_here && cin[e]) {
+                    J0 = j_source(g, f, src, nsrc, 0, i0 + e, j, k);
+                    J1 = j_source(g, f, src, nsrc, 1, i0 + e, j, k);
+                    J2 = j_source(g, f, src, nsrc, 2, i0 + e, j, k);
+                }
+                const T hzm = e > 0 ? hz[e > 0 ? e - 1 : 0] : hzl;
+                const T hym = e > 0 ? hy[e > 0 ? e - 1 : 0] : hyl;
+                // Ex (i+1/2, j, k)
+                {
+                    const T rest = (hz[e] - hzu[e]) * idy;
+                    const T zp = -(hy[e] - hyp[e]) * idz;
+                    T v, z = T(0);
+                    if (pml) {
+                        z = (ca[0][e] * (zo0[e] * hdamp) + cb[0][e] * zp) * hdamp;
+                        v = ca[0][e] * (eo[0][e] - zo0[e]) + cb[0][e] * (rest - J0) + z;
+                    } else {
+                        v = ca[0][e] * eo[0][e] + cb[0][e] * (rest + zp - J0);
+                    }
+                    const bool on = lane_on && cin[e] && !wy && !wz;
+                    ex[e] = on ? v : T(0);
+                    zn0[e] = on ? z : T(0);
+                }
+                // Ey (i, j+1/2, k)
+                {
+                    const T zp = (hx[e] - hxp[e]) * idz;
+                    const T rest = -(hz[e] - hzm) * idx;
+                    T v, z = T(0);
+                    if (pml) {
+                        z = (ca[1][e] * (zo1[e] * hdamp) + cb[1][e] * zp) * hdamp;
+                        v = ca[1][e] * (eo[1][e] - zo1[e]) + cb[1][e] * (rest - J1) + z;
+                    } else {
+                        v = ca[1][e] * eo[1][e] + cb[1][e] * (rest + zp - J1);
+                    }
+                    const bool on = lane_on && cin[e] && !xw[e] && !wz;
+                    ey[e] = on ? v : T(0);
+                    zn1[e] = on ? z : T(0);
+                }
+                // Ez (i, j, k+1/2)
+                {
+                    const T rest = (hy[e] - hym) * idx - (hx[e] - hxu[e]) * idy;
+                    const T v = ca[2][e] * eo[2][e] + cb[2][e] * (rest - J2);
+                    const bool on = lane_on && cin[e] && !xw[e] && !wy && k < nz;
+                    ez[e] = on ? v : T(0);
+                }
+            }
+        }
+        {
+            T *dx = SEx(b, w) + col;
+            T *dz = SEz(b, w) + col;
+#pragma unroll
+            for (int e = 0; e < V; e++) {
+                dx[e] = ex[e];
+                dz[e] = ez[e];
+            }
+        }
+        if (store && own_plane) {
+            vstore(io.En[0] + q, ex);
+            vstore(io.En[1] + q, ey);
+            if (k < nz) vstore(io.En[2] + q, ez);
+            if (pml) {
+                vstore(io.Zn[0] + q, zn0);
+                vstore(io.Zn[1] + q, zn1);
+            }
+#pragma unroll
+            for (int e = 0; e < V; e++) acc += ex[e] + ey[e] + ez[e];
+        }
+        __syncthreads();          // E^(n+1) of plane k visible to the row above
+
+        // ---- H: Hz at plane k, Hx and Hy at layer k-1/2
+        const T eyr = __shfl_down_sync(0xffffffffu, ey[0], 1);
+        const T ezr = __shfl_down_sync(0xffffffffu, ezq[0], 1);
+        if (w < BY) {
+            if (store && own_plane) {
+                T fh[V], exd[V];
+                if (GEN && f.fh[2])
+                    vload(fh, f.fh[2] + q);
+                else
+                    vfill<T, V>(fh, fh0);
+                sload(exd, SEx(b, w + 1) + col);
+                T hn[V];
+#pragma unroll
+                for (int e = 0; e < V; e++) {
+                    const T eyn = e < V - 1 ? ey[e < V - 1 ? e + 1 : 0] : (lane < 31 ? eyr : T(0));
+                    const T cz = (eyn - ey[e]) * idx - (exd[e] - ex[e]) * idy;
+                    T v = hz[e] - fh[e] * cz;
+                    if (NH == 2) v = v - fh[e] * cz;
+                    hn[e] = (cin[e] && !wz) ? v : T(0);
+                    acc += hn[e];
+                }
+                vstore(io.Hn[2] + q, hn);
+            }
+            if (store && k > k0) {
+                const int kl = k - 1;
+                const unsigned ql = q - XY;
+                const bool hp = PMLK && pml_h_plane(g, kl);
+                const T hdh = hp ? f.dampH[kl] : T(1);
+                T fhx[V], fhy[V], sx[V], sy[V], ezd[V];
+                if (GEN && f.fh[0])
+                    vload(fhx, f.fh[0] + ql);
+                else
+                    vfill<T, V>(fhx, fh0);
+                if (GEN && f.fh[1])
+                    vload(fhy, f.fh[1] + ql);
+                else
+                    vfill<T, V>(fhy, fh0);
+                if (hp) {
+                    vload_rw(sx, f.Hzp[0] + ql);
+                    vload_rw(sy, f.Hzp[1] + ql);
+                } else {
+                    vzero<T, V>(sx);
+                    vzero<T, V>(sy);
+                }
+                sload(ezd, SEz(b ^ 1, w + 1) + col);
+                T hxn[V], hyn[V];
+#pragma unroll
+                for (int e = 0; e < V; e++) {
+                    // Hx (i, j+1/2, k-1/2)
+                    {
+                        const T rest = (ezd[e] - ezq[e]) * idy;
+                        const T zp = -(ey[e] - eyq[e]) * idz;
+                        T v;
+                        if (hp) {
+                            T hzp = sx[e];
+                            T hr = hxp[e] - hzp;
+#pragma unroll
+                            for (int s = 0; s < NH; s++) {
+                                hzp = (hzp * hdh - fhx[e] * zp) * hdh;
+                                hr = hr - fhx[e] * rest;
+                            }
+                            sx[e] = (cin[e] && !xw[e]) ? hzp : T(0);
+                            v = hr + hzp;
+                        } else {
+                            v = hxp[e] - fhx[e] * (rest + zp);
+                            if (NH == 2) v = v - fhx[e] * (rest + zp);
+                        }
+                        hxn[e] = (cin[e] && !xw[e]) ? v : T(0);
+                    }
+                    // Hy (i+1/2, j, k-1/2)
+                    {
+                        const T ezn = e < V - 1 ? ezq[e < V - 1 ? e + 1 : 0] : (lane < 31 ? ezr : T(0));
+                        const T zp = (ex[e] - exq[e]) * idz;
+                        const T rest = -(ezn - ezq[e]) * idx;
+                        T v;
+                        if (hp) {
+                            T hzp = sy[e];
+                            T hr = hyp[e] - hzp;
+#pragma unroll
+                            for (int s = 0; s < NH; s++) {
+                                hzp = (hzp * hdh - fhy[e] * zp) * hdh;
+                                hr = hr - fhy[e] * rest;
+                            }
+                            sy[e] = (cin[e] && !wy) ? hzp : T(0);
+                            v = hr + hzp;
+                        } else {
+                            v = hyp[e] - fhy[e] * (rest + zp);
+                            if (NH == 2) v = v - fhy[e] * (rest + zp);
+                        }
+                        hyn[e] = (cin[e] && !wy) ? v : T(0);
+                    }
+                    acc += hxn[e] + hyn[e];
+                }
+                vstore(io.Hn[0] + ql, hxn);
+                vstore(io.Hn[1] + ql, hyn);
+                if (hp) {
+                    vstore(f.Hzp[0] + ql, sx);
+                    vstore(f.Hzp[1] + ql, sy);
+                }
+            }
+        }
+        // ---- advance
+        vcopy<T, V>(hxp, hx);
+        vcopy<T, V>(hyp, hy);
+        vcopy<T, V>(exq, ex);
+        vcopy<T, V>(eyq, ey);
+        vcopy<T, V>(ezq, ez);
+    }
+    if (!isfinite(acc)) atomicOr(f.err, kErrNonFinite);
+}
+
+// Zero the wall column x = nx and the wall row y = ny (all planes) of up to
+// 16 Yee arrays: every component there is either a PEC wall value or does
+// not exist, and the vectorised kernel never writes it.
+template <typename T> struct WallList {
+    T *p[16];
+    int n;
+};
+
+template <typename T> __global__ void k_zero_walls(const Geo g, WallList<T> L)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    size_t q;
+    if (t < g.Y)
+        q = gidx(g, g.n[0], t, k);
+    else if (t < g.Y + g.X)
+        q = gidx(g, t - g.Y, g.n[1], k);
+    else
+        return;
+    for (int a = 0; a < L.n; a++) L.p[a][q] = T(0);
+}
+
+} // namespace mmx
