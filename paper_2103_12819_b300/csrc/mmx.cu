@@ -65,7 +65,8 @@ struct mmx_ctx {
     int bx = 0, by = 0, bz = 0;
     long long nb = 0;
     std::vector<void *> box_allocs;
-    void *bM[9] = {}, *bbeta[9] = {}, *bdM[2][9] = {}, *bCp[3] = {}, *be0[3] = {}, *bHit[2][3] = {};
+    void *bM[9] = {}, *bHit[2][3] = {}, *bHit2[2][3] = {};
+    void *fcst = nullptr, *fmn = nullptr, *fbc = nullptr, *fdm[2] = {};   // per magnetic face (list order)
     void *bms[3] = {}, *bk1[3] = {}, *bk2[3] = {};
     int4 *dmag = nullptr, *dnon = nullptr;
     int nmag = 0, nnon = 0;
@@ -239,17 +240,17 @@ template <typename T> static Box<T> make_box(mmx_ctx *c)
     memset(&b, 0, sizeof b);
     for (int a = 0; a < 3; a++) b.lo[a] = c->lo[a];
     b.bx = c->bx; b.by = c->by; b.bz = c->bz; b.nb = c->nb;
-    for (int q = 0; q < 9; q++) {
-        b.M[q] = (T *)c->bM[q];
-        b.beta[q] = (T *)c->bbeta[q];
-        b.dM[0][q] = (T *)c->bdM[0][q];
-        b.dM[1][q] = (T *)c->bdM[1][q];
-    }
+    for (int q = 0; q < 9; q++) b.M[q] = (T *)c->bM[q];
+    b.cst = (const Q4<T> *)c->fcst;
+    b.mn = (Q4<T> *)c->fmn;
+    b.bc = (Q4<T> *)c->fbc;
+    b.dm[0] = (Q4<T> *)c->fdm[0];
+    b.dm[1] = (Q4<T> *)c->fdm[1];
     for (int a = 0; a < 3; a++) {
-        b.Cp[a] = (T *)c->bCp[a];
-        b.e0[a] = (T *)c->be0[a];
         b.Hit[0][a] = (T *)c->bHit[0][a];
         b.Hit[1][a] = (T *)c->bHit[1][a];
+        b.Hit2[0][a] = (T *)c->bHit2[0][a];
+        b.Hit2[1][a] = (T *)c->bHit2[1][a];
         b.ms[a] = (const T *)c->bms[a];
         b.k1[a] = (const T *)c->bk1[a];
         b.k2[a] = (const T *)c->bk2[a];
@@ -357,6 +358,7 @@ static void free_box(mmx_ctx *c)
     c->nb = 0;
     c->dmag = c->dnon = nullptr;
     c->nmag = c->nnon = 0;
+    c->fcst = c->fmn = c->fbc = c->fdm[0] = c->fdm[1] = nullptr;
 }
 
 // Work lists of the box kernel: every valid face of the box, split into
@@ -450,6 +452,10 @@ template <typename T> static int set_materials_t(mmx_ctx *ctx)
         int nblk = (int)((ctx->nb + 255) / 256);
         for (int d = 0; d < 3; d++) {
             k_box_materials<T><<<nblk, 256, 0, ctx->stream>>>(g, b, d, ctx->cell[3], ctx->cell[4], ctx->cell[5]);
+            CK(cudaGetLastError());
+        }
+        if (ctx->nmag > 0) {
+            k_box_cst<T><<<(ctx->nmag + 255) / 256, 256, 0, ctx->stream>>>(b);
             CK(cudaGetLastError());
         }
         int rc = compute_coop<T>(ctx);
@@ -605,7 +611,12 @@ static void launch_fused(mmx_ctx *ctx, dim3 G, dim3 B, const Fields<T> &f, Ptr3<
 
 // ------------------------------------------- vectorised fused kernel (PEC x, y)
 
-constexpr int kVBY = 8;   // rows per CTA (+1 halo warp)
+// Rows per CTA (+1 halo warp), chosen by measurement on the 128x128x512
+// waveguide: FP32 7 rows (8 warps, 2 CTAs/SM, no spills: 110 us; 8 rows 123,
+// 15 rows 122), FP64 8 rows (1269 us; 7 rows 1316).
+template <typename T> struct VecRows;
+template <> struct VecRows<float> { static constexpr int value = 7; };
+template <> struct VecRows<double> { static constexpr int value = 8; };
 
 // The vectorised kernel covers grids with PEC x and y walls whose magnetic
 // box stays clear of the PML layers (it writes box faces for the box kernel
@@ -622,8 +633,9 @@ static bool vec_usable(const mmx_ctx *ctx)
 // Opt every variant in to its dynamic shared memory (above the 48 KB default).
 template <typename T, int NH, bool PMLK, bool GEN> static cudaError_t set_vec_smem_v()
 {
-    return cudaFuncSetAttribute(k_fused_vec<T, kVBY, NH, PMLK, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)VecLayout<T, kVBY, GEN>::bytes);
+    constexpr int BY = VecRows<T>::value;
+    return cudaFuncSetAttribute(k_fused_vec<T, BY, NH, PMLK, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)VecLayout<T, BY, GEN>::bytes);
 }
 
 template <typename T> static cudaError_t set_vec_smem()
@@ -645,13 +657,14 @@ template <typename T> static int plan_vec(mmx_ctx *ctx)
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     CK(set_vec_smem<T>());
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused_vec<T, kVBY, 2, true, false>,
-                                                     32 * (kVBY + 1), VecLayout<T, kVBY, false>::bytes));
+    constexpr int BY = VecRows<T>::value;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused_vec<T, BY, 2, true, false>, 32 * (BY + 1),
+                                                     VecLayout<T, BY, false>::bytes));
     per = std::max(per, 1);
     const int *n = ctx->desc.n;
     const int xs = W - Lanes<T>::V;
     const int ntx = n[0] <= W ? 1 : 1 + (n[0] - W + xs - 1) / xs;
-    const int nty = (n[1] + kVBY - 1) / kVBY;
+    const int nty = (n[1] + BY - 1) / BY;
     long long nch = std::max(1LL, ((long long)per * nsm) / ((long long)ntx * nty));
     int chunk = (int)std::max(2LL, (n[2] + nch - 1) / nch);
     chunk = std::min(chunk, n[2]);
@@ -692,8 +705,9 @@ template <typename T> static int zero_walls(mmx_ctx *ctx)
 template <typename T, int NH, bool PMLK, bool GEN>
 static void launch_vec_v(mmx_ctx *ctx, const Fields<T> &f, const FusedIO<T> &io, int nsrc)
 {
-    k_fused_vec<T, kVBY, NH, PMLK, GEN><<<ctx->vec_grid, dim3(32, kVBY + 1), VecLayout<T, kVBY, GEN>::bytes,
-                                          ctx->stream>>>(
+    constexpr int BY = VecRows<T>::value;
+    k_fused_vec<T, BY, NH, PMLK, GEN><<<ctx->vec_grid, dim3(32, BY + 1), VecLayout<T, BY, GEN>::bytes,
+                                        ctx->stream>>>(
         ctx->g, f, io, (const Src<T> *)ctx->dsrc, nsrc, ctx->vec_chunk, ctx->vec_xstride);
 }
 
@@ -1061,17 +1075,12 @@ int mmx_set_materials(mmx_ctx *ctx, const double *eps_r, const double *sigma, co
         ctx->bz = ctx->hi[2] - ctx->lo[2];
         ctx->nb = (long long)ctx->bx * ctx->by * ctx->bz;
         int rc = MMX_OK;
-        for (int q = 0; q < 9 && !rc; q++) {
-            rc = box_alloc(ctx, &ctx->bM[q]);
-            if (!rc) rc = box_alloc(ctx, &ctx->bbeta[q]);
-            if (!rc) rc = box_alloc(ctx, &ctx->bdM[0][q]);
-            if (!rc) rc = box_alloc(ctx, &ctx->bdM[1][q]);
-        }
+        for (int q = 0; q < 9 && !rc; q++) rc = box_alloc(ctx, &ctx->bM[q]);
         for (int a = 0; a < 3 && !rc; a++) {
-            rc = box_alloc(ctx, &ctx->bCp[a]);
-            if (!rc) rc = box_alloc(ctx, &ctx->be0[a]);
-            if (!rc) rc = box_alloc(ctx, &ctx->bHit[0][a]);
+            rc = box_alloc(ctx, &ctx->bHit[0][a]);
             if (!rc) rc = box_alloc(ctx, &ctx->bHit[1][a]);
+            if (!rc) rc = box_alloc(ctx, &ctx->bHit2[0][a]);
+            if (!rc) rc = box_alloc(ctx, &ctx->bHit2[1][a]);
             if (!rc) rc = box_alloc(ctx, &ctx->bms[a]);
             if (!rc) rc = box_alloc(ctx, &ctx->bk1[a]);
             if (!rc) rc = box_alloc(ctx, &ctx->bk2[a]);
@@ -1079,6 +1088,15 @@ int mmx_set_materials(mmx_ctx *ctx, const double *eps_r, const double *sigma, co
         if (!rc && (ctx->nb >= (1LL << 30) || (long long)ctx->g.X * ctx->g.Y * (ctx->desc.n[2] + 1LL) >= (1LL << 32)))
             rc = fail(ctx, MMX_ERR_INVALID, "magnetic box or grid too large for 32-bit box indexing");
         if (!rc) rc = build_box_lists(ctx, Ms);
+        {
+            // per magnetic face records: 4 values of the storage type each
+            const size_t fb = (size_t)std::max(ctx->nmag, 1) * 4 * ctx->esz;
+            void **rec[5] = {&ctx->fcst, &ctx->fmn, &ctx->fbc, &ctx->fdm[0], &ctx->fdm[1]};
+            for (int q = 0; q < 5 && !rc; q++) {
+                rc = dalloc(ctx, rec[q], fb);
+                if (!rc) ctx->box_allocs.push_back(*rec[q]);
+            }
+        }
         if (rc) {
             free_box(ctx);
             return rc;

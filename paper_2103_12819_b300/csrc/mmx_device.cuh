@@ -92,16 +92,24 @@ template <typename T> struct Fields {
 // every side (so every neighbour a magnetic face reads lies inside), stored
 // box-locally with dims (bx, by, bz), element (i,j,k) at
 // (i-lo0) + bx*((j-lo1) + by*(k-lo2)).
+// Four values of one magnetic face, moved as one 16-byte (FP32) or two
+// 16-byte (FP64) accesses.
+template <typename T> struct alignas(4 * sizeof(T)) Q4 {
+    T x, y, z, w;
+};
+
 template <typename T> struct Box {
     int lo[3];
     int bx, by, bz;
     long long nb;
-    T *M[9];            // M^n per face family: M[3*fam + comp]
-    T *beta[9];         // -kappa M^n x Heff^n
-    T *dM[2][9];        // iterates of DeltaM = M^r - M^n
-    T *Cp[3];           // H^n - dt/(2 mu0) curl E
-    T *e0[3];           // Ms^2 - |M^n|^2 (formed in FP64)
-    T *Hit[2][3];       // H iterates
+    T *M[9];            // M per face family: M[3*fam + comp] (box layout)
+    T *Hit[2][3];       // H iterates (box layout; neighbours read them)
+    T *Hit2[2][3];      // H iterates of the second half step of a launch
+    // per magnetic face, in the order of the magnetic-face list:
+    const Q4<T> *cst;   // Ms, k1, k2
+    Q4<T> *mn;          // M^n, e0 = Ms^2 - |M^n|^2
+    Q4<T> *bc;          // beta = -kappa M^n x Heff^n, C' = H^n - dt/(2 mu0) curl E
+    Q4<T> *dm[2];       // iterates of DeltaM = M^r - M^n
     const T *ms[3];     // Ms on faces
     const T *k1[3];     // order 2: kappa = mu0|gamma|dt/4; order 1: (dt/2) mu0 gamma_L
     const T *k2[3];     // order 2: alpha/Ms;               order 1: (dt/2) alpha mu0 gamma_L / Ms
@@ -261,9 +269,11 @@ __device__ __forceinline__ void e_edge(const Geo &g, const Fields<T> &f, int c, 
 // H^(n+1/2) = H^n - dt/(2 mu) curl E (Eq. iterate_H with mu for mu0, Ms = 0),
 // PEC wall faces zero, time-centred z-PML split.  Reads Hin, writes Hout
 // (the same array for the streaming kernel).
+// The same with the old value hn passed in (the box kernel's second half
+// step takes it from its box-local iterate).
 template <typename T>
-__device__ __forceinline__ T h_face_nonmag(const Geo &g, const Fields<T> &f, int d, int i, int j, int k,
-                                           const T *Hin)
+__device__ __forceinline__ T h_face_nonmag_val(const Geo &g, const Fields<T> &f, int d, int i, int j, int k,
+                                               T hn)
 {
     size_t q = gidx(g, i, j, k);
     int ix[3] = {i, j, k};
@@ -278,15 +288,22 @@ __device__ __forceinline__ T h_face_nonmag(const Geo &g, const Fields<T> &f, int
     if (d < 2 && pml_h_plane(g, k)) {
         T h = f.dampH[k];
         T hz = f.Hzp[d][q];
-        T hr = Hin[q] - hz;
+        T hr = hn - hz;
         T hz1 = (hz * h - fh * zp) * h;
         T hr1 = hr - fh * rest;
         f.Hzp[d][q] = hz1;
         v = hr1 + hz1;
     } else {
-        v = Hin[q] - fh * (rest + zp);
+        v = hn - fh * (rest + zp);
     }
     return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T h_face_nonmag(const Geo &g, const Fields<T> &f, int d, int i, int j, int k,
+                                           const T *Hin)
+{
+    return h_face_nonmag_val(g, f, d, i, j, k, Hin[gidx(g, i, j, k)]);
 }
 
 // ------------------------------------------------ LLG: one iterate

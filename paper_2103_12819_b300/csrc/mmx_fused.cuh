@@ -147,7 +147,7 @@ template <typename T, int BY, bool GEN> struct VecLayout {
 };
 
 template <typename T, int BY, int NH, bool PMLK, bool GEN>
-__global__ void __launch_bounds__(32 * (BY + 1), 2)
+__global__ void __launch_bounds__(32 * (BY + 1), BY <= 8 ? 2 : 1)
     k_fused_vec(const __grid_constant__ Geo g, const __grid_constant__ Fields<T> f,
                 const __grid_constant__ FusedIO<T> io, const Src<T> *__restrict__ src, int nsrc, int chunk,
                 int xstride)

@@ -198,6 +198,22 @@ __global__ void k_box_init_m(const Geo g, Box<T> b, int d, const double *__restr
     for (int c = 0; c < 3; c++) b.M[3 * d + c][l] = (T)m[c];
 }
 
+// Per-magnetic-face constants in list order: Ms, k1, k2 from the box arrays.
+template <typename T> __global__ void k_box_cst(Box<T> b)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= b.nmag) return;
+    const int4 e = b.mag[t];
+    const unsigned l = (unsigned)e.x & 0x3fffffffu;
+    const int d = (int)((unsigned)e.x >> 30);
+    Q4<T> c;
+    c.x = b.ms[d][l];
+    c.y = b.k1[d][l];
+    c.z = b.k2[d][l];
+    c.w = T(0);
+    const_cast<Q4<T> *>(b.cst)[t] = c;
+}
+
 // ============================================================ field copies
 
 // Gather a padded device field (or a box-local M component) into a compact
@@ -419,186 +435,243 @@ __device__ __forceinline__ void h_vector(const Geo &g, const Box<T> &b, T *const
     }
 }
 
-// First iterate on one magnetic face of family D: forms
-// Cp = H^n - dt/(2 mu0) curl E, beta = -kappa M^n x H_eff^n, e0 and
-// DeltaM^1 from H^n; returns max_c |DeltaM^1_c| / Ms.
-template <int D, typename T>
+template <typename T> __device__ __forceinline__ Q4<T> q4_load(const Q4<T> *p)
+{
+    return *p;
+}
+
+// Phase 0 on a magnetic face of family D (list position t): forms
+// C' = H^n - dt/(2 mu0) curl E, beta = -kappa M^n x H_eff^n, e0 and the first
+// iterate DeltaM^1 from H^n, which is the global H (SECOND false) or the
+// previous half step's box-local iterate Hp (SECOND true, with M^n the
+// previous M^n plus its converged increment dmp).  Writes the face's
+// records and H^1 into Hw; returns max_c |DeltaM^1_c| / Ms.
+template <int D, bool SECOND, typename T>
 __device__ __forceinline__ T mag_first(const Geo &g, const Fields<T> &f, const Box<T> &b, T *const Hin[3],
-                                       const FaceOf &fo, const T h0[3])
+                                       T *const Hp[3], const Q4<T> *dmp, T *const Hw[3], const FaceOf &fo,
+                                       int t, const T h0[3])
 {
     const unsigned l = fo.l;
-    const T Ms = b.ms[D][l];
+    const Q4<T> cs = q4_load(b.cst + t);
+    const T Ms = cs.x, k1 = cs.y, k2 = cs.z;
     T rest, zp;
     curl_e(g, f.E, f.inv_d, D, fo.i, fo.j, fo.k, rest, zp);
-    const T cp = Hin[D][gidx32(g, fo.i, fo.j, fo.k)] - b.cfar * (rest + zp);
-    const T Mn[3] = {b.M[3 * D][l], b.M[3 * D + 1][l], b.M[3 * D + 2][l]};
-    const T e0 = norm_defect(Ms, Mn[0], Mn[1], Mn[2]);
+    T Mn[3], hn;
     T h[3], heff[3];
-    h_vector<D>(g, b, Hin, Hin, 0, fo.i, fo.j, fo.k, h);
+    if (SECOND) {
+        const Q4<T> m0 = q4_load(b.mn + t);
+        const Q4<T> d0 = q4_load(dmp + t);
+        Mn[0] = m0.x + d0.x;
+        Mn[1] = m0.y + d0.y;
+        Mn[2] = m0.z + d0.z;
+        hn = Hp[D][l];
+        h_vector<D>(g, b, Hp, Hp, 1, fo.i, fo.j, fo.k, h);
+    } else {
+        Mn[0] = b.M[3 * D][l];
+        Mn[1] = b.M[3 * D + 1][l];
+        Mn[2] = b.M[3 * D + 2][l];
+        hn = Hin[D][gidx32(g, fo.i, fo.j, fo.k)];
+        h_vector<D>(g, b, Hin, Hin, 0, fo.i, fo.j, fo.k, h);
+    }
+    const T cp = hn - b.cfar * (rest + zp);
+    const T e0 = norm_defect(Ms, Mn[0], Mn[1], Mn[2]);
 #pragma unroll
     for (int c = 0; c < 3; c++) heff[c] = h0[c] + h[c];
     T dM[3], dMh;
-    const T k1 = b.k1[D][l], k2 = b.k2[D][l];
+    Q4<T> bq;
     if (b.order == 2) {
         const T beta[3] = {-k1 * (Mn[1] * heff[2] - Mn[2] * heff[1]), -k1 * (Mn[2] * heff[0] - Mn[0] * heff[2]),
                            -k1 * (Mn[0] * heff[1] - Mn[1] * heff[0])};
         llg_iterate(Mn, beta, heff, k1, k2, Ms, e0, D, dM, dMh);
-#pragma unroll
-        for (int c = 0; c < 3; c++) b.beta[3 * D + c][l] = beta[c];
+        bq.x = beta[0];
+        bq.y = beta[1];
+        bq.z = beta[2];
     } else {
         llg_euler(Mn, heff, k1, k2, Ms, e0, D, dM, dMh);
+        bq.x = bq.y = bq.z = T(0);
     }
-    b.Cp[D][l] = cp;
-    b.e0[D][l] = e0;
+    bq.w = cp;
+    b.bc[t] = bq;
+    Q4<T> mq;
+    mq.x = Mn[0];
+    mq.y = Mn[1];
+    mq.z = Mn[2];
+    mq.w = e0;
+    b.mn[t] = mq;
+    Q4<T> dq;
+    dq.x = dM[0];
+    dq.y = dM[1];
+    dq.z = dM[2];
+    dq.w = T(0);
+    b.dm[1][t] = dq;
     const bool wall = wall_node(g, D, D == 0 ? fo.i : D == 1 ? fo.j : fo.k);
-    b.Hit[1][D][l] = wall ? T(0) : cp - dMh;
-    T amax = T(0);
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        b.dM[1][3 * D + c][l] = dM[c];
-        amax = max(amax, abs(dM[c]));
-    }
-    return amax / Ms;
+    Hw[D][l] = wall ? T(0) : cp - dMh;
+    return max(abs(dM[0]), max(abs(dM[1]), abs(dM[2]))) / Ms;
 }
 
 // Phase 0 on a non-magnetic face of family D: its final H in both iterate
-// buffers.
-template <int D, typename T>
-__device__ __forceinline__ void non_first(const Geo &g, const Fields<T> &f, const Box<T> &b, T *const Hin[3],
-                                          const FaceOf &fo)
+// buffers W0, W1.
+template <int D, bool SECOND, typename T>
+__device__ __forceinline__ void non_first(const Geo &g, const Fields<T> &f, T *const Hin[3], T *const Hp[3],
+                                          T *const W0[3], T *const W1[3], const FaceOf &fo)
 {
-    const T v = h_face_nonmag(g, f, D, fo.i, fo.j, fo.k, Hin[D]);
-    b.Hit[0][D][fo.l] = v;
-    b.Hit[1][D][fo.l] = v;
+    const T hn = SECOND ? Hp[D][fo.l] : Hin[D][gidx32(g, fo.i, fo.j, fo.k)];
+    const T v = h_face_nonmag_val(g, f, D, fo.i, fo.j, fo.k, hn);
+    W0[D][fo.l] = v;
+    W1[D][fo.l] = v;
 }
 
 // Iterate r >= 2 on one magnetic face of family D from the neighbours'
-// iterate r-1 (buffers pr -> cr); returns max_c |DeltaM^r_c - DeltaM^(r-1)_c| / Ms.
+// iterate r-1 (Hprev, dM buffer pr -> cr); returns
+// max_c |DeltaM^r_c - DeltaM^(r-1)_c| / Ms.
 template <int D, typename T>
-__device__ __forceinline__ T mag_next(const Geo &g, const Box<T> &b, const FaceOf &fo, T *const Hprev[3],
-                                      int pr, int cr, const T h0[3])
+__device__ __forceinline__ T mag_next(const Geo &g, const Box<T> &b, const FaceOf &fo, int t, T *const Hprev[3],
+                                      T *const Hcur[3], int pr, int cr, const T h0[3])
 {
     const unsigned l = fo.l;
-    const T Ms = b.ms[D][l];
-    const T Mn[3] = {b.M[3 * D][l], b.M[3 * D + 1][l], b.M[3 * D + 2][l]};
-    const T beta[3] = {b.beta[3 * D][l], b.beta[3 * D + 1][l], b.beta[3 * D + 2][l]};
-    const T prev[3] = {b.dM[pr][3 * D][l], b.dM[pr][3 * D + 1][l], b.dM[pr][3 * D + 2][l]};
-    const T k1 = b.k1[D][l], k2 = b.k2[D][l], e0 = b.e0[D][l], cp = b.Cp[D][l];
+    const Q4<T> cs = q4_load(b.cst + t);
+    const Q4<T> mq = q4_load(b.mn + t);
+    const Q4<T> bq = q4_load(b.bc + t);
+    const Q4<T> pq = q4_load(b.dm[pr] + t);
+    const T Ms = cs.x, k1 = cs.y, k2 = cs.z;
+    const T Mn[3] = {mq.x, mq.y, mq.z};
+    const T beta[3] = {bq.x, bq.y, bq.z};
     T h[3], heff[3];
     h_vector<D>(g, b, Hprev, Hprev, 1, fo.i, fo.j, fo.k, h);
 #pragma unroll
     for (int c = 0; c < 3; c++) heff[c] = h0[c] + h[c];
     T dM[3], dMh;
-    llg_iterate(Mn, beta, heff, k1, k2, Ms, e0, D, dM, dMh);
+    llg_iterate(Mn, beta, heff, k1, k2, Ms, mq.w, D, dM, dMh);
     const bool wall = wall_node(g, D, D == 0 ? fo.i : D == 1 ? fo.j : fo.k);
-    b.Hit[cr][D][l] = wall ? T(0) : cp - dMh;
-    T amax = T(0);
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        b.dM[cr][3 * D + c][l] = dM[c];
-        amax = max(amax, abs(dM[c] - prev[c]));
-    }
-    return amax / Ms;
+    Hcur[D][l] = wall ? T(0) : bq.w - dMh;
+    Q4<T> dq;
+    dq.x = dM[0];
+    dq.y = dM[1];
+    dq.z = dM[2];
+    dq.w = T(0);
+    b.dm[cr][t] = dq;
+    return max(abs(dM[0] - pq.x), max(abs(dM[1] - pq.y), abs(dM[2] - pq.z))) / Ms;
 }
 
-// Final H and M^(n+1/2) on one magnetic face of family D; returns false if a
-// written value is not finite.
+// Final H and M^(n+1/2) on one magnetic face of family D; returns false if
+// a written value is not finite.
 template <int D, typename T>
-__device__ __forceinline__ bool mag_store(const Geo &g, const Box<T> &b, const FaceOf &fo, T *const Hout[3],
-                                          int fr)
+__device__ __forceinline__ bool mag_store(const Geo &g, const Box<T> &b, const FaceOf &fo, int t,
+                                          T *const Hfin[3], T *const Hout[3], int fr)
 {
     const unsigned l = fo.l;
-    const T v = b.Hit[fr][D][l];
+    const T v = Hfin[D][l];
     Hout[D][gidx32(g, fo.i, fo.j, fo.k)] = v;
-    bool ok = isfinite(v);
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        const T m = b.M[3 * D + c][l] + b.dM[fr][3 * D + c][l];
-        b.M[3 * D + c][l] = m;
-        ok &= isfinite(m);
-    }
-    return ok;
+    const Q4<T> mq = q4_load(b.mn + t);
+    const Q4<T> dq = q4_load(b.dm[fr] + t);
+    const T m0 = mq.x + dq.x, m1 = mq.y + dq.y, m2 = mq.z + dq.z;
+    b.M[3 * D][l] = m0;
+    b.M[3 * D + 1][l] = m1;
+    b.M[3 * D + 2][l] = m2;
+    return isfinite(v) && isfinite(m0) && isfinite(m1) && isfinite(m2);
 }
 
 // One H/M half step on every face of the magnetic box (Sec. 3.2.2 Step 1 or
-// Step 3) with the E in f.E, from H^n in Hin to H^(n+1/2) in Hout (the same
-// arrays for the in-place plain path).  Work comes from two lists built when
-// the materials are set, each ordered by family: the magnetic faces and the
-// other faces of the box.  Phase 0 gives non-magnetic faces their final H and
-// forms the first iterate on magnetic faces; each further iteration r
-// updates every magnetic face from the neighbours' iterate r-1 (Jacobi),
-// reduces max |DeltaM^r - DeltaM^(r-1)|/Ms into res[r] (warp shuffle, block
-// max, one atomicMax on the FP64 bit pattern per block) and meets at a
-// bounded grid barrier; all blocks then read res[r] and stop together at the
-// first r with res[r] < tol (or at max_iter, latching kErrNotConverged).
-// Returns false if a barrier timed out.
-template <typename T>
-__device__ bool hm_half_step(const Geo &g, const Fields<T> &f, const Box<T> &b, T *const Hin[3],
-                             T *const Hout[3], unsigned long long *res)
+// Step 3) with the E in f.E.  Work comes from two lists built when the
+// materials are set, each ordered by family: the magnetic faces and the
+// other faces of the box; the same thread takes the same faces in every
+// phase.  Phase 0 gives non-magnetic faces their final H and forms the
+// first iterate on magnetic faces; each further iteration r updates every
+// magnetic face from the neighbours' iterate r-1 (Jacobi), reduces
+// max |DeltaM^r - DeltaM^(r-1)|/Ms into res[r] (warp shuffle, block max, one
+// atomicMax on the FP64 bit pattern per block) and meets at a bounded grid
+// barrier; all blocks then read res[r] and stop together at the first r with
+// res[r] < tol (or at max_iter, latching kErrNotConverged).
+//   SECOND false: H^n and M^n come from the global H (Hin) and the box M.
+//   SECOND true:  they come from the previous half step of this launch,
+//                 which ended in iterate buffer fprev without writing back.
+//   WRITE true:   H^(n+1/2) goes to the global Hout and M^(n+1/2) to the box
+//                 M; otherwise both stay in the iterate buffers.
+// Returns the final iterate parity, or -1 if a barrier timed out.
+template <bool SECOND, bool WRITE, typename T>
+__device__ int hm_half_step(const Geo &g, const Fields<T> &f, const Box<T> &b, T *const Hin[3], T *const Hout[3],
+                            int fprev, unsigned long long *res)
 {
     const int stride = gridDim.x * blockDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
     const T h0[3] = {(T)b.h0[0], (T)b.h0[1], (T)b.h0[2]};
+    // iterate buffers of this half step; H^n of a second half step
+    T *const W0[3] = {SECOND ? b.Hit2[0][0] : b.Hit[0][0], SECOND ? b.Hit2[0][1] : b.Hit[0][1],
+                      SECOND ? b.Hit2[0][2] : b.Hit[0][2]};
+    T *const W1[3] = {SECOND ? b.Hit2[1][0] : b.Hit[1][0], SECOND ? b.Hit2[1][1] : b.Hit[1][1],
+                      SECOND ? b.Hit2[1][2] : b.Hit[1][2]};
+    T *const Hp[3] = {b.Hit[fprev & 1][0], b.Hit[fprev & 1][1], b.Hit[fprev & 1][2]};
+    const Q4<T> *dmp = b.dm[fprev & 1];
 
     // ---- phase 0: r = 1
     for (int t = t0; t < b.nnon; t += stride) {
         const FaceOf fo = face_of(b.nonmag[t]);
         if (fo.d == 0)
-            non_first<0>(g, f, b, Hin, fo);
+            non_first<0, SECOND>(g, f, Hin, Hp, W0, W1, fo);
         else if (fo.d == 1)
-            non_first<1>(g, f, b, Hin, fo);
+            non_first<1, SECOND>(g, f, Hin, Hp, W0, W1, fo);
         else
-            non_first<2>(g, f, b, Hin, fo);
+            non_first<2, SECOND>(g, f, Hin, Hp, W0, W1, fo);
     }
     T rmax = T(0);
-    for (int t = t0; t < b.nmag; t += stride) {
-        const FaceOf fo = face_of(b.mag[t]);
-        T rv = fo.d == 0   ? mag_first<0>(g, f, b, Hin, fo, h0)
-               : fo.d == 1 ? mag_first<1>(g, f, b, Hin, fo, h0)
-                           : mag_first<2>(g, f, b, Hin, fo, h0);
-        rmax = max(rmax, rv);
+    {
+        int4 nx = t0 < b.nmag ? b.mag[t0] : make_int4(0, 0, 0, 0);
+        for (int t = t0; t < b.nmag; t += stride) {
+            const FaceOf fo = face_of(nx);
+            if (t + stride < b.nmag) nx = b.mag[t + stride];
+            T rv = fo.d == 0   ? mag_first<0, SECOND>(g, f, b, Hin, Hp, dmp, W1, fo, t, h0)
+                   : fo.d == 1 ? mag_first<1, SECOND>(g, f, b, Hin, Hp, dmp, W1, fo, t, h0)
+                               : mag_first<2, SECOND>(g, f, b, Hin, Hp, dmp, W1, fo, t, h0);
+            rmax = max(rmax, rv);
+        }
     }
     rmax = block_max(rmax);
     publish_residual(&res[1], rmax);
-    if (!grid_barrier(b.bar, b.err)) return false;
+    if (!grid_barrier(b.bar, b.err)) return -1;
 
     int r = 1;
     bool conv = residual_below(&res[1], b.tol) || b.order == 1;
     while (!conv && r < b.max_iter) {
         r++;
         const int pr = (r - 1) & 1, cr = r & 1;
-        T *const Hprev[3] = {b.Hit[pr][0], b.Hit[pr][1], b.Hit[pr][2]};
+        T *const Hprev[3] = {pr ? W1[0] : W0[0], pr ? W1[1] : W0[1], pr ? W1[2] : W0[2]};
+        T *const Hcur[3] = {cr ? W1[0] : W0[0], cr ? W1[1] : W0[1], cr ? W1[2] : W0[2]};
         rmax = T(0);
+        int4 nx = t0 < b.nmag ? b.mag[t0] : make_int4(0, 0, 0, 0);
         for (int t = t0; t < b.nmag; t += stride) {
-            const FaceOf fo = face_of(b.mag[t]);
-            T rv = fo.d == 0   ? mag_next<0>(g, b, fo, Hprev, pr, cr, h0)
-                   : fo.d == 1 ? mag_next<1>(g, b, fo, Hprev, pr, cr, h0)
-                               : mag_next<2>(g, b, fo, Hprev, pr, cr, h0);
+            const FaceOf fo = face_of(nx);
+            if (t + stride < b.nmag) nx = b.mag[t + stride];
+            T rv = fo.d == 0   ? mag_next<0>(g, b, fo, t, Hprev, Hcur, pr, cr, h0)
+                   : fo.d == 1 ? mag_next<1>(g, b, fo, t, Hprev, Hcur, pr, cr, h0)
+                               : mag_next<2>(g, b, fo, t, Hprev, Hcur, pr, cr, h0);
             rmax = max(rmax, rv);
         }
         rmax = block_max(rmax);
         publish_residual(&res[r], rmax);
-        if (!grid_barrier(b.bar, b.err)) return false;
+        if (!grid_barrier(b.bar, b.err)) return -1;
         conv = residual_below(&res[r], b.tol);
     }
 
-    // ---- write back H (all box faces) and M (magnetic faces)
     const int fr = r & 1;
-    bool ok = true;
-    for (int t = t0; t < b.nnon; t += stride) {
-        const FaceOf fo = face_of(b.nonmag[t]);
-        const T v = b.Hit[fr][fo.d][fo.l];
-        T *const Ho = fo.d == 0 ? Hout[0] : fo.d == 1 ? Hout[1] : Hout[2];
-        Ho[gidx32(g, fo.i, fo.j, fo.k)] = v;
-        ok &= isfinite(v);
+    if (WRITE) {
+        // ---- write back H (all box faces) and M (magnetic faces)
+        T *const Hfin[3] = {fr ? W1[0] : W0[0], fr ? W1[1] : W0[1], fr ? W1[2] : W0[2]};
+        bool ok = true;
+        for (int t = t0; t < b.nnon; t += stride) {
+            const FaceOf fo = face_of(b.nonmag[t]);
+            const T v = Hfin[fo.d][fo.l];
+            T *const Ho = fo.d == 0 ? Hout[0] : fo.d == 1 ? Hout[1] : Hout[2];
+            Ho[gidx32(g, fo.i, fo.j, fo.k)] = v;
+            ok &= isfinite(v);
+        }
+        for (int t = t0; t < b.nmag; t += stride) {
+            const FaceOf fo = face_of(b.mag[t]);
+            ok &= fo.d == 0   ? mag_store<0>(g, b, fo, t, Hfin, Hout, fr)
+                  : fo.d == 1 ? mag_store<1>(g, b, fo, t, Hfin, Hout, fr)
+                              : mag_store<2>(g, b, fo, t, Hfin, Hout, fr);
+        }
+        if (!ok) atomicOr(b.err, kErrNonFinite);
     }
-    for (int t = t0; t < b.nmag; t += stride) {
-        const FaceOf fo = face_of(b.mag[t]);
-        ok &= fo.d == 0   ? mag_store<0>(g, b, fo, Hout, fr)
-              : fo.d == 1 ? mag_store<1>(g, b, fo, Hout, fr)
-                          : mag_store<2>(g, b, fo, Hout, fr);
-    }
-    if (!ok) atomicOr(b.err, kErrNonFinite);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (!conv && b.order == 2) atomicOr(b.err, kErrNotConverged);
         unsigned long long hs = *b.halfsteps;
@@ -606,7 +679,7 @@ __device__ bool hm_half_step(const Geo &g, const Fields<T> &f, const Box<T> &b, 
         *b.halfsteps = hs + 1;
         *b.last_res = b.order == 2 ? __longlong_as_double((long long)res[r]) : 0.0;
     }
-    return true;
+    return fr;
 }
 
 // Cooperative launch over the magnetic box: nsub = 1 runs one H/M half step
@@ -625,10 +698,14 @@ __global__ void __launch_bounds__(256) k_hm_box(const __grid_constant__ Geo g,
         unsigned long long *other = b.res + 2 * (1 - slot) * W;
         for (int r = threadIdx.x; r < 2 * W; r += blockDim.x) other[r] = 0ull;
     }
-    if (!hm_half_step(g, f, b, f.H, Hout.p, b.res + 2 * slot * W)) return;
     if (nsub == 2) {
-        if (!grid_barrier(b.bar, b.err)) return;
-        hm_half_step(g, f, b, Hout.p, Hout.p, b.res + (2 * slot + 1) * W);
+        // two half steps with one E; the first keeps its result in the
+        // iterate buffers, the second starts from there and writes back
+        const int fr = hm_half_step<false, false>(g, f, b, f.H, Hout.p, 0, b.res + 2 * slot * W);
+        if (fr < 0) return;
+        hm_half_step<true, true>(g, f, b, f.H, Hout.p, fr, b.res + (2 * slot + 1) * W);
+    } else {
+        hm_half_step<false, true>(g, f, b, f.H, Hout.p, 0, b.res + 2 * slot * W);
     }
 }
 
