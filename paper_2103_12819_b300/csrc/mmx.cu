@@ -21,9 +21,11 @@ using namespace mmx;
 namespace {
 
 // Kernel kinds timed by the optional profiler.
-enum KernelKind { KK_HM_BOX = 0, KK_H_UPDATE, KK_E_UPDATE, KK_HARD, KK_FUSED, KK_FUSED_VEC, KK_ZERO_WALLS, KK_COUNT };
-const char *const kKernelNames[KK_COUNT] = {"hm_box",   "h_update",     "e_update",  "hard_source",
-                                            "fused_eh", "fused_eh_vec", "zero_walls"};
+enum KernelKind {
+    KK_HM_BOX = 0, KK_H_UPDATE, KK_E_UPDATE, KK_HARD, KK_FUSED, KK_FUSED_VEC, KK_ZERO_WALLS, KK_M_SYNC, KK_COUNT
+};
+const char *const kKernelNames[KK_COUNT] = {"hm_box",   "h_update",     "e_update",   "hard_source",
+                                            "fused_eh", "fused_eh_vec", "zero_walls", "box_m_sync"};
 
 struct ProfRec {
     int kind;
@@ -74,7 +76,7 @@ struct mmx_ctx {
 
     // control words (device)
     unsigned long long *res = nullptr;     // [4][kMaxIter+1]
-    unsigned int *bar = nullptr;           // [2]
+    unsigned long long *bar = nullptr;     // grid-barrier arrival count
     int *iterlog = nullptr;                // [kIterLogCap]
     unsigned long long *halfsteps = nullptr;
     double *last_res = nullptr;
@@ -556,6 +558,16 @@ constexpr int kFBX = 32, kFBY = 8;   // fused block: 31 x 7 output columns + hal
 // z chunk of the fused kernel: as many chunks as fill one resident wave of
 // blocks (each block marches its whole chunk, so a second wave would double
 // the time).
+template <typename T> static int box_m_sync(mmx_ctx *ctx, int to_rec)
+{
+    if (!ctx->magnetic || ctx->nmag == 0) return MMX_OK;
+    prof_begin(ctx, KK_M_SYNC);
+    k_box_m_sync<T><<<(ctx->nmag + 255) / 256, 256, 0, ctx->stream>>>(make_box<T>(ctx), to_rec);
+    prof_end(ctx);
+    CK(cudaGetLastError());
+    return MMX_OK;
+}
+
 template <typename T> static int plan_fused(mmx_ctx *ctx)
 {
     int dev = 0, nsm = 0, per = 0;
@@ -868,8 +880,7 @@ static int read_status(mmx_ctx *ctx)
         CK(cudaStreamSynchronize(ctx->stream));
     }
     if (w & kErrTimeout) {
-        unsigned int zz[2] = {0, 0};
-        CK(cudaMemcpyAsync(ctx->bar, zz, sizeof zz, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned long long), ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         return fail(ctx, MMX_ERR_TIMEOUT, "a device-side wait gave up");
     }
@@ -942,7 +953,7 @@ int mmx_create(const mmx_grid_desc *desc, void *cuda_stream, mmx_ctx **out)
             if (!rc) rc = dalloc(ctx, &ctx->Hzp[a], fb);
         }
     if (!rc) rc = dalloc(ctx, (void **)&ctx->res, 4 * (kMaxIter + 1) * sizeof(unsigned long long));
-    if (!rc) rc = dalloc(ctx, (void **)&ctx->bar, 2 * sizeof(unsigned int));
+    if (!rc) rc = dalloc(ctx, (void **)&ctx->bar, sizeof(unsigned long long));
     if (!rc) rc = dalloc(ctx, (void **)&ctx->iterlog, kIterLogCap * sizeof(int));
     if (!rc) rc = dalloc(ctx, (void **)&ctx->halfsteps, sizeof(unsigned long long));
     if (!rc) rc = dalloc(ctx, (void **)&ctx->last_res, sizeof(double));
@@ -1251,12 +1262,20 @@ int mmx_step(mmx_ctx *ctx, int nsteps)
 {
     if (!ctx || !ctx->E[0] || nsteps < 0) return MMX_ERR_INVALID;
     if (nsteps == 0) return MMX_OK;
-    CK(cudaMemsetAsync(ctx->bar, 0, 2 * sizeof(unsigned int), ctx->stream));
+    CK(cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned long long), ctx->stream));
     bool hard = false;
     for (auto &q : ctx->src) hard |= q.kind >= 2;
+    const bool fp64 = is_fp64(ctx);
+    // M lives in the magnetic-face records while stepping and in the box
+    // arrays between calls (where the API reads and writes it)
+    int rc = fp64 ? box_m_sync<double>(ctx, 1) : box_m_sync<float>(ctx, 1);
+    if (rc) return rc;
     if (ctx->path == MMX_PATH_FUSED && !hard)
-        return is_fp64(ctx) ? step_fused<double>(ctx, nsteps) : step_fused<float>(ctx, nsteps);
-    return is_fp64(ctx) ? step_plain<double>(ctx, nsteps) : step_plain<float>(ctx, nsteps);
+        rc = fp64 ? step_fused<double>(ctx, nsteps) : step_fused<float>(ctx, nsteps);
+    else
+        rc = fp64 ? step_plain<double>(ctx, nsteps) : step_plain<float>(ctx, nsteps);
+    int rc2 = fp64 ? box_m_sync<double>(ctx, 0) : box_m_sync<float>(ctx, 0);
+    return rc ? rc : rc2;
 }
 
 int mmx_sync(mmx_ctx *ctx)

@@ -119,7 +119,7 @@ template <typename T> struct Box {
     int order;
     T cfar;             // dt/(2 mu0)
     unsigned long long *res;   // [2][kMaxIter+1] residual bit patterns
-    unsigned int *bar;         // grid barrier: [0] count, [1] generation
+    unsigned long long *bar;   // grid barrier: monotonic arrival count
     int *iterlog;
     unsigned long long *halfsteps;
     double *last_res;

@@ -214,6 +214,31 @@ template <typename T> __global__ void k_box_cst(Box<T> b)
     const_cast<Q4<T> *>(b.cst)[t] = c;
 }
 
+// M between the box arrays (read and written through the API) and the
+// magnetic-face records (used while stepping): to_rec copies box -> records,
+// otherwise records -> box.
+template <typename T> __global__ void k_box_m_sync(Box<T> b, int to_rec)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= b.nmag) return;
+    const int4 e = b.mag[t];
+    const unsigned l = (unsigned)e.x & 0x3fffffffu;
+    const int d = (int)((unsigned)e.x >> 30);
+    if (to_rec) {
+        Q4<T> q;
+        q.x = b.M[3 * d][l];
+        q.y = b.M[3 * d + 1][l];
+        q.z = b.M[3 * d + 2][l];
+        q.w = T(0);
+        b.mn[t] = q;
+    } else {
+        const Q4<T> q = b.mn[t];
+        b.M[3 * d][l] = q.x;
+        b.M[3 * d + 1][l] = q.y;
+        b.M[3 * d + 2][l] = q.z;
+    }
+}
+
 // ============================================================ field copies
 
 // Gather a padded device field (or a box-local M component) into a compact
@@ -315,32 +340,31 @@ __global__ void k_hard(const Geo g, Ptr3<T> F, const Src<T> *__restrict__ src, i
 
 // ================================================== magnetic box kernel
 
-// Bounded grid-wide barrier for a cooperative launch (all blocks resident).
-// Returns false (and latches kErrTimeout) if the others did not arrive
-// within ~2^31 clock cycles.
-__device__ __forceinline__ bool grid_barrier(unsigned int *bar, int *err)
+// Grid barrier on one monotonic 64-bit arrival counter.  Thread 0 of each
+// block fences the block's writes and adds 1; the barrier round a block is
+// in completes when the counter reaches the next multiple of gridDim.x,
+// which the block derives from the value its own add returned, so no reset
+// or generation word is needed.  The wait is bounded (~2^31 cycles): on
+// expiry the block latches kErrTimeout and returns false.
+__device__ __forceinline__ bool grid_barrier(unsigned long long *bar, int *err)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned int *vgen = bar + 1;
-        unsigned int gen = *vgen;
+        const unsigned long long nb = gridDim.x;
         __threadfence();
-        unsigned int arrived = atomicAdd(bar, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            long long t0 = clock64();
-            while (*vgen == gen) {
-                __nanosleep(64);
-                if (clock64() - t0 > (1LL << 31)) {
-                    atomicOr(err, kErrTimeout);
-                    ok = 0;
-                    break;
-                }
+        const unsigned long long old = atomicAdd(bar, 1ull);
+        const unsigned long long target = (old / nb + 1) * nb;
+        const long long t0 = clock64();
+        for (;;) {
+            unsigned long long cur;
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(cur) : "l"(bar) : "memory");
+            if (cur >= target) break;
+            if (clock64() - t0 > (1LL << 31)) {
+                atomicOr(err, kErrTimeout);
+                ok = 0;
+                break;
             }
         }
         __threadfence();
@@ -440,72 +464,81 @@ template <typename T> __device__ __forceinline__ Q4<T> q4_load(const Q4<T> *p)
     return *p;
 }
 
-// Phase 0 on a magnetic face of family D (list position t): forms
-// C' = H^n - dt/(2 mu0) curl E, beta = -kappa M^n x H_eff^n, e0 and the first
-// iterate DeltaM^1 from H^n, which is the global H (SECOND false) or the
-// previous half step's box-local iterate Hp (SECOND true, with M^n the
-// previous M^n plus its converged increment dmp).  Writes the face's
-// records and H^1 into Hw; returns max_c |DeltaM^1_c| / Ms.
-template <int D, bool SECOND, typename T>
-__device__ __forceinline__ T mag_first(const Geo &g, const Fields<T> &f, const Box<T> &b, T *const Hin[3],
-                                       T *const Hp[3], const Q4<T> *dmp, T *const Hw[3], const FaceOf &fo,
-                                       int t, const T h0[3])
+template <typename T> __device__ __forceinline__ Q4<T> q4(T x, T y, T z, T w)
 {
-    const unsigned l = fo.l;
-    const Q4<T> cs = q4_load(b.cst + t);
-    const T Ms = cs.x, k1 = cs.y, k2 = cs.z;
-    T rest, zp;
-    curl_e(g, f.E, f.inv_d, D, fo.i, fo.j, fo.k, rest, zp);
-    T Mn[3], hn;
-    T h[3], heff[3];
+    Q4<T> q;
+    q.x = x;
+    q.y = y;
+    q.z = z;
+    q.w = w;
+    return q;
+}
+
+// Everything phase 0 reads for one magnetic face.
+template <typename T> struct FirstIn {
+    Q4<T> cs;       // Ms, k1, k2
+    T Mn[3];
+    T hn, rest, zp;
+    T h[3];
+};
+
+// Loads of phase 0 on a magnetic face of family D (list position t): H^n is
+// the global H (SECOND false) or the previous half step's box-local iterate
+// Hp (SECOND true); M^n is the face record, plus the previous half step's
+// converged increment dmp when SECOND.
+template <int D, bool SECOND, typename T>
+__device__ __forceinline__ void first_load(const Geo &g, const Fields<T> &f, const Box<T> &b, T *const Hin[3],
+                                           T *const Hp[3], const Q4<T> *dmp, const FaceOf &fo, int t,
+                                           FirstIn<T> &in)
+{
+    in.cs = q4_load(b.cst + t);
+    curl_e(g, f.E, f.inv_d, D, fo.i, fo.j, fo.k, in.rest, in.zp);
+    const Q4<T> m0 = q4_load(b.mn + t);
     if (SECOND) {
-        const Q4<T> m0 = q4_load(b.mn + t);
         const Q4<T> d0 = q4_load(dmp + t);
-        Mn[0] = m0.x + d0.x;
-        Mn[1] = m0.y + d0.y;
-        Mn[2] = m0.z + d0.z;
-        hn = Hp[D][l];
-        h_vector<D>(g, b, Hp, Hp, 1, fo.i, fo.j, fo.k, h);
+        in.Mn[0] = m0.x + d0.x;
+        in.Mn[1] = m0.y + d0.y;
+        in.Mn[2] = m0.z + d0.z;
+        in.hn = Hp[D][fo.l];
+        h_vector<D>(g, b, Hp, Hp, 1, fo.i, fo.j, fo.k, in.h);
     } else {
-        Mn[0] = b.M[3 * D][l];
-        Mn[1] = b.M[3 * D + 1][l];
-        Mn[2] = b.M[3 * D + 2][l];
-        hn = Hin[D][gidx32(g, fo.i, fo.j, fo.k)];
-        h_vector<D>(g, b, Hin, Hin, 0, fo.i, fo.j, fo.k, h);
+        in.Mn[0] = m0.x;
+        in.Mn[1] = m0.y;
+        in.Mn[2] = m0.z;
+        in.hn = Hin[D][gidx32(g, fo.i, fo.j, fo.k)];
+        h_vector<D>(g, b, Hin, Hin, 0, fo.i, fo.j, fo.k, in.h);
     }
-    const T cp = hn - b.cfar * (rest + zp);
+}
+
+// Arithmetic and stores of phase 0: C' = H^n - dt/(2 mu0) curl E,
+// beta = -kappa M^n x H_eff^n, e0 and DeltaM^1; H^1 into Hw.  Returns
+// max_c |DeltaM^1_c| / Ms.
+template <int D, typename T>
+__device__ __forceinline__ T first_finish(const Geo &g, const Box<T> &b, T *const Hw[3], const FaceOf &fo, int t,
+                                          const FirstIn<T> &in, const T h0[3])
+{
+    const T Ms = in.cs.x, k1 = in.cs.y, k2 = in.cs.z;
+    const T *Mn = in.Mn;
+    const T cp = in.hn - b.cfar * (in.rest + in.zp);
     const T e0 = norm_defect(Ms, Mn[0], Mn[1], Mn[2]);
+    T heff[3];
 #pragma unroll
-    for (int c = 0; c < 3; c++) heff[c] = h0[c] + h[c];
+    for (int c = 0; c < 3; c++) heff[c] = h0[c] + in.h[c];
     T dM[3], dMh;
-    Q4<T> bq;
+    T beta[3] = {T(0), T(0), T(0)};
     if (b.order == 2) {
-        const T beta[3] = {-k1 * (Mn[1] * heff[2] - Mn[2] * heff[1]), -k1 * (Mn[2] * heff[0] - Mn[0] * heff[2]),
-                           -k1 * (Mn[0] * heff[1] - Mn[1] * heff[0])};
+        beta[0] = -k1 * (Mn[1] * heff[2] - Mn[2] * heff[1]);
+        beta[1] = -k1 * (Mn[2] * heff[0] - Mn[0] * heff[2]);
+        beta[2] = -k1 * (Mn[0] * heff[1] - Mn[1] * heff[0]);
         llg_iterate(Mn, beta, heff, k1, k2, Ms, e0, D, dM, dMh);
-        bq.x = beta[0];
-        bq.y = beta[1];
-        bq.z = beta[2];
     } else {
         llg_euler(Mn, heff, k1, k2, Ms, e0, D, dM, dMh);
-        bq.x = bq.y = bq.z = T(0);
     }
-    bq.w = cp;
-    b.bc[t] = bq;
-    Q4<T> mq;
-    mq.x = Mn[0];
-    mq.y = Mn[1];
-    mq.z = Mn[2];
-    mq.w = e0;
-    b.mn[t] = mq;
-    Q4<T> dq;
-    dq.x = dM[0];
-    dq.y = dM[1];
-    dq.z = dM[2];
-    dq.w = T(0);
-    b.dm[1][t] = dq;
+    b.bc[t] = q4(beta[0], beta[1], beta[2], cp);
+    b.mn[t] = q4(Mn[0], Mn[1], Mn[2], e0);
+    b.dm[1][t] = q4(dM[0], dM[1], dM[2], T(0));
     const bool wall = wall_node(g, D, D == 0 ? fo.i : D == 1 ? fo.j : fo.k);
-    Hw[D][l] = wall ? T(0) : cp - dMh;
+    Hw[D][fo.l] = wall ? T(0) : cp - dMh;
     return max(abs(dM[0]), max(abs(dM[1]), abs(dM[2]))) / Ms;
 }
 
@@ -521,53 +554,56 @@ __device__ __forceinline__ void non_first(const Geo &g, const Fields<T> &f, T *c
     W1[D][fo.l] = v;
 }
 
-// Iterate r >= 2 on one magnetic face of family D from the neighbours'
-// iterate r-1 (Hprev, dM buffer pr -> cr); returns
-// max_c |DeltaM^r_c - DeltaM^(r-1)_c| / Ms.
+// Everything iteration r reads for one magnetic face.
+template <typename T> struct NextIn {
+    Q4<T> cs, mq, bq, pq;
+    T h[3];
+};
+
 template <int D, typename T>
-__device__ __forceinline__ T mag_next(const Geo &g, const Box<T> &b, const FaceOf &fo, int t, T *const Hprev[3],
-                                      T *const Hcur[3], int pr, int cr, const T h0[3])
+__device__ __forceinline__ void next_load(const Geo &g, const Box<T> &b, const FaceOf &fo, int t, T *const Hprev[3],
+                                          int pr, NextIn<T> &in)
 {
-    const unsigned l = fo.l;
-    const Q4<T> cs = q4_load(b.cst + t);
-    const Q4<T> mq = q4_load(b.mn + t);
-    const Q4<T> bq = q4_load(b.bc + t);
-    const Q4<T> pq = q4_load(b.dm[pr] + t);
-    const T Ms = cs.x, k1 = cs.y, k2 = cs.z;
-    const T Mn[3] = {mq.x, mq.y, mq.z};
-    const T beta[3] = {bq.x, bq.y, bq.z};
-    T h[3], heff[3];
-    h_vector<D>(g, b, Hprev, Hprev, 1, fo.i, fo.j, fo.k, h);
-#pragma unroll
-    for (int c = 0; c < 3; c++) heff[c] = h0[c] + h[c];
-    T dM[3], dMh;
-    llg_iterate(Mn, beta, heff, k1, k2, Ms, mq.w, D, dM, dMh);
-    const bool wall = wall_node(g, D, D == 0 ? fo.i : D == 1 ? fo.j : fo.k);
-    Hcur[D][l] = wall ? T(0) : bq.w - dMh;
-    Q4<T> dq;
-    dq.x = dM[0];
-    dq.y = dM[1];
-    dq.z = dM[2];
-    dq.w = T(0);
-    b.dm[cr][t] = dq;
-    return max(abs(dM[0] - pq.x), max(abs(dM[1] - pq.y), abs(dM[2] - pq.z))) / Ms;
+    in.cs = q4_load(b.cst + t);
+    in.mq = q4_load(b.mn + t);
+    in.bq = q4_load(b.bc + t);
+    in.pq = q4_load(b.dm[pr] + t);
+    h_vector<D>(g, b, Hprev, Hprev, 1, fo.i, fo.j, fo.k, in.h);
 }
 
-// Final H and M^(n+1/2) on one magnetic face of family D; returns false if
-// a written value is not finite.
+// Iterate r >= 2 from the neighbours' iterate r-1: DeltaM^r into dm[cr], H^r
+// into Hcur; returns max_c |DeltaM^r_c - DeltaM^(r-1)_c| / Ms.
+template <int D, typename T>
+__device__ __forceinline__ T next_finish(const Geo &g, const Box<T> &b, const FaceOf &fo, int t, T *const Hcur[3],
+                                         int cr, const NextIn<T> &in, const T h0[3])
+{
+    const T Ms = in.cs.x, k1 = in.cs.y, k2 = in.cs.z;
+    const T Mn[3] = {in.mq.x, in.mq.y, in.mq.z};
+    const T beta[3] = {in.bq.x, in.bq.y, in.bq.z};
+    T heff[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) heff[c] = h0[c] + in.h[c];
+    T dM[3], dMh;
+    llg_iterate(Mn, beta, heff, k1, k2, Ms, in.mq.w, D, dM, dMh);
+    const bool wall = wall_node(g, D, D == 0 ? fo.i : D == 1 ? fo.j : fo.k);
+    Hcur[D][fo.l] = wall ? T(0) : in.bq.w - dMh;
+    b.dm[cr][t] = q4(dM[0], dM[1], dM[2], T(0));
+    return max(abs(dM[0] - in.pq.x), max(abs(dM[1] - in.pq.y), abs(dM[2] - in.pq.z))) / Ms;
+}
+
+// Final H and M^(n+1/2) on one magnetic face of family D: H to the global
+// Hout, M into the face record (the box M is refreshed from the records at
+// the end of every mmx_step call).  Returns false if a value is not finite.
 template <int D, typename T>
 __device__ __forceinline__ bool mag_store(const Geo &g, const Box<T> &b, const FaceOf &fo, int t,
                                           T *const Hfin[3], T *const Hout[3], int fr)
 {
-    const unsigned l = fo.l;
-    const T v = Hfin[D][l];
+    const T v = Hfin[D][fo.l];
     Hout[D][gidx32(g, fo.i, fo.j, fo.k)] = v;
     const Q4<T> mq = q4_load(b.mn + t);
     const Q4<T> dq = q4_load(b.dm[fr] + t);
     const T m0 = mq.x + dq.x, m1 = mq.y + dq.y, m2 = mq.z + dq.z;
-    b.M[3 * D][l] = m0;
-    b.M[3 * D + 1][l] = m1;
-    b.M[3 * D + 2][l] = m2;
+    b.mn[t] = q4(m0, m1, m2, T(0));
     return isfinite(v) && isfinite(m0) && isfinite(m1) && isfinite(m2);
 }
 
@@ -575,18 +611,19 @@ __device__ __forceinline__ bool mag_store(const Geo &g, const Box<T> &b, const F
 // Step 3) with the E in f.E.  Work comes from two lists built when the
 // materials are set, each ordered by family: the magnetic faces and the
 // other faces of the box; the same thread takes the same faces in every
-// phase.  Phase 0 gives non-magnetic faces their final H and forms the
-// first iterate on magnetic faces; each further iteration r updates every
-// magnetic face from the neighbours' iterate r-1 (Jacobi), reduces
-// max |DeltaM^r - DeltaM^(r-1)|/Ms into res[r] (warp shuffle, block max, one
-// atomicMax on the FP64 bit pattern per block) and meets at a bounded grid
-// barrier; all blocks then read res[r] and stop together at the first r with
-// res[r] < tol (or at max_iter, latching kErrNotConverged).
-//   SECOND false: H^n and M^n come from the global H (Hin) and the box M.
-//   SECOND true:  they come from the previous half step of this launch,
+// phase.  Phase 0 gives
+// non-magnetic faces their final H and forms the first iterate on magnetic
+// faces; each further iteration r updates every magnetic face from the
+// neighbours' iterate r-1 (Jacobi), reduces max |DeltaM^r - DeltaM^(r-1)|/Ms
+// into res[r] (warp shuffle, block max, one atomicMax on the FP64 bit
+// pattern per block) and meets at a bounded grid barrier; all blocks then
+// read res[r] and stop together at the first r with res[r] < tol (or at
+// max_iter, latching kErrNotConverged).  M lives in the face records.
+//   SECOND false: H^n comes from the global H (Hin), M^n from the records.
+//   SECOND true:  both come from the previous half step of this launch,
 //                 which ended in iterate buffer fprev without writing back.
-//   WRITE true:   H^(n+1/2) goes to the global Hout and M^(n+1/2) to the box
-//                 M; otherwise both stay in the iterate buffers.
+//   WRITE true:   H^(n+1/2) goes to the global Hout and M^(n+1/2) into the
+//                 records; otherwise both stay in the iterate buffers.
 // Returns the final iterate parity, or -1 if a barrier timed out.
 template <bool SECOND, bool WRITE, typename T>
 __device__ int hm_half_step(const Geo &g, const Fields<T> &f, const Box<T> &b, T *const Hin[3], T *const Hout[3],
@@ -619,9 +656,18 @@ __device__ int hm_half_step(const Geo &g, const Fields<T> &f, const Box<T> &b, T
         for (int t = t0; t < b.nmag; t += stride) {
             const FaceOf fo = face_of(nx);
             if (t + stride < b.nmag) nx = b.mag[t + stride];
-            T rv = fo.d == 0   ? mag_first<0, SECOND>(g, f, b, Hin, Hp, dmp, W1, fo, t, h0)
-                   : fo.d == 1 ? mag_first<1, SECOND>(g, f, b, Hin, Hp, dmp, W1, fo, t, h0)
-                               : mag_first<2, SECOND>(g, f, b, Hin, Hp, dmp, W1, fo, t, h0);
+            FirstIn<T> in;
+            T rv;
+            if (fo.d == 0) {
+                first_load<0, SECOND>(g, f, b, Hin, Hp, dmp, fo, t, in);
+                rv = first_finish<0>(g, b, W1, fo, t, in, h0);
+            } else if (fo.d == 1) {
+                first_load<1, SECOND>(g, f, b, Hin, Hp, dmp, fo, t, in);
+                rv = first_finish<1>(g, b, W1, fo, t, in, h0);
+            } else {
+                first_load<2, SECOND>(g, f, b, Hin, Hp, dmp, fo, t, in);
+                rv = first_finish<2>(g, b, W1, fo, t, in, h0);
+            }
             rmax = max(rmax, rv);
         }
     }
@@ -641,9 +687,18 @@ __device__ int hm_half_step(const Geo &g, const Fields<T> &f, const Box<T> &b, T
         for (int t = t0; t < b.nmag; t += stride) {
             const FaceOf fo = face_of(nx);
             if (t + stride < b.nmag) nx = b.mag[t + stride];
-            T rv = fo.d == 0   ? mag_next<0>(g, b, fo, t, Hprev, Hcur, pr, cr, h0)
-                   : fo.d == 1 ? mag_next<1>(g, b, fo, t, Hprev, Hcur, pr, cr, h0)
-                               : mag_next<2>(g, b, fo, t, Hprev, Hcur, pr, cr, h0);
+            NextIn<T> in;
+            T rv;
+            if (fo.d == 0) {
+                next_load<0>(g, b, fo, t, Hprev, pr, in);
+                rv = next_finish<0>(g, b, fo, t, Hcur, cr, in, h0);
+            } else if (fo.d == 1) {
+                next_load<1>(g, b, fo, t, Hprev, pr, in);
+                rv = next_finish<1>(g, b, fo, t, Hcur, cr, in, h0);
+            } else {
+                next_load<2>(g, b, fo, t, Hprev, pr, in);
+                rv = next_finish<2>(g, b, fo, t, Hcur, cr, in, h0);
+            }
             rmax = max(rmax, rv);
         }
         rmax = block_max(rmax);
@@ -654,7 +709,7 @@ __device__ int hm_half_step(const Geo &g, const Fields<T> &f, const Box<T> &b, T
 
     const int fr = r & 1;
     if (WRITE) {
-        // ---- write back H (all box faces) and M (magnetic faces)
+        // ---- write back H (all box faces) and M (magnetic-face records)
         T *const Hfin[3] = {fr ? W1[0] : W0[0], fr ? W1[1] : W0[1], fr ? W1[2] : W0[2]};
         bool ok = true;
         for (int t = t0; t < b.nnon; t += stride) {
