@@ -16,9 +16,11 @@ scaling is weak and `value` is the sum over ranks.  `--impl reference` times
 the FP64 CPU oracle on the host cores instead (rank 0 only).
 """
 import argparse
+import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -33,6 +35,7 @@ METRIC = "coupled E/H/M cell-updates/s and % of HBM roofline; FP32 vs FP64 path 
 UNIT = "cell-updates/s"
 WORKLOAD = "waveguide_128x128x512"
 L2_BYTES = 126 * 2 ** 20
+ACCURACY_STEPS = (1000, 5000)   # the waveguide's stated checkpoints
 
 
 def peaks():
@@ -189,6 +192,32 @@ def run_path(torch, mmx, w, prec, path, K, W, stream, dist=None, profile=True):
     return sim, ms, prof, stats
 
 
+def kernel_source_sha256():
+    """sha256 over the CUDA sources (sorted by name): a captured DRAM traffic
+    figure is reported only while it still describes the built kernels."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2103_12819_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def captured_traffic(kernel, prec_name):
+    """DRAM bytes (read + write) per launch of `kernel` on this workload from
+    the committed ncu summary, or None if there is none for these sources."""
+    path = os.path.join(ROOT, "profiles", "%s_%s_%s.md" % (kernel, WORKLOAD, prec_name))
+    try:
+        with open(path) as f:
+            text = f.read()
+    except OSError:
+        return None
+    fields = dict(re.findall(r"^- (source_sha256|traffic_bytes_per_launch): `?([0-9a-f]+)`?$", text, re.M))
+    if fields.get("source_sha256") != kernel_source_sha256() or "traffic_bytes_per_launch" not in fields:
+        return None
+    return int(fields["traffic_bytes_per_launch"])
+
+
 def roofline_of(prof, K, w, esz, peak_gbs, peak_kind):
     if not prof:
         return None, None
@@ -202,10 +231,39 @@ def roofline_of(prof, K, w, esz, peak_gbs, peak_kind):
                 "frac": None, "traffic": None, "peak_kind": peak_kind}, launches_per_step
     achieved = bpc * w.ncells / (avg_ms * 1e-3) / 1e9
     shares = {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in prof.items()}
+    traffic = captured_traffic(name, "fp32" if esz == 4 else "fp64")
     return {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak_gbs,
-            "unit": "GB/s", "frac": round(achieved / peak_gbs, 4), "traffic": None,
+            "unit": "GB/s", "frac": round(achieved / peak_gbs, 4), "traffic": traffic,
+            "alg_bytes_per_launch": bpc * w.ncells,
             "peak_kind": peak_kind, "alg_bytes_per_cell": bpc, "avg_launch_us": round(avg_ms * 1e3, 2),
             "kernel_shares": shares}, launches_per_step
+
+
+def accuracy_leg(mmx, w, stream, checkpoints=ACCURACY_STEPS):
+    """The FP32 path against the FP64 path (which matches the FP64 oracle to
+    1e-12, see the parity tests) after each of `checkpoints` steps from the
+    same initial state: relative L2 per field (E 0-2, H 3-5, M 6-14, PML split
+    parts 15-18, a split part against the norm of its component)."""
+    sims = {prec: mmx.from_workload(w, prec=prec, stream=stream.cuda_stream, path=mmx.PATH_FUSED)
+            for prec in (mmx.FP32, mmx.FP64)}
+    parent = {15: 0, 16: 1, 17: 3, 18: 4}
+    out, done = {}, 0
+    for n in checkpoints:
+        for x in sims.values():
+            x.step(n - done)
+            x.sync()
+        done = n
+        a_s, b_s = sims[mmx.FP32], sims[mmx.FP64]
+        errs = {}
+        for fid in range(19):
+            a, b = a_s.get_field(fid), b_s.get_field(fid)
+            nb = np.linalg.norm(b_s.get_field(parent[fid]) if fid in parent else b)
+            errs[fid] = float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.abs(a - b).max())
+        out[str(n)] = {"max": max(errs.values()),
+                       "per_field": {str(k): float("%.3e" % v) for k, v in errs.items()}}
+    for x in sims.values():
+        x.close()
+    return out
 
 
 def e2e_leg(torch, mmx, w, prec, path, K, stream):
@@ -305,14 +363,9 @@ def ours_arm(args):
         simp, msp, profp, _ = run_path(torch, mmx, w, mmx.FP64, mmx.PATH_PLAIN, K, W, stream, dist,
                                        profile=False)
         simp.close()
-        # FP32 vs FP64 after the same (W + 2K) steps
-        errs = {}
-        for fid in range(15):
-            a, b = sim32.get_field(fid), sim64.get_field(fid)
-            nb = np.linalg.norm(b)
-            errs[fid] = float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.abs(a - b).max())
         sim32.close()
         sim64.close()
+        acc = accuracy_leg(mmx, w, stream)
         e2e = e2e_leg(torch, mmx, w, mmx.FP32, path, K, stream)
     value = whole_job_rate(w.ncells, world, K, ms32)
     mag_frac = float(np.count_nonzero(w.Ms > 0)) / w.ncells
@@ -331,8 +384,7 @@ def ours_arm(args):
         "fp64": {"value": whole_job_rate(w.ncells, world, K, ms64), "ms_per_step": ms64 / K, "roofline": roof64,
                  "iters_min": stats64["iters_min"], "iters_max": stats64["iters_max"]},
         "plain_fp64": {"value": whole_job_rate(w.ncells, world, K, msp), "ms_per_step": msp / K},
-        "fp32_vs_fp64_rel_l2_after_steps": {"steps": W + 2 * K, "max": max(errs.values()),
-                                            "per_field": {str(k): float("%.3e" % v) for k, v in errs.items()}},
+        "fp32_vs_fp64_rel_l2_after_steps": acc,
         "iters": {"min": stats32["iters_min"], "max": stats32["iters_max"]},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
