@@ -205,6 +205,47 @@ typedef struct {
     double total_ms;
 } mmx_kernel_profile;
 
+/* Point probes of E: the time series from which the paper's air-filled guide
+ * analysis (Sec. 5.2.1) takes the Fourier transform of E on the guide's
+ * central line.
+ * mmx_add_probe registers E component `field` (0-2) at (i, j, k) within that
+ * component's extent and returns the probe's index (0-15), or
+ * MMX_ERR_INVALID (bad field or index, more than 16 probes).  Adding a probe
+ * discards the samples recorded so far.  After every completed time step the
+ * context appends one row of samples (E^(n+1) of every probe, converted to
+ * double) to a device table of 65536 rows; later steps are not recorded
+ * until the table is read with reset.  mmx_get_probes copies up to max_rows
+ * rows, row-major (out[r * nprobe + p], row r = the r-th step since the last
+ * reset), into the host array out, synchronises the context stream, clears
+ * the table if reset is nonzero, and returns the number of rows copied (or a
+ * negative error code). */
+MMX_API int mmx_add_probe(mmx_ctx *ctx, int field, int i, int j, int k);
+MMX_API long long mmx_get_probes(mmx_ctx *ctx, double *out, long long max_rows, int reset);
+
+/* Discrete electromagnetic energy of the grid, in joules per the units of
+ * the inputs: W = 1/2 sum_edges eps E^2 + 1/2 sum_faces mu (H^2 -
+ * (dt/(2 mu) curl E)^2), the quantity the half-step leapfrog of Sec. 3.2
+ * conserves exactly in lossless, source-free, non-magnetic media (mu = mu0
+ * mu_r on non-magnetic faces, mu0 on magnetic faces; periodic duplicates
+ * counted once).  Valid between mmx_step calls, where E and H share a time
+ * level.  Summed in FP64 with Neumaier compensation whatever the storage
+ * precision; synchronises the context stream. */
+MMX_API int mmx_energy(mmx_ctx *ctx, double *out);
+
+/* Poynting flux monitors.  mmx_add_flux_plane registers the z node plane k
+ * (0 <= k <= nz; at most 4 planes) and returns its index.  After every time
+ * step the context adds dt * P to the plane's accumulator, where
+ * P = sum (Ex <Hy>_z - Ey <Hx>_z) dx dy is the power through the plane in
+ * +z, each E edge paired with the mean of the two H faces above and below it
+ * and H taken at the time level of E (on the fused path the mean of the two
+ * half-step values, exact on non-magnetic faces outside the PML).  The sum
+ * and the accumulation are FP64 with Neumaier compensation.
+ * mmx_get_flux writes out[0] = the time-integrated flux (J) since the plane
+ * was added or last reset and out[1] = P of the last step (W), synchronising
+ * the context stream; reset = 1 then clears the accumulator. */
+MMX_API int mmx_add_flux_plane(mmx_ctx *ctx, int k);
+MMX_API int mmx_get_flux(mmx_ctx *ctx, int index, double out[2], int reset);
+
 MMX_API int mmx_set_profiling(mmx_ctx *ctx, int enable);
 MMX_API int mmx_get_profile(mmx_ctx *ctx, mmx_kernel_profile *out, int cap, int reset);
 

@@ -50,8 +50,9 @@ class KernelProfile(ctypes.Structure):
 EXPORTS = ("mmx_create", "mmx_set_materials", "mmx_set_bias", "mmx_set_M_cells", "mmx_set_field",
            "mmx_get_field", "mmx_get_material", "mmx_add_source", "mmx_set_path", "mmx_step",
            "mmx_sync", "mmx_get_stats", "mmx_get_iter_log", "mmx_get_field_device",
-           "mmx_set_profiling", "mmx_get_profile", "mmx_material_average_noalloc", "mmx_last_error",
-           "mmx_destroy")
+           "mmx_add_probe", "mmx_get_probes", "mmx_energy", "mmx_add_flux_plane", "mmx_get_flux",
+           "mmx_set_profiling", "mmx_get_profile",
+           "mmx_material_average_noalloc", "mmx_last_error", "mmx_destroy")
 
 _lib = None
 
@@ -96,6 +97,16 @@ def lib():
     L.mmx_get_field_device.argtypes = [P, I, ctypes.POINTER(P), ctypes.POINTER(LL), ctypes.POINTER(LL)]
     L.mmx_set_profiling.restype = I
     L.mmx_set_profiling.argtypes = [P, I]
+    L.mmx_add_probe.restype = I
+    L.mmx_add_probe.argtypes = [P, I, I, I, I]
+    L.mmx_get_probes.restype = LL
+    L.mmx_get_probes.argtypes = [P, dp, LL, I]
+    L.mmx_energy.restype = I
+    L.mmx_energy.argtypes = [P, dp]
+    L.mmx_add_flux_plane.restype = I
+    L.mmx_add_flux_plane.argtypes = [P, I]
+    L.mmx_get_flux.restype = I
+    L.mmx_get_flux.argtypes = [P, I, dp, I]
     L.mmx_get_profile.restype = I
     L.mmx_get_profile.argtypes = [P, ctypes.POINTER(KernelProfile), I, I]
     L.mmx_material_average_noalloc.restype = I
@@ -258,6 +269,37 @@ class Solver:
         self._check(self._L.mmx_get_field_device(self._h, int(fid), ctypes.byref(p), ctypes.byref(sx),
                                                  ctypes.byref(sy)), "mmx_get_field_device")
         return p.value, sx.value, sy.value
+
+    def add_probe(self, fid, i, j, k):
+        """Record E component `fid` (0-2) at (i, j, k) after every step; returns
+        the probe index.  Samples recorded so far are discarded."""
+        idx = self._check(self._L.mmx_add_probe(self._h, int(fid), int(i), int(j), int(k)), "mmx_add_probe")
+        self._nprobe = idx + 1
+        return idx
+
+    def get_probes(self, max_rows=1 << 16, reset=True):
+        """Samples since the last reset as a float64 array [steps, probes]."""
+        nprobe = getattr(self, "_nprobe", 0)
+        buf = np.zeros(max(1, int(max_rows) * nprobe), dtype=np.float64)
+        rows = self._L.mmx_get_probes(self._h, _dp(buf), int(max_rows), 1 if reset else 0)
+        self._check(int(rows), "mmx_get_probes")
+        return buf[: rows * nprobe].reshape(rows, nprobe)
+
+    def energy(self):
+        """Discrete electromagnetic energy (J) at the current time level."""
+        out = ctypes.c_double()
+        self._check(self._L.mmx_energy(self._h, ctypes.byref(out)), "mmx_energy")
+        return out.value
+
+    def add_flux_plane(self, k):
+        """Accumulate the Poynting flux through z node plane k; returns its index."""
+        return self._check(self._L.mmx_add_flux_plane(self._h, int(k)), "mmx_add_flux_plane")
+
+    def get_flux(self, index, reset=False):
+        """(time-integrated flux in J, power of the last step in W)."""
+        out = (ctypes.c_double * 2)()
+        self._check(self._L.mmx_get_flux(self._h, int(index), out, 1 if reset else 0), "mmx_get_flux")
+        return out[0], out[1]
 
     def set_profiling(self, enable=True):
         self._check(self._L.mmx_set_profiling(self._h, 1 if enable else 0), "mmx_set_profiling")

@@ -15,6 +15,7 @@
 
 #include "mmx.h"
 #include "mmx_fused.cuh"
+#include "mmx_monitor.cuh"
 
 using namespace mmx;
 
@@ -73,6 +74,19 @@ struct mmx_ctx {
     int4 *dmag = nullptr, *dnon = nullptr;
     int nmag = 0, nnon = 0;
     int coop_blocks = 0;
+
+    // point probes of E: (field, padded index) per probe and a device table
+    // of samples, one row of nprobe doubles per completed time step
+    std::vector<int2> probes;
+    int2 *dprobe = nullptr;
+    double *probe_buf = nullptr;
+    long long probe_rows = 0;
+
+    // monitors: block partial sums, flux planes and their accumulators
+    // ({sum, correction, last power, unused} per plane)
+    double2 *mon_partial = nullptr;
+    std::vector<int> flux_k;
+    double *flux_acc = nullptr;
 
     // control words (device)
     unsigned long long *res = nullptr;     // [4][kMaxIter+1]
@@ -188,6 +202,14 @@ static void face_ext(const mmx_ctx *c, int fam, int e[3])
 }
 
 // Extents of a field id; returns false for an unknown id.
+static size_t gidx_host(const mmx_ctx *c, int i, int j, int k)
+{
+    return (size_t)i + (size_t)c->g.X * ((size_t)j + (size_t)c->g.Y * (size_t)k);
+}
+
+constexpr int kMaxProbes = 16;
+constexpr long long kProbeRows = 1 << 16;
+
 static bool field_ext(const mmx_ctx *c, int id, int e[3])
 {
     if (id >= 0 && id < 3) { edge_ext(c, id, e); return true; }
@@ -514,6 +536,34 @@ template <typename T> static int half_step(mmx_ctx *ctx, const Fields<T> &f, con
     return MMX_OK;
 }
 
+// Record the probes after a completed time step (E^(n+1) in ctx->E).
+template <typename T> static int record_probes(mmx_ctx *ctx)
+{
+    if (ctx->probes.empty() || ctx->probe_rows >= kProbeRows) return MMX_OK;
+    Ptr3<T> E = {{(T *)ctx->E[0], (T *)ctx->E[1], (T *)ctx->E[2]}};
+    const int np = (int)ctx->probes.size();
+    k_probe<T><<<1, 64, 0, ctx->stream>>>(E, ctx->dprobe, np, ctx->probe_buf + ctx->probe_rows * np);
+    CK(cudaGetLastError());
+    ctx->probe_rows++;
+    return MMX_OK;
+}
+
+// Add this step's Poynting power x dt to every flux plane's accumulator; H
+// at the time level of E is the mean of Ha and Hb.
+template <typename T> static int record_flux(mmx_ctx *ctx, Ptr3<T> E, Ptr3<T> Ha, Ptr3<T> Hb)
+{
+    const int npt = ctx->g.X * (ctx->desc.n[1] + 1);
+    const int nblk = std::min(kMonitorBlocks, (npt + kMonitorThreads - 1) / kMonitorThreads);
+    for (size_t p = 0; p < ctx->flux_k.size(); p++) {
+        k_flux_partial<T><<<nblk, kMonitorThreads, 0, ctx->stream>>>(ctx->g, E, Ha, Hb, ctx->flux_k[p],
+                                                                       ctx->mon_partial);
+        k_flux_accumulate<<<1, kMonitorThreads, 0, ctx->stream>>>(ctx->mon_partial, nblk, ctx->desc.dt,
+                                                                  ctx->flux_acc + 4 * p);
+        CK(cudaGetLastError());
+    }
+    return MMX_OK;
+}
+
 template <typename T> static int step_plain(mmx_ctx *ctx, int nsteps)
 {
     Fields<T> f = make_fields<T>(ctx);
@@ -547,6 +597,12 @@ template <typename T> static int step_plain(mmx_ctx *ctx, int nsteps)
         rc = half_step<T>(ctx, f, b, (n + 1.0) * dt);
         if (rc) return rc;
         ctx->steps++;
+        rc = record_probes<T>(ctx);
+        if (!rc && !ctx->flux_k.empty()) {
+            Ptr3<T> E = {{f.E[0], f.E[1], f.E[2]}}, H = {{f.H[0], f.H[1], f.H[2]}};
+            rc = record_flux<T>(ctx, E, H, H);
+        }
+        if (rc) return rc;
     }
     return MMX_OK;
 }
@@ -555,9 +611,7 @@ template <typename T> static int step_plain(mmx_ctx *ctx, int nsteps)
 
 constexpr int kFBX = 32, kFBY = 8;   // fused block: 31 x 7 output columns + halo
 
-// z chunk of the fused kernel: as many chunks as fill one resident wave of
-// blocks (each block marches its whole chunk, so a second wave would double
-// the time).
+// M between the box arrays and the magnetic-face records (see k_box_m_sync).
 template <typename T> static int box_m_sync(mmx_ctx *ctx, int to_rec)
 {
     if (!ctx->magnetic || ctx->nmag == 0) return MMX_OK;
@@ -568,6 +622,9 @@ template <typename T> static int box_m_sync(mmx_ctx *ctx, int to_rec)
     return MMX_OK;
 }
 
+// z chunk of the fused kernel: as many chunks as fill one resident wave of
+// blocks (each block marches its whole chunk, so a second wave would double
+// the time).
 template <typename T> static int plan_fused(mmx_ctx *ctx)
 {
     int dev = 0, nsm = 0, per = 0;
@@ -626,9 +683,27 @@ static void launch_fused(mmx_ctx *ctx, dim3 G, dim3 B, const Fields<T> &f, Ptr3<
 // Rows per CTA (+1 halo warp), chosen by measurement on the 128x128x512
 // waveguide: FP32 7 rows (8 warps, 2 CTAs/SM, no spills: 110 us; 8 rows 123,
 // 15 rows 122), FP64 8 rows (1269 us; 7 rows 1316).
+#ifndef MMX_VEC_F32_ROWS
+#define MMX_VEC_F32_ROWS 7
+#endif
+#ifndef MMX_VEC_F32_STAGES
+#define MMX_VEC_F32_STAGES 2
+#endif
 template <typename T> struct VecRows;
-template <> struct VecRows<float> { static constexpr int value = 7; };
+template <> struct VecRows<float> { static constexpr int value = MMX_VEC_F32_ROWS; };
 template <> struct VecRows<double> { static constexpr int value = 8; };
+// Plane stages in the shared-memory ring (2: two CTAs per SM; more: one CTA
+// per SM with ST-1 planes in flight).  Variants that also stage the ca
+// arrays (sigma != 0) keep two stages to fit in shared memory.
+template <typename T, bool GEN> struct VecStages { static constexpr int value = 2; };
+template <> struct VecStages<float, false> { static constexpr int value = MMX_VEC_F32_STAGES; };
+
+template <typename T, bool GEN> constexpr size_t vec_smem_bytes()
+{
+    constexpr size_t b = VecLayout<T, VecRows<T>::value, GEN, VecStages<T, GEN>::value>::bytes;
+    static_assert(b <= 227 * 1024, "vectorised kernel shared memory above the per-CTA limit");
+    return b;
+}
 
 // The vectorised kernel covers grids with PEC x and y walls whose magnetic
 // box stays clear of the PML layers (it writes box faces for the box kernel
@@ -645,9 +720,9 @@ static bool vec_usable(const mmx_ctx *ctx)
 // Opt every variant in to its dynamic shared memory (above the 48 KB default).
 template <typename T, int NH, bool PMLK, bool GEN> static cudaError_t set_vec_smem_v()
 {
-    constexpr int BY = VecRows<T>::value;
-    return cudaFuncSetAttribute(k_fused_vec<T, BY, NH, PMLK, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)VecLayout<T, BY, GEN>::bytes);
+    constexpr int BY = VecRows<T>::value, ST = VecStages<T, GEN>::value;
+    return cudaFuncSetAttribute(k_fused_vec<T, BY, ST, NH, PMLK, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)vec_smem_bytes<T, GEN>());
 }
 
 template <typename T> static cudaError_t set_vec_smem()
@@ -669,9 +744,9 @@ template <typename T> static int plan_vec(mmx_ctx *ctx)
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     CK(set_vec_smem<T>());
-    constexpr int BY = VecRows<T>::value;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused_vec<T, BY, 2, true, false>, 32 * (BY + 1),
-                                                     VecLayout<T, BY, false>::bytes));
+    constexpr int BY = VecRows<T>::value, ST = VecStages<T, false>::value;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused_vec<T, BY, ST, 2, true, false>, 32 * (BY + 1),
+                                                     vec_smem_bytes<T, false>()));
     per = std::max(per, 1);
     const int *n = ctx->desc.n;
     const int xs = W - Lanes<T>::V;
@@ -717,9 +792,9 @@ template <typename T> static int zero_walls(mmx_ctx *ctx)
 template <typename T, int NH, bool PMLK, bool GEN>
 static void launch_vec_v(mmx_ctx *ctx, const Fields<T> &f, const FusedIO<T> &io, int nsrc)
 {
-    constexpr int BY = VecRows<T>::value;
-    k_fused_vec<T, BY, NH, PMLK, GEN><<<ctx->vec_grid, dim3(32, BY + 1), VecLayout<T, BY, GEN>::bytes,
-                                        ctx->stream>>>(
+    constexpr int BY = VecRows<T>::value, ST = VecStages<T, GEN>::value;
+    k_fused_vec<T, BY, ST, NH, PMLK, GEN><<<ctx->vec_grid, dim3(32, BY + 1), vec_smem_bytes<T, GEN>(),
+                                            ctx->stream>>>(
         ctx->g, f, io, (const Src<T> *)ctx->dsrc, nsrc, ctx->vec_chunk, ctx->vec_xstride);
 }
 
@@ -810,8 +885,16 @@ template <typename T> static int step_fused(mmx_ctx *ctx, int nsteps)
             int rc = launch_box<T>(ctx, fb, b, Hn, nhalf);
             if (rc) return rc;
         }
+        if (!ctx->flux_k.empty()) {
+            // E^(n+1) with H^(n+1) = mean of H^(n+1/2) and H^(n+3/2), or
+            // H^(n+1) itself after the single half step of a call's last step
+            int rc = record_flux<T>(ctx, En, nhalf == 2 ? Ho : Hn, Hn);
+            if (rc) return rc;
+        }
         swap_buffers<T>(ctx);
         ctx->steps++;
+        int rc = record_probes<T>(ctx);
+        if (rc) return rc;
     }
     return MMX_OK;
 }
@@ -892,6 +975,37 @@ static int read_status(mmx_ctx *ctx)
 }
 
 // ================================================================= C ABI
+
+static int ensure_monitor(mmx_ctx *ctx)
+{
+    if (ctx->mon_partial) return MMX_OK;
+    int rc = dalloc(ctx, (void **)&ctx->mon_partial, kMonitorBlocks * sizeof(double2));
+    if (!rc) rc = dalloc(ctx, (void **)&ctx->flux_acc, 4 * kMaxFluxPlanes * sizeof(double));
+    return rc;
+}
+
+template <typename T> static int energy_t(mmx_ctx *ctx, double *out)
+{
+    int rc = ensure_monitor(ctx);
+    if (rc) return rc;
+    Fields<T> f = make_fields<T>(ctx);
+    k_energy<T><<<kMonitorBlocks, kMonitorThreads, 0, ctx->stream>>>(ctx->g, f, ctx->cell[0], ctx->cell[2],
+                                                                     ctx->cell[3], ctx->mon_partial);
+    CK(cudaGetLastError());
+    std::vector<double2> part(kMonitorBlocks);
+    CK(cudaMemcpyAsync(part.data(), ctx->mon_partial, kMonitorBlocks * sizeof(double2), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    double s = 0.0, c = 0.0;
+    for (const double2 &v : part) {
+        const double t = s + v.x;
+        c += std::fabs(s) >= std::fabs(v.x) ? (s - t) + v.x : (v.x - t) + s;
+        s = t;
+        c += v.y;
+    }
+    *out = s + c;
+    return MMX_OK;
+}
 
 extern "C" {
 
@@ -999,6 +1113,8 @@ void mmx_destroy(mmx_ctx *ctx)
     for (int a = 0; a < 6; a++) cudaFree(ctx->cell[a]);
     free_box(ctx);
     cudaFree(ctx->dampE); cudaFree(ctx->dampH);
+    cudaFree(ctx->probe_buf); cudaFree(ctx->dprobe);
+    cudaFree(ctx->mon_partial); cudaFree(ctx->flux_acc);
     cudaFree(ctx->res); cudaFree(ctx->bar); cudaFree(ctx->iterlog); cudaFree(ctx->halfsteps);
     cudaFree(ctx->last_res); cudaFree(ctx->errw); cudaFree(ctx->dsrc); cudaFree(ctx->stage);
     cudaFree(ctx->damp); cudaFree(ctx->dprof[0]); cudaFree(ctx->dprof[1]);
@@ -1359,6 +1475,76 @@ int mmx_get_profile(mmx_ctx *ctx, mmx_kernel_profile *out, int cap, int reset)
             ctx->prof_ms[k] = 0.0;
         }
     return m;
+}
+
+int mmx_add_probe(mmx_ctx *ctx, int field, int i, int j, int k)
+{
+    if (!ctx || !ctx->E[0]) return MMX_ERR_INVALID;
+    if (field < 0 || field > 2) return fail(ctx, MMX_ERR_INVALID, "probes record E components (fields 0-2)");
+    if ((int)ctx->probes.size() >= kMaxProbes) return fail(ctx, MMX_ERR_INVALID, "at most %d probes", kMaxProbes);
+    int e[3];
+    field_ext(ctx, field, e);
+    const int ix[3] = {i, j, k};
+    for (int a = 0; a < 3; a++)
+        if (ix[a] < 0 || ix[a] >= e[a]) return fail(ctx, MMX_ERR_INVALID, "probe index out of range");
+    if (!ctx->probe_buf) {
+        int rc = dalloc(ctx, (void **)&ctx->probe_buf, (size_t)kProbeRows * kMaxProbes * sizeof(double));
+        if (!rc) rc = dalloc(ctx, (void **)&ctx->dprobe, kMaxProbes * sizeof(int2));
+        if (rc) return rc;
+    }
+    // samples so far were recorded with the old probe count: start afresh
+    ctx->probe_rows = 0;
+    ctx->probes.push_back(make_int2(field, (int)gidx_host(ctx, i, j, k)));
+    CK(cudaMemcpyAsync(ctx->dprobe, ctx->probes.data(), ctx->probes.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return (int)ctx->probes.size() - 1;
+}
+
+long long mmx_get_probes(mmx_ctx *ctx, double *out, long long max_rows, int reset)
+{
+    if (!ctx || !ctx->E[0] || (max_rows > 0 && !out) || max_rows < 0) return MMX_ERR_INVALID;
+    const long long np = (long long)ctx->probes.size();
+    const long long rows = std::min(ctx->probe_rows, max_rows);
+    if (np > 0 && rows > 0)
+        CK(cudaMemcpyAsync(out, ctx->probe_buf, (size_t)(rows * np) * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (reset) ctx->probe_rows = 0;
+    return rows;
+}
+
+int mmx_energy(mmx_ctx *ctx, double *out)
+{
+    if (!ctx || !ctx->E[0] || !out) return MMX_ERR_INVALID;
+    int rc = is_fp64(ctx) ? energy_t<double>(ctx, out) : energy_t<float>(ctx, out);
+    return rc ? rc : read_status(ctx);
+}
+
+int mmx_add_flux_plane(mmx_ctx *ctx, int k)
+{
+    if (!ctx || !ctx->E[0]) return MMX_ERR_INVALID;
+    if (k < 0 || k > ctx->desc.n[2]) return fail(ctx, MMX_ERR_INVALID, "flux plane k must be in [0, nz]");
+    if ((int)ctx->flux_k.size() >= kMaxFluxPlanes)
+        return fail(ctx, MMX_ERR_INVALID, "at most %d flux planes", kMaxFluxPlanes);
+    int rc = ensure_monitor(ctx);
+    if (rc) return rc;
+    const int idx = (int)ctx->flux_k.size();
+    CK(cudaMemsetAsync(ctx->flux_acc + 4 * idx, 0, 4 * sizeof(double), ctx->stream));
+    ctx->flux_k.push_back(k);
+    return idx;
+}
+
+int mmx_get_flux(mmx_ctx *ctx, int index, double out[2], int reset)
+{
+    if (!ctx || !ctx->E[0] || !out || index < 0 || index >= (int)ctx->flux_k.size()) return MMX_ERR_INVALID;
+    double acc[4];
+    CK(cudaMemcpyAsync(acc, ctx->flux_acc + 4 * index, sizeof acc, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    out[0] = acc[0] + acc[1];
+    out[1] = acc[2];
+    if (reset) CK(cudaMemsetAsync(ctx->flux_acc + 4 * index, 0, 4 * sizeof(double), ctx->stream));
+    return MMX_OK;
 }
 
 int mmx_get_field_device(mmx_ctx *ctx, int id, void **ptr, long long *sx, long long *sy)

@@ -120,39 +120,41 @@ __device__ __forceinline__ void cp_commit()
 {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
-__device__ __forceinline__ void cp_wait_all()
+// Wait until at most N of this thread's copy groups are still in flight.
+template <int N> __device__ __forceinline__ void cp_wait()
 {
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Shared-memory layout of the vectorised kernel (elements of T):
-//   stage [2][NF][R][W]  per plane: Hx, Hy (layer k+1/2), Hz (node k), Ex, Ey,
+// Shared-memory layout of the vectorised kernel (elements of T), a ring of
+// ST plane stages:
+//   stage [ST][NF][R][W] per plane: Hx, Hy (layer k+1/2), Hz (node k), Ex, Ey,
 //                        Ez, cbx, cby, cbz [, cax, cay, caz] of rows y0..y0+BY
-//   up    [2][2][W]      Hx, Hz of row y0-1
-//   left  [2][2][RP]     Hy, Hz of column x0-1, one per row
+//   up    [ST][2][W]     Hx, Hz of row y0-1
+//   left  [ST][2][RP]    Hy, Hz of column x0-1, one per row
 //   sEx, sEz [2][R][W]   E^(n+1) exchanged between rows
-template <typename T, int BY, bool GEN> struct VecLayout {
+template <typename T, int BY, bool GEN, int ST> struct VecLayout {
     static constexpr int V = Lanes<T>::V;
     static constexpr int W = 32 * V;
     static constexpr int R = BY + 1;
     static constexpr int RP = (R + 3) / 4 * 4;
     static constexpr int NF = GEN ? 12 : 9;
     static constexpr int stage = 0;
-    static constexpr int up = stage + 2 * NF * R * W;
-    static constexpr int left = up + 2 * 2 * W;
-    static constexpr int ex = left + 2 * 2 * RP;
+    static constexpr int up = stage + ST * NF * R * W;
+    static constexpr int left = up + ST * 2 * W;
+    static constexpr int ex = left + ST * 2 * RP;
     static constexpr int ez = ex + 2 * R * W;
     static constexpr int total = ez + 2 * R * W;
     static constexpr size_t bytes = (size_t)total * sizeof(T);
 };
 
-template <typename T, int BY, int NH, bool PMLK, bool GEN>
-__global__ void __launch_bounds__(32 * (BY + 1), BY <= 8 ? 2 : 1)
+template <typename T, int BY, int ST, int NH, bool PMLK, bool GEN>
+__global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
     k_fused_vec(const __grid_constant__ Geo g, const __grid_constant__ Fields<T> f,
                 const __grid_constant__ FusedIO<T> io, const Src<T> *__restrict__ src, int nsrc, int chunk,
                 int xstride)
 {
-    using L = VecLayout<T, BY, GEN>;
+    using L = VecLayout<T, BY, GEN, ST>;
     constexpr int V = L::V, W = L::W, R = L::R, RP = L::RP, NF = L::NF;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *const sm = reinterpret_cast<T *>(smem_raw);
@@ -240,14 +242,28 @@ __global__ void __launch_bounds__(32 * (BY + 1), BY <= 8 ? 2 : 1)
             vzero<T, V>(hyp);
         }
     }
-    issue(k0, 0);
+    // prologue: planes k0 .. k0+ST-2 in flight (one copy group per plane,
+    // empty groups past the chunk keep the group count uniform)
+#pragma unroll
+    for (int s = 0; s < ST - 1; s++) {
+        if (k0 + s <= k1)
+            issue(k0 + s, s);
+        else
+            cp_commit();
+    }
     T acc = T(0);
-    int b = 0;
-    for (int k = k0; k <= k1; k++, b ^= 1) {
-        const int st = b;
-        cp_wait_all();
+    int b = 0, st = 0;
+    for (int k = k0; k <= k1; k++, b ^= 1, st = st + 1 == ST ? 0 : st + 1) {
+        cp_wait<ST - 2>();
         __syncthreads();          // plane k staged; every thread is done with plane k-1
-        if (k < k1) issue(k + 1, st ^ 1);
+        {
+            // plane k+ST-1 into the stage plane k-1 used
+            const int sn = st == 0 ? ST - 1 : st - 1;
+            if (k + ST - 1 <= k1)
+                issue(k + ST - 1, sn);
+            else
+                cp_commit();
+        }
 
         T hx[V], hy[V], hz[V], hzu[V], hxu[V];
         sload(hx, S(st, 0, w) + col);

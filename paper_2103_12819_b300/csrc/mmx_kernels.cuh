@@ -239,6 +239,16 @@ template <typename T> __global__ void k_box_m_sync(Box<T> b, int to_rec)
     }
 }
 
+// Point probes: row[p] = E component probe[p].x at padded index probe[p].y.
+template <typename T> __global__ void k_probe(Ptr3<T> E, const int2 *__restrict__ probe, int np, double *row)
+{
+    const int p = threadIdx.x;
+    if (p < np) {
+        const int2 q = probe[p];
+        row[p] = (double)E.p[q.x][q.y];
+    }
+}
+
 // ============================================================ field copies
 
 // Gather a padded device field (or a box-local M component) into a compact

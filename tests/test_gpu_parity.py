@@ -256,3 +256,34 @@ def test_fp32_multi_strip_against_oracle():
     for fid in range(15):
         a, b = sim.get_field(fid), ref.get_field(fid)
         assert rel_l2(a, b) <= 1e-4, fid
+
+
+# ----------------------------------------------------------- probes
+
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_probes_record_e_after_every_step(path):
+    """Each probe row is E^(n+1) after step n: the last row equals the field
+    read back at the end, and row r equals a run stopped after r+1 steps."""
+    w = W.waveguide(n=(24, 20, 48), steps=12)
+    pts = [(0, 5, 6, 7), (1, 12, 3, 30), (2, 3, 4, 5)]
+    s = mmx.from_workload(w, path=path)
+    for p in pts:
+        s.add_probe(*p)
+    s.step(5)
+    s.step(7)
+    rows = s.get_probes()
+    assert rows.shape == (12, 3)
+    for c, (fid, i, j, k) in enumerate(pts):
+        ext = W.field_extent(fid, w.n)
+        fin = s.get_field(fid).reshape(ext[2], ext[1], ext[0])[k, j, i]
+        assert rows[-1, c] == fin
+    r = mmx.from_workload(w, path=path)
+    r.step(4)
+    for c, (fid, i, j, k) in enumerate(pts):
+        ext = W.field_extent(fid, w.n)
+        assert rows[3, c] == r.get_field(fid).reshape(ext[2], ext[1], ext[0])[k, j, i]
+    assert s.get_probes().shape == (0, 3)          # reset by the previous read
+    with pytest.raises(mmx.MMXError):
+        s.add_probe(3, 0, 0, 0)                    # H is not probed
+    with pytest.raises(mmx.MMXError):
+        s.add_probe(0, w.n[0], 0, 0)               # Ex has nx edges along x

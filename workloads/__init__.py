@@ -187,6 +187,27 @@ def waveguide(seed: int = 1, steps: int = 5000, n=(128, 128, 512), dx: float = 2
         steps=steps)
 
 
+def air_guide(steps: int = 8000, nz: int = 600, f0: float = 10.5e9, tp: Optional[float] = None) -> Workload:
+    """Air-filled rectangular guide of the paper's Sec. 5.2.1: W = 14.95 mm,
+    h = 10.16 mm (75 x 51 cells), PEC side walls, 10-cell PML at both z ends
+    (the paper instead closes one end with PEC and drives it there).  A TE10
+    soft Jy plane at z node 20 carries a modulated Gaussian: by default the
+    paper's pulse (f0 = 10.5 GHz, Tp = one period, t0 = 3 Tp); a long tp gives
+    a narrow-band drive at f0.  TE10 cutoff c/(2W) = 10.03 GHz."""
+    W, h = 14.95e-3, 10.16e-3
+    n = (75, 51, nz)
+    d = (W / n[0], h / n[1], W / n[0])
+    dt = cfl_dt(d, 0.9)
+    shp = _cell_shape(n)
+    tp = 1.0 / f0 if tp is None else tp
+    src = Source(SRC_PLANE_J_TE10, 1, 0, 0, 20, amp=1e7, f0=f0, tp=tp, t0=3 * tp)
+    return Workload(
+        name="air_guide_75x51x%d" % nz, n=n, d=d, dt=dt, bc=(PEC, PEC, PML), pml_cells=10,
+        tol=1e-6, max_iter=64, h0=(0.0, 0.0, 0.0), eps_r=np.ones(shp), sigma=np.zeros(shp),
+        mu_r=np.ones(shp), Ms=np.zeros(shp), alpha=np.zeros(shp), gamma=np.zeros(shp),
+        m_cells=None, sources=[src], steps=steps)
+
+
 def stress(seed: int = 2, steps: int = 1000, n: int = 512, tol: float = 1e-6) -> Workload:
     """n^3 PEC box, dx = 1e-6 m; centred (n/2)^3 magnetic block with seeded
     uniformly random unit M directions times Ms = 1.4e5 A/m, alpha = 0.01;
