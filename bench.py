@@ -122,16 +122,19 @@ class ClockSampler:
 
 # --------------------------------------------------------------- helpers
 
-def alg_bytes_per_cell(kernel, w, esz):
+def alg_bytes_per_cell(kernel, w, esz, ssz=None):
     """Algorithmic DRAM bytes per cell for one launch of each kernel (what the
     method must move, single pass): E update reads E, H, eps_r and writes E
     (10 words); a non-magnetic H half step reads E, H and writes H (9 words);
     a fused E+H+H pass reads E, H, eps_r and writes E, H (13 words); the H/M
     box kernel reads E, H, M, Ms, alpha, gamma and writes H, M on its faces
-    (per magnetic cell 6 + 9 + 3 read, 3 + 9 written)."""
-    words = {"e_update": 10, "h_update": 9, "fused_eh": 13, "fused_eh_vec": 13}.get(kernel)
-    if words is not None:
-        return words * esz
+    (per magnetic cell 6 + 9 + 3 read, 3 + 9 written).  E and H words are
+    ssz bytes (the stored type), eps_r esz bytes (the arithmetic type)."""
+    ssz = esz if ssz is None else ssz
+    fields = {"e_update": 9, "h_update": 9, "fused_eh": 12, "fused_eh_vec": 12}.get(kernel)
+    coef = {"e_update": 1, "h_update": 0, "fused_eh": 1, "fused_eh_vec": 1}.get(kernel)
+    if fields is not None:
+        return fields * ssz + coef * esz
     return None
 
 
@@ -218,20 +221,20 @@ def captured_traffic(kernel, prec_name):
     return int(fields["traffic_bytes_per_launch"])
 
 
-def roofline_of(prof, K, w, esz, peak_gbs, peak_kind):
+def roofline_of(prof, K, w, esz, peak_gbs, peak_kind, ssz=None, prec_name=None):
     if not prof:
         return None, None
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     name, (launches, total_ms) = dom
     avg_ms = total_ms / launches
-    bpc = alg_bytes_per_cell(name, w, esz)
+    bpc = alg_bytes_per_cell(name, w, esz, ssz)
     launches_per_step = sum(v[0] for v in prof.values()) / K
     if bpc is None:
         return {"bound": "hbm", "kernel": name, "achieved": None, "peak": peak_gbs, "unit": "GB/s",
                 "frac": None, "traffic": None, "peak_kind": peak_kind}, launches_per_step
     achieved = bpc * w.ncells / (avg_ms * 1e-3) / 1e9
     shares = {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in prof.items()}
-    traffic = captured_traffic(name, "fp32" if esz == 4 else "fp64")
+    traffic = captured_traffic(name, prec_name or ("fp32" if esz == 4 else "fp64"))
     return {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak_gbs,
             "unit": "GB/s", "frac": round(achieved / peak_gbs, 4), "traffic": traffic,
             "alg_bytes_per_launch": bpc * w.ncells,
@@ -239,13 +242,14 @@ def roofline_of(prof, K, w, esz, peak_gbs, peak_kind):
             "kernel_shares": shares}, launches_per_step
 
 
-def accuracy_leg(mmx, w, stream, checkpoints=ACCURACY_STEPS):
-    """The FP32 path against the FP64 path (which matches the FP64 oracle to
-    1e-12, see the parity tests) after each of `checkpoints` steps from the
-    same initial state: relative L2 per field (E 0-2, H 3-5, M 6-14, PML split
-    parts 15-18, a split part against the norm of its component)."""
-    sims = {prec: mmx.from_workload(w, prec=prec, stream=stream.cuda_stream, path=mmx.PATH_FUSED)
-            for prec in (mmx.FP32, mmx.FP64)}
+def accuracy_leg(mmx, w, stream, checkpoints=ACCURACY_STEPS, prec=None):
+    """The FP32 (or `prec`) path against the FP64 path (which matches the FP64
+    oracle to 1e-12, see the parity tests) after each of `checkpoints` steps
+    from the same initial state: relative L2 per field (E 0-2, H 3-5, M 6-14,
+    PML split parts 15-18, a split part against the norm of its component)."""
+    low = mmx.FP32 if prec is None else prec
+    sims = {p: mmx.from_workload(w, prec=p, stream=stream.cuda_stream, path=mmx.PATH_FUSED)
+            for p in (low, mmx.FP64)}
     parent = {15: 0, 16: 1, 17: 3, 18: 4}
     out, done = {}, 0
     for n in checkpoints:
@@ -253,13 +257,20 @@ def accuracy_leg(mmx, w, stream, checkpoints=ACCURACY_STEPS):
             x.step(n - done)
             x.sync()
         done = n
-        a_s, b_s = sims[mmx.FP32], sims[mmx.FP64]
+        a_s, b_s = sims[low], sims[mmx.FP64]
         errs = {}
         for fid in range(19):
             a, b = a_s.get_field(fid), b_s.get_field(fid)
             nb = np.linalg.norm(b_s.get_field(parent[fid]) if fid in parent else b)
             errs[fid] = float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.abs(a - b).max())
-        out[str(n)] = {"max": max(errs.values()),
+        # the E, H and M vector fields as a whole (components near zero, such
+        # as Ex and Ez of a TE10 guide, are measured against their vector)
+        vec = {}
+        for grp, fids in (("E", range(0, 3)), ("H", range(3, 6)), ("M", range(6, 15))):
+            e2 = sum(float(np.sum((a_s.get_field(f) - b_s.get_field(f)) ** 2)) for f in fids)
+            n2 = sum(float(np.sum(b_s.get_field(f) ** 2)) for f in fids)
+            vec[grp] = float("%.3e" % ((e2 / n2) ** 0.5)) if n2 > 0 else 0.0
+        out[str(n)] = {"max": max(errs.values()), "vector_fields": vec,
                        "per_field": {str(k): float("%.3e" % v) for k, v in errs.items()}}
     for x in sims.values():
         x.close()
@@ -360,12 +371,16 @@ def ours_arm(args):
         roof, lps = roofline_of(prof32, K, w, 4, peak, peak_kind)
         sim64, ms64, prof64, stats64 = run_path(torch, mmx, w, mmx.FP64, path, K, W, stream, dist)
         roof64, _ = roofline_of(prof64, K, w, 8, peak, peak_kind)
+        sim16, ms16, prof16, stats16 = run_path(torch, mmx, w, mmx.FP16, path, K, W, stream, dist)
+        roof16, _ = roofline_of(prof16, K, w, 4, peak, peak_kind, ssz=2, prec_name="fp16")
+        sim16.close()
         simp, msp, profp, _ = run_path(torch, mmx, w, mmx.FP64, mmx.PATH_PLAIN, K, W, stream, dist,
                                        profile=False)
         simp.close()
         sim32.close()
         sim64.close()
         acc = accuracy_leg(mmx, w, stream)
+        acc16 = accuracy_leg(mmx, w, stream, checkpoints=(1000,), prec=mmx.FP16)
         e2e = e2e_leg(torch, mmx, w, mmx.FP32, path, K, stream)
     value = whole_job_rate(w.ncells, world, K, ms32)
     mag_frac = float(np.count_nonzero(w.Ms > 0)) / w.ncells
@@ -384,6 +399,9 @@ def ours_arm(args):
         "fp64": {"value": whole_job_rate(w.ncells, world, K, ms64), "ms_per_step": ms64 / K, "roofline": roof64,
                  "iters_min": stats64["iters_min"], "iters_max": stats64["iters_max"]},
         "plain_fp64": {"value": whole_job_rate(w.ncells, world, K, msp), "ms_per_step": msp / K},
+        "fp16_storage": {"value": whole_job_rate(w.ncells, world, K, ms16), "ms_per_step": ms16 / K,
+                         "roofline": roof16, "iters_min": stats16["iters_min"], "iters_max": stats16["iters_max"],
+                         "vs_fp64_rel_l2_after_steps": acc16},
         "fp32_vs_fp64_rel_l2_after_steps": acc,
         "iters": {"min": stats32["iters_min"], "max": stats32["iters_max"]},
     }

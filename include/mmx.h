@@ -55,7 +55,12 @@ extern "C" {
 #define MMX_ERR_NONFINITE (-5)      /* a field became NaN/Inf */
 #define MMX_ERR_TIMEOUT (-6)        /* a bounded device wait gave up */
 
-typedef enum { MMX_FP64 = 0, MMX_FP32 = 1 } mmx_precision;
+/* MMX_FP16: E, H and their PML split parts stored in FP16 (each value divided
+ * by a per-context scale, see mmx_set_storage_scale), all arithmetic in FP32;
+ * materials, M and the H/M iteration state stay FP32.  Supported on the
+ * fused path for grids with PEC x and y walls and no hard sources; other
+ * configurations make mmx_step return MMX_ERR_INVALID. */
+typedef enum { MMX_FP64 = 0, MMX_FP32 = 1, MMX_FP16 = 2 } mmx_precision;
 typedef enum { MMX_BC_PERIODIC = 0, MMX_BC_PEC = 1, MMX_BC_PML = 2 } mmx_bc;
 typedef enum { MMX_PATH_PLAIN = 0, MMX_PATH_FUSED = 1 } mmx_path;
 
@@ -204,6 +209,14 @@ typedef struct {
     long long launches;
     double total_ms;
 } mmx_kernel_profile;
+
+/* FP16 storage scales: E is stored as E / sE and H (with its PML split part)
+ * as H / sH, so that the fields of a problem sit inside FP16's range
+ * (|value / scale| < 65504, full precision above 6.1e-5).  Defaults:
+ * sH = 64 A/m, sE = 376.73 * sH V/m (the vacuum impedance times sH).  Only
+ * for MMX_FP16 contexts, and only before any field value is set or any step
+ * is taken (MMX_ERR_INVALID otherwise); both scales must be positive. */
+MMX_API int mmx_set_storage_scale(mmx_ctx *ctx, double sE, double sH);
 
 /* Point probes of E: the time series from which the paper's air-filled guide
  * analysis (Sec. 5.2.1) takes the Fourier transform of E on the guide's

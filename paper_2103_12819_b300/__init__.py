@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libmmx.so")
 
 MMX_OK = 0
 ERRORS = {-1: "INVALID", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED", -5: "NONFINITE", -6: "TIMEOUT"}
-FP64, FP32 = 0, 1
+FP64, FP32, FP16 = 0, 1, 2     # FP16: FP16 storage of E and H, FP32 arithmetic
 PERIODIC, PEC, PML = 0, 1, 2
 PATH_PLAIN, PATH_FUSED = 0, 1
 
@@ -50,7 +50,7 @@ class KernelProfile(ctypes.Structure):
 EXPORTS = ("mmx_create", "mmx_set_materials", "mmx_set_bias", "mmx_set_M_cells", "mmx_set_field",
            "mmx_get_field", "mmx_get_material", "mmx_add_source", "mmx_set_path", "mmx_step",
            "mmx_sync", "mmx_get_stats", "mmx_get_iter_log", "mmx_get_field_device",
-           "mmx_add_probe", "mmx_get_probes", "mmx_energy", "mmx_add_flux_plane", "mmx_get_flux",
+           "mmx_set_storage_scale", "mmx_add_probe", "mmx_get_probes", "mmx_energy", "mmx_add_flux_plane", "mmx_get_flux",
            "mmx_set_profiling", "mmx_get_profile",
            "mmx_material_average_noalloc", "mmx_last_error", "mmx_destroy")
 
@@ -97,6 +97,8 @@ def lib():
     L.mmx_get_field_device.argtypes = [P, I, ctypes.POINTER(P), ctypes.POINTER(LL), ctypes.POINTER(LL)]
     L.mmx_set_profiling.restype = I
     L.mmx_set_profiling.argtypes = [P, I]
+    L.mmx_set_storage_scale.restype = I
+    L.mmx_set_storage_scale.argtypes = [P, D, D]
     L.mmx_add_probe.restype = I
     L.mmx_add_probe.argtypes = [P, I, I, I, I]
     L.mmx_get_probes.restype = LL
@@ -269,6 +271,10 @@ class Solver:
         self._check(self._L.mmx_get_field_device(self._h, int(fid), ctypes.byref(p), ctypes.byref(sx),
                                                  ctypes.byref(sy)), "mmx_get_field_device")
         return p.value, sx.value, sy.value
+
+    def set_storage_scale(self, sE, sH):
+        """FP16 contexts: store E as E/sE and H as H/sH (before any field or step)."""
+        self._check(self._L.mmx_set_storage_scale(self._h, float(sE), float(sH)), "mmx_set_storage_scale")
 
     def add_probe(self, fid, i, j, k):
         """Record E component `fid` (0-2) at (i, j, k) after every step; returns

@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "mmx.h"
@@ -39,7 +40,10 @@ struct mmx_ctx {
     mmx_grid_desc desc;
     Geo g;
     size_t npad = 0;            // padded elements per Yee array
-    int esz = 8;                // bytes per element
+    int esz = 8;                // bytes per element of the arithmetic type
+    int ssz = 8;                // bytes per stored E/H element
+    double sE = 1.0, sH = 1.0;  // FP16 storage scales
+    bool touched = false;       // a field was set or a step taken
     cudaStream_t stream = nullptr;
     int path = MMX_PATH_FUSED;
     std::string err;
@@ -143,6 +147,7 @@ static int fail(mmx_ctx *c, int code, const char *fmt, ...)
     } while (0)
 
 static bool is_fp64(const mmx_ctx *c) { return c->desc.prec == MMX_FP64; }
+static bool is_fp16(const mmx_ctx *c) { return c->desc.prec == MMX_FP16; }
 
 constexpr int kAmpChunk = 1024;   // steps whose source values are uploaded at once
 
@@ -233,20 +238,24 @@ static int dalloc(mmx_ctx *ctx, void **p, size_t bytes)
     return MMX_OK;
 }
 
-template <typename T> static Fields<T> make_fields(mmx_ctx *c)
+template <typename T, typename S = T> static Fields<T, S> make_fields(mmx_ctx *c)
 {
-    Fields<T> f;
+    Fields<T, S> f;
     for (int a = 0; a < 3; a++) {
-        f.E[a] = (T *)c->E[a];
-        f.H[a] = (T *)c->H[a];
+        f.E[a] = (S *)c->E[a];
+        f.H[a] = (S *)c->H[a];
         f.ca[a] = (const T *)c->ca[a];
         f.cb[a] = (const T *)c->cb[a];
         f.fh[a] = (const T *)c->fh[a];
     }
     for (int a = 0; a < 2; a++) {
-        f.Ezp[a] = (T *)c->Ezp[a];
-        f.Hzp[a] = (T *)c->Hzp[a];
+        f.Ezp[a] = (S *)c->Ezp[a];
+        f.Hzp[a] = (S *)c->Hzp[a];
     }
+    f.sE = (T)c->sE;
+    f.sH = (T)c->sH;
+    f.isE = (T)(1.0 / c->sE);
+    f.isH = (T)(1.0 / c->sH);
     f.fh0 = (T)(c->desc.dt / (2.0 * kMu0));
     f.dampE = (const T *)c->dampE;
     f.dampH = (const T *)c->dampH;
@@ -443,12 +452,12 @@ static int box_alloc(mmx_ctx *ctx, void **p)
     return rc;
 }
 
-template <typename T> static int compute_coop(mmx_ctx *ctx)
+template <typename T, typename S = T> static int compute_coop(mmx_ctx *ctx)
 {
     int dev = 0, nsm = 0, per = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hm_box<T>, 256, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hm_box<T, S>, 256, 0));
     if (per < 1) return fail(ctx, MMX_ERR_CUDA, "H/M kernel cannot be resident");
     long long need = (std::max(ctx->nmag, ctx->nnon) + 255) / 256;
     long long cap = (long long)per * nsm;
@@ -458,7 +467,7 @@ template <typename T> static int compute_coop(mmx_ctx *ctx)
 
 // ------------------------------------------------------------ materials
 
-template <typename T> static int set_materials_t(mmx_ctx *ctx)
+template <typename T, typename S = T> static int set_materials_t(mmx_ctx *ctx)
 {
     const Geo &g = ctx->g;
     dim3 B = node_block(), G = node_grid(ctx);
@@ -482,7 +491,7 @@ template <typename T> static int set_materials_t(mmx_ctx *ctx)
             k_box_cst<T><<<(ctx->nmag + 255) / 256, 256, 0, ctx->stream>>>(b);
             CK(cudaGetLastError());
         }
-        int rc = compute_coop<T>(ctx);
+        int rc = compute_coop<T, S>(ctx);
         if (rc) return rc;
     }
     CK(cudaStreamSynchronize(ctx->stream));
@@ -493,39 +502,41 @@ template <typename T> static int set_materials_t(mmx_ctx *ctx)
 
 // One cooperative launch over the magnetic box: nsub H/M half steps with
 // the E in f.E, starting from the H in f.H and ending in Hout.
-template <typename T>
-static int launch_box(mmx_ctx *ctx, const Fields<T> &f, const Box<T> &b, Ptr3<T> Hout, int nsub)
+template <typename T, typename S>
+static int launch_box(mmx_ctx *ctx, const Fields<T, S> &f, const Box<T> &b, Ptr3<S> Hout, int nsub)
 {
     int slot = ctx->box_slot;
     ctx->box_slot ^= 1;
     void *args[] = {(void *)&ctx->g, (void *)&f, (void *)&b, (void *)&Hout, (void *)&nsub, (void *)&slot};
     prof_begin(ctx, KK_HM_BOX);
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_hm_box<T>, dim3(ctx->coop_blocks), dim3(256),
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_hm_box<T, S>, dim3(ctx->coop_blocks), dim3(256),
                                                 args, 0, ctx->stream);
     prof_end(ctx);
     CK(e);
     return MMX_OK;
 }
 
-template <typename T> static int half_step(mmx_ctx *ctx, const Fields<T> &f, const Box<T> &b, double t_end)
+template <typename T, typename S>
+static int half_step(mmx_ctx *ctx, const Fields<T, S> &f, const Box<T> &b, double t_end)
 {
     dim3 B = node_block(), G = node_grid(ctx);
     if (ctx->magnetic) {
-        Ptr3<T> Hout = {{f.H[0], f.H[1], f.H[2]}};
-        int rc = launch_box<T>(ctx, f, b, Hout, 1);
+        Ptr3<S> Hout = {{f.H[0], f.H[1], f.H[2]}};
+        int rc = launch_box<T, S>(ctx, f, b, Hout, 1);
         if (rc) return rc;
         prof_begin(ctx, KK_H_UPDATE);
-        k_h_update<T><<<G, B, 0, ctx->stream>>>(ctx->g, f, ctx->lo[0], ctx->lo[1], ctx->lo[2], ctx->hi[0],
-                                                 ctx->hi[1], ctx->hi[2]);
+        k_h_update<T, S><<<G, B, 0, ctx->stream>>>(ctx->g, f, ctx->lo[0], ctx->lo[1], ctx->lo[2], ctx->hi[0],
+                                                    ctx->hi[1], ctx->hi[2]);
         prof_end(ctx);
     } else {
         prof_begin(ctx, KK_H_UPDATE);
-        k_h_update<T><<<G, B, 0, ctx->stream>>>(ctx->g, f, 0, 0, 0, 0, 0, 0);
+        k_h_update<T, S><<<G, B, 0, ctx->stream>>>(ctx->g, f, 0, 0, 0, 0, 0, 0);
         prof_end(ctx);
     }
     CK(cudaGetLastError());
     bool hardH = false;
     for (auto &s : ctx->src) hardH |= s.kind == 3;
+    if constexpr (std::is_same<T, S>::value)
     if (hardH) {
         Ptr3<T> F = {{f.H[0], f.H[1], f.H[2]}};
         prof_begin(ctx, KK_HARD);
@@ -537,12 +548,13 @@ template <typename T> static int half_step(mmx_ctx *ctx, const Fields<T> &f, con
 }
 
 // Record the probes after a completed time step (E^(n+1) in ctx->E).
-template <typename T> static int record_probes(mmx_ctx *ctx)
+template <typename T, typename S = T> static int record_probes(mmx_ctx *ctx)
 {
     if (ctx->probes.empty() || ctx->probe_rows >= kProbeRows) return MMX_OK;
-    Ptr3<T> E = {{(T *)ctx->E[0], (T *)ctx->E[1], (T *)ctx->E[2]}};
+    Ptr3<S> E = {{(S *)ctx->E[0], (S *)ctx->E[1], (S *)ctx->E[2]}};
     const int np = (int)ctx->probes.size();
-    k_probe<T><<<1, 64, 0, ctx->stream>>>(E, ctx->dprobe, np, ctx->probe_buf + ctx->probe_rows * np);
+    k_probe<S, T><<<1, 64, 0, ctx->stream>>>(E, (T)ctx->sE, ctx->dprobe, np,
+                                             ctx->probe_buf + ctx->probe_rows * np);
     CK(cudaGetLastError());
     ctx->probe_rows++;
     return MMX_OK;
@@ -550,13 +562,13 @@ template <typename T> static int record_probes(mmx_ctx *ctx)
 
 // Add this step's Poynting power x dt to every flux plane's accumulator; H
 // at the time level of E is the mean of Ha and Hb.
-template <typename T> static int record_flux(mmx_ctx *ctx, Ptr3<T> E, Ptr3<T> Ha, Ptr3<T> Hb)
+template <typename T, typename S = T> static int record_flux(mmx_ctx *ctx, Ptr3<S> E, Ptr3<S> Ha, Ptr3<S> Hb)
 {
     const int npt = ctx->g.X * (ctx->desc.n[1] + 1);
     const int nblk = std::min(kMonitorBlocks, (npt + kMonitorThreads - 1) / kMonitorThreads);
     for (size_t p = 0; p < ctx->flux_k.size(); p++) {
-        k_flux_partial<T><<<nblk, kMonitorThreads, 0, ctx->stream>>>(ctx->g, E, Ha, Hb, ctx->flux_k[p],
-                                                                       ctx->mon_partial);
+        k_flux_partial<S, T><<<nblk, kMonitorThreads, 0, ctx->stream>>>(ctx->g, E, Ha, Hb, (T)ctx->sE, (T)ctx->sH,
+                                                                          ctx->flux_k[p], ctx->mon_partial);
         k_flux_accumulate<<<1, kMonitorThreads, 0, ctx->stream>>>(ctx->mon_partial, nblk, ctx->desc.dt,
                                                                   ctx->flux_acc + 4 * p);
         CK(cudaGetLastError());
@@ -581,7 +593,7 @@ template <typename T> static int step_plain(mmx_ctx *ctx, int nsteps)
             if (rc) return rc;
         }
         f.src_amp = amp0 + (size_t)(s % kAmpChunk) * nsrc;
-        int rc = half_step<T>(ctx, f, b, (n + 0.5) * dt);
+        int rc = half_step<T, T>(ctx, f, b, (n + 0.5) * dt);
         if (rc) return rc;
         prof_begin(ctx, KK_E_UPDATE);
         k_e_update<T><<<G, B, 0, ctx->stream>>>(ctx->g, f, (const Src<T> *)ctx->dsrc, nsrc);
@@ -594,13 +606,13 @@ template <typename T> static int step_plain(mmx_ctx *ctx, int nsteps)
             prof_end(ctx);
             CK(cudaGetLastError());
         }
-        rc = half_step<T>(ctx, f, b, (n + 1.0) * dt);
+        rc = half_step<T, T>(ctx, f, b, (n + 1.0) * dt);
         if (rc) return rc;
         ctx->steps++;
-        rc = record_probes<T>(ctx);
+        rc = record_probes<T, T>(ctx);
         if (!rc && !ctx->flux_k.empty()) {
             Ptr3<T> E = {{f.E[0], f.E[1], f.E[2]}}, H = {{f.H[0], f.H[1], f.H[2]}};
-            rc = record_flux<T>(ctx, E, H, H);
+            rc = record_flux<T, T>(ctx, E, H, H);
         }
         if (rc) return rc;
     }
@@ -698,9 +710,9 @@ template <> struct VecRows<double> { static constexpr int value = 8; };
 template <typename T, bool GEN> struct VecStages { static constexpr int value = 2; };
 template <> struct VecStages<float, false> { static constexpr int value = MMX_VEC_F32_STAGES; };
 
-template <typename T, bool GEN> constexpr size_t vec_smem_bytes()
+template <typename T, typename S, bool GEN> constexpr size_t vec_smem_bytes()
 {
-    constexpr size_t b = VecLayout<T, VecRows<T>::value, GEN, VecStages<T, GEN>::value>::bytes;
+    constexpr size_t b = VecLayout<T, S, VecRows<T>::value, GEN, VecStages<T, GEN>::value>::bytes;
     static_assert(b <= 227 * 1024, "vectorised kernel shared memory above the per-CTA limit");
     return b;
 }
@@ -718,35 +730,38 @@ static bool vec_usable(const mmx_ctx *ctx)
 }
 
 // Opt every variant in to its dynamic shared memory (above the 48 KB default).
-template <typename T, int NH, bool PMLK, bool GEN> static cudaError_t set_vec_smem_v()
+template <typename T, typename S, int NH, bool PMLK, bool GEN> static cudaError_t set_vec_smem_v()
 {
     constexpr int BY = VecRows<T>::value, ST = VecStages<T, GEN>::value;
-    return cudaFuncSetAttribute(k_fused_vec<T, BY, ST, NH, PMLK, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)vec_smem_bytes<T, GEN>());
+    return cudaFuncSetAttribute(k_fused_vec<T, S, BY, ST, NH, PMLK, GEN>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem_bytes<T, S, GEN>());
 }
 
-template <typename T> static cudaError_t set_vec_smem()
+template <typename T, typename S> static cudaError_t set_vec_smem()
 {
     cudaError_t e = cudaSuccess;
-    cudaError_t r[8] = {set_vec_smem_v<T, 1, false, false>(), set_vec_smem_v<T, 1, false, true>(),
-                        set_vec_smem_v<T, 1, true, false>(),  set_vec_smem_v<T, 1, true, true>(),
-                        set_vec_smem_v<T, 2, false, false>(), set_vec_smem_v<T, 2, false, true>(),
-                        set_vec_smem_v<T, 2, true, false>(),  set_vec_smem_v<T, 2, true, true>()};
+    cudaError_t r[8] = {set_vec_smem_v<T, S, 1, false, false>(), set_vec_smem_v<T, S, 1, false, true>(),
+                        set_vec_smem_v<T, S, 1, true, false>(),  set_vec_smem_v<T, S, 1, true, true>(),
+                        set_vec_smem_v<T, S, 2, false, false>(), set_vec_smem_v<T, S, 2, false, true>(),
+                        set_vec_smem_v<T, S, 2, true, false>(),  set_vec_smem_v<T, S, 2, true, true>()};
     for (cudaError_t x : r)
         if (x != cudaSuccess) e = x;
     return e;
 }
 
-template <typename T> static int plan_vec(mmx_ctx *ctx)
+template <typename T, typename S> static int plan_vec(mmx_ctx *ctx)
 {
     constexpr int W = 32 * Lanes<T>::V;
     int dev = 0, nsm = 0, per = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    CK(set_vec_smem<T>());
+    {
+        cudaError_t e = set_vec_smem<T, S>();
+        CK(e);
+    }
     constexpr int BY = VecRows<T>::value, ST = VecStages<T, false>::value;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused_vec<T, BY, ST, 2, true, false>, 32 * (BY + 1),
-                                                     vec_smem_bytes<T, false>()));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused_vec<T, S, BY, ST, 2, true, false>,
+                                                     32 * (BY + 1), vec_smem_bytes<T, S, false>()));
     per = std::max(per, 1);
     const int *n = ctx->desc.n;
     const int xs = W - Lanes<T>::V;
@@ -761,7 +776,7 @@ template <typename T> static int plan_vec(mmx_ctx *ctx)
     return MMX_OK;
 }
 
-template <typename T> static int zero_walls(mmx_ctx *ctx)
+template <typename T> static int zero_walls(mmx_ctx *ctx)   // T: the stored type
 {
     WallList<T> L;
     L.n = 0;
@@ -789,22 +804,22 @@ template <typename T> static int zero_walls(mmx_ctx *ctx)
     return MMX_OK;
 }
 
-template <typename T, int NH, bool PMLK, bool GEN>
-static void launch_vec_v(mmx_ctx *ctx, const Fields<T> &f, const FusedIO<T> &io, int nsrc)
+template <typename T, typename S, int NH, bool PMLK, bool GEN>
+static void launch_vec_v(mmx_ctx *ctx, const Fields<T, S> &f, const FusedIO<S> &io, int nsrc)
 {
     constexpr int BY = VecRows<T>::value, ST = VecStages<T, GEN>::value;
-    k_fused_vec<T, BY, ST, NH, PMLK, GEN><<<ctx->vec_grid, dim3(32, BY + 1), vec_smem_bytes<T, GEN>(),
-                                            ctx->stream>>>(
+    k_fused_vec<T, S, BY, ST, NH, PMLK, GEN><<<ctx->vec_grid, dim3(32, BY + 1), vec_smem_bytes<T, S, GEN>(),
+                                               ctx->stream>>>(
         ctx->g, f, io, (const Src<T> *)ctx->dsrc, nsrc, ctx->vec_chunk, ctx->vec_xstride);
 }
 
-template <typename T>
-static void launch_vec(mmx_ctx *ctx, const Fields<T> &f, const FusedIO<T> &io, int nsrc, int nhalf)
+template <typename T, typename S>
+static void launch_vec(mmx_ctx *ctx, const Fields<T, S> &f, const FusedIO<S> &io, int nsrc, int nhalf)
 {
     const bool pml = ctx->g.npml > 0, gen = ctx->any_sigma || ctx->any_mu;
 #define MMX_VEC_CASE(NHV, PV, GV)                                                                    \
     if (nhalf == NHV && pml == PV && gen == GV) {                                                    \
-        launch_vec_v<T, NHV, PV, GV>(ctx, f, io, nsrc);                                              \
+        launch_vec_v<T, S, NHV, PV, GV>(ctx, f, io, nsrc);                                           \
         return;                                                                                      \
     }
     MMX_VEC_CASE(2, true, false) MMX_VEC_CASE(2, false, false) MMX_VEC_CASE(2, true, true)
@@ -813,33 +828,37 @@ static void launch_vec(mmx_ctx *ctx, const Fields<T> &f, const FusedIO<T> &io, i
 #undef MMX_VEC_CASE
 }
 
-template <typename T> static int step_fused(mmx_ctx *ctx, int nsteps)
+template <typename T, typename S = T> static int step_fused(mmx_ctx *ctx, int nsteps)
 {
+    constexpr bool same = std::is_same<T, S>::value;
     const bool vec = vec_usable(ctx);
+    if (!same && !vec) return fail(ctx, MMX_ERR_INVALID, "FP16 storage needs PEC x and y walls");
     if (vec) {
         if (!ctx->vec_chunk) {
-            int rc = plan_vec<T>(ctx);
+            int rc = plan_vec<T, S>(ctx);
             if (rc) return rc;
         }
     }
-    if (!ctx->fused_chunk) {
-        int rc = plan_fused<T>(ctx);
-        if (rc) return rc;
+    if constexpr (same) {
+        if (!ctx->fused_chunk) {
+            int rc = plan_fused<T>(ctx);
+            if (rc) return rc;
+        }
     }
     Box<T> b = make_box<T>(ctx);
     int nsrc = (int)ctx->src.size();
     const T *amp0 = (const T *)ctx->damp;
     // Step 1 of the first step in place: H^n -> H^(n+1/2)
     {
-        Fields<T> f = make_fields<T>(ctx);
-        int rc = half_step<T>(ctx, f, b, (ctx->steps + 0.5) * ctx->desc.dt);
+        Fields<T, S> f = make_fields<T, S>(ctx);
+        int rc = half_step<T, S>(ctx, f, b, (ctx->steps + 0.5) * ctx->desc.dt);
         if (rc) return rc;
     }
     // Wall values set through mmx_set_field have been used by that half step
     // (as the per-update path uses them); from here on they are zero, which
     // the vectorised kernel relies on for the x = nx column and y = ny row.
     if (vec && ctx->walls_dirty) {
-        int rc = zero_walls<T>(ctx);
+        int rc = zero_walls<S>(ctx);
         if (rc) return rc;
         ctx->walls_dirty = false;
     }
@@ -852,17 +871,17 @@ template <typename T> static int step_fused(mmx_ctx *ctx, int nsteps)
             if (rc) return rc;
         }
         const int nhalf = s == nsteps - 1 ? 1 : 2;
-        Fields<T> f = make_fields<T>(ctx);
+        Fields<T, S> f = make_fields<T, S>(ctx);
         f.src_amp = amp0 + (size_t)(s % kAmpChunk) * nsrc;
-        Ptr3<T> Eo = {{(T *)ctx->E[0], (T *)ctx->E[1], (T *)ctx->E[2]}};
-        Ptr3<T> Ho = {{(T *)ctx->H[0], (T *)ctx->H[1], (T *)ctx->H[2]}};
-        Ptr3<T> En = {{(T *)ctx->Ealt[0], (T *)ctx->Ealt[1], (T *)ctx->Ealt[2]}};
-        Ptr3<T> Hn = {{(T *)ctx->Halt[0], (T *)ctx->Halt[1], (T *)ctx->Halt[2]}};
-        Ptr3<T> Zo = {{(T *)ctx->Ezp[0], (T *)ctx->Ezp[1], nullptr}};
-        Ptr3<T> Zn = {{(T *)ctx->Ezpalt[0], (T *)ctx->Ezpalt[1], nullptr}};
+        Ptr3<S> Eo = {{(S *)ctx->E[0], (S *)ctx->E[1], (S *)ctx->E[2]}};
+        Ptr3<S> Ho = {{(S *)ctx->H[0], (S *)ctx->H[1], (S *)ctx->H[2]}};
+        Ptr3<S> En = {{(S *)ctx->Ealt[0], (S *)ctx->Ealt[1], (S *)ctx->Ealt[2]}};
+        Ptr3<S> Hn = {{(S *)ctx->Halt[0], (S *)ctx->Halt[1], (S *)ctx->Halt[2]}};
+        Ptr3<S> Zo = {{(S *)ctx->Ezp[0], (S *)ctx->Ezp[1], nullptr}};
+        Ptr3<S> Zn = {{(S *)ctx->Ezpalt[0], (S *)ctx->Ezpalt[1], nullptr}};
         prof_begin(ctx, vec ? KK_FUSED_VEC : KK_FUSED);
         if (vec) {
-            FusedIO<T> io;
+            FusedIO<S> io;
             for (int a = 0; a < 3; a++) {
                 io.Eo[a] = Eo.p[a];
                 io.Ho[a] = Ho.p[a];
@@ -873,33 +892,58 @@ template <typename T> static int step_fused(mmx_ctx *ctx, int nsteps)
                 io.Zo[a] = Zo.p[a];
                 io.Zn[a] = Zn.p[a];
             }
-            launch_vec<T>(ctx, f, io, nsrc, nhalf);
+            launch_vec<T, S>(ctx, f, io, nsrc, nhalf);
         } else {
-            launch_fused<T>(ctx, G, B, f, Eo, Ho, En, Hn, Zo, Zn, nsrc, nhalf);
+            if constexpr (same) launch_fused<T>(ctx, G, B, f, Eo, Ho, En, Hn, Zo, Zn, nsrc, nhalf);
         }
         prof_end(ctx);
         CK(cudaGetLastError());
         if (ctx->magnetic) {
-            Fields<T> fb = f;
+            Fields<T, S> fb = f;
             for (int a = 0; a < 3; a++) fb.E[a] = En.p[a];   // E^(n+1); fb.H = H^(n+1/2)
-            int rc = launch_box<T>(ctx, fb, b, Hn, nhalf);
+            int rc = launch_box<T, S>(ctx, fb, b, Hn, nhalf);
             if (rc) return rc;
         }
         if (!ctx->flux_k.empty()) {
             // E^(n+1) with H^(n+1) = mean of H^(n+1/2) and H^(n+3/2), or
             // H^(n+1) itself after the single half step of a call's last step
-            int rc = record_flux<T>(ctx, En, nhalf == 2 ? Ho : Hn, Hn);
+            int rc = record_flux<T, S>(ctx, En, nhalf == 2 ? Ho : Hn, Hn);
             if (rc) return rc;
         }
         swap_buffers<T>(ctx);
         ctx->steps++;
-        int rc = record_probes<T>(ctx);
+        int rc = record_probes<T, S>(ctx);
         if (rc) return rc;
     }
     return MMX_OK;
 }
 
 // ------------------------------------------------------------ field copy
+
+// FP16-stored E, H and PML split parts (ids 0-5, 15-18) of an MMX_FP16
+// context; value = stored * scale.
+static int copy_field_half(mmx_ctx *ctx, int id, double *host, long long N, const int e[3], int dir)
+{
+    __half *dev = id < 3 ? (__half *)ctx->E[id] : id < 6 ? (__half *)ctx->H[id - 3]
+                : id < 17 ? (__half *)ctx->Ezp[id - 15] : (__half *)ctx->Hzp[id - 17];
+    const float scale = (float)(id < 3 || id == 15 || id == 16 ? ctx->sE : ctx->sH);
+    int blocks = (int)((N + 255) / 256);
+    if (!dev) {
+        if (dir == 0) {
+            memset(host, 0, (size_t)N * sizeof(double));
+            return MMX_OK;
+        }
+        return fail(ctx, MMX_ERR_INVALID, "field %d exists only with a z-PML", id);
+    }
+    if (dir == 1)
+        CK(cudaMemcpyAsync(ctx->stage, host, (size_t)N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    k_copy_field_h<<<blocks, 256, 0, ctx->stream>>>(ctx->g, dev, scale, e[0], e[1], e[2], ctx->stage, dir);
+    CK(cudaGetLastError());
+    if (dir == 0)
+        CK(cudaMemcpyAsync(host, ctx->stage, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MMX_OK;
+}
 
 template <typename T> static int copy_field_t(mmx_ctx *ctx, int id, double *host, long long n, int dir)
 {
@@ -908,6 +952,7 @@ template <typename T> static int copy_field_t(mmx_ctx *ctx, int id, double *host
     long long N = (long long)e[0] * e[1] * e[2];
     int rc = ensure_stage(ctx, (size_t)N);
     if (rc) return rc;
+    if (is_fp16(ctx) && (id < 6 || id >= 15)) return copy_field_half(ctx, id, host, N, e, dir);
     T *dev = nullptr;
     int boxed = 0;
     if (id < 3) dev = (T *)ctx->E[id];
@@ -984,12 +1029,12 @@ static int ensure_monitor(mmx_ctx *ctx)
     return rc;
 }
 
-template <typename T> static int energy_t(mmx_ctx *ctx, double *out)
+template <typename T, typename S = T> static int energy_t(mmx_ctx *ctx, double *out)
 {
     int rc = ensure_monitor(ctx);
     if (rc) return rc;
-    Fields<T> f = make_fields<T>(ctx);
-    k_energy<T><<<kMonitorBlocks, kMonitorThreads, 0, ctx->stream>>>(ctx->g, f, ctx->cell[0], ctx->cell[2],
+    Fields<T, S> f = make_fields<T, S>(ctx);
+    k_energy<T, S><<<kMonitorBlocks, kMonitorThreads, 0, ctx->stream>>>(ctx->g, f, ctx->cell[0], ctx->cell[2],
                                                                      ctx->cell[3], ctx->mon_partial);
     CK(cudaGetLastError());
     std::vector<double2> part(kMonitorBlocks);
@@ -1027,7 +1072,8 @@ int mmx_create(const mmx_grid_desc *desc, void *cuda_stream, mmx_ctx **out)
     if (d.order != 1 && d.order != 2) rc = fail(ctx, MMX_ERR_INVALID, "order must be 1 or 2");
     if (!(d.tol > 0)) rc = fail(ctx, MMX_ERR_INVALID, "tol must be positive");
     if (d.max_iter < 1 || d.max_iter > kMaxIter) rc = fail(ctx, MMX_ERR_INVALID, "max_iter must be 1..64");
-    if (d.prec != MMX_FP64 && d.prec != MMX_FP32) rc = fail(ctx, MMX_ERR_INVALID, "bad precision");
+    if (d.prec != MMX_FP64 && d.prec != MMX_FP32 && d.prec != MMX_FP16)
+        rc = fail(ctx, MMX_ERR_INVALID, "bad precision");
     if (d.bc[2] == MMX_BC_PML && (d.pml_cells < 1 || 2 * d.pml_cells >= d.n[2]))
         rc = fail(ctx, MMX_ERR_INVALID, "pml_cells must be in [1, nz/2)");
     long long X = ((long long)d.n[0] + 1 + 7) / 8 * 8;
@@ -1040,6 +1086,11 @@ int mmx_create(const mmx_grid_desc *desc, void *cuda_stream, mmx_ctx **out)
     }
     ctx->stream = (cudaStream_t)cuda_stream;
     ctx->esz = d.prec == MMX_FP64 ? 8 : 4;
+    ctx->ssz = d.prec == MMX_FP64 ? 8 : d.prec == MMX_FP32 ? 4 : 2;
+    if (d.prec == MMX_FP16) {
+        ctx->sH = 64.0;
+        ctx->sE = kMu0 * kC0 * ctx->sH;
+    }
     Geo &g = ctx->g;
     for (int a = 0; a < 3; a++) {
         g.n[a] = d.n[a];
@@ -1052,19 +1103,19 @@ int mmx_create(const mmx_grid_desc *desc, void *cuda_stream, mmx_ctx **out)
     g.npml = d.bc[2] == MMX_BC_PML ? d.pml_cells : 0;
     g.dt = d.dt;
     ctx->npad = (size_t)npad;
-    size_t fb = ctx->npad * ctx->esz;
+    size_t fb = ctx->npad * ctx->esz, sb = ctx->npad * ctx->ssz;
     for (int a = 0; a < 3 && !rc; a++) {
-        rc = dalloc(ctx, &ctx->E[a], fb);
-        if (!rc) rc = dalloc(ctx, &ctx->H[a], fb);
-        if (!rc) rc = dalloc(ctx, &ctx->Ealt[a], fb);
-        if (!rc) rc = dalloc(ctx, &ctx->Halt[a], fb);
+        rc = dalloc(ctx, &ctx->E[a], sb);
+        if (!rc) rc = dalloc(ctx, &ctx->H[a], sb);
+        if (!rc) rc = dalloc(ctx, &ctx->Ealt[a], sb);
+        if (!rc) rc = dalloc(ctx, &ctx->Halt[a], sb);
         if (!rc) rc = dalloc(ctx, &ctx->cb[a], fb);
     }
     if (!rc && g.npml > 0)
         for (int a = 0; a < 2 && !rc; a++) {
-            rc = dalloc(ctx, &ctx->Ezp[a], fb);
-            if (!rc) rc = dalloc(ctx, &ctx->Ezpalt[a], fb);
-            if (!rc) rc = dalloc(ctx, &ctx->Hzp[a], fb);
+            rc = dalloc(ctx, &ctx->Ezp[a], sb);
+            if (!rc) rc = dalloc(ctx, &ctx->Ezpalt[a], sb);
+            if (!rc) rc = dalloc(ctx, &ctx->Hzp[a], sb);
         }
     if (!rc) rc = dalloc(ctx, (void **)&ctx->res, 4 * (kMaxIter + 1) * sizeof(unsigned long long));
     if (!rc) rc = dalloc(ctx, (void **)&ctx->bar, sizeof(unsigned long long));
@@ -1092,7 +1143,9 @@ int mmx_create(const mmx_grid_desc *desc, void *cuda_stream, mmx_ctx **out)
         rc = is_fp64(ctx) ? upload_table<double>(ctx, &ctx->dampE, dE) : upload_table<float>(ctx, &ctx->dampE, dE);
         if (!rc) rc = is_fp64(ctx) ? upload_table<double>(ctx, &ctx->dampH, dH) : upload_table<float>(ctx, &ctx->dampH, dH);
     }
-    if (!rc) rc = is_fp64(ctx) ? set_materials_t<double>(ctx) : set_materials_t<float>(ctx);
+    if (!rc)
+        rc = is_fp64(ctx) ? set_materials_t<double>(ctx)
+             : is_fp16(ctx) ? set_materials_t<float, __half>(ctx) : set_materials_t<float>(ctx);
     if (rc) {
         *out = ctx;
         return rc;
@@ -1232,7 +1285,8 @@ int mmx_set_materials(mmx_ctx *ctx, const double *eps_r, const double *sigma, co
     } else {
         for (int a = 0; a < 3; a++) ctx->lo[a] = ctx->hi[a] = 0;
     }
-    return is_fp64(ctx) ? set_materials_t<double>(ctx) : set_materials_t<float>(ctx);
+    return is_fp64(ctx) ? set_materials_t<double>(ctx)
+           : is_fp16(ctx) ? set_materials_t<float, __half>(ctx) : set_materials_t<float>(ctx);
 }
 
 int mmx_set_bias(mmx_ctx *ctx, double hx, double hy, double hz)
@@ -1282,6 +1336,7 @@ int mmx_set_field(mmx_ctx *ctx, int id, const double *host, long long n)
     if (!field_ext(ctx, id, e)) return fail(ctx, MMX_ERR_INVALID, "bad field id %d", id);
     if (n != (long long)e[0] * e[1] * e[2]) return fail(ctx, MMX_ERR_INVALID, "field %d needs %lld values", id, (long long)e[0] * e[1] * e[2]);
     ctx->walls_dirty = true;
+    ctx->touched = true;
     return is_fp64(ctx) ? copy_field_t<double>(ctx, id, const_cast<double *>(host), n, 1)
                         : copy_field_t<float>(ctx, id, const_cast<double *>(host), n, 1);
 }
@@ -1386,7 +1441,13 @@ int mmx_step(mmx_ctx *ctx, int nsteps)
     // arrays between calls (where the API reads and writes it)
     int rc = fp64 ? box_m_sync<double>(ctx, 1) : box_m_sync<float>(ctx, 1);
     if (rc) return rc;
-    if (ctx->path == MMX_PATH_FUSED && !hard)
+    ctx->touched = true;
+    if (is_fp16(ctx)) {
+        if (ctx->path != MMX_PATH_FUSED || hard)
+            rc = fail(ctx, MMX_ERR_INVALID, "FP16 storage runs the fused path without hard sources");
+        else
+            rc = step_fused<float, __half>(ctx, nsteps);
+    } else if (ctx->path == MMX_PATH_FUSED && !hard)
         rc = fp64 ? step_fused<double>(ctx, nsteps) : step_fused<float>(ctx, nsteps);
     else
         rc = fp64 ? step_plain<double>(ctx, nsteps) : step_plain<float>(ctx, nsteps);
@@ -1477,6 +1538,18 @@ int mmx_get_profile(mmx_ctx *ctx, mmx_kernel_profile *out, int cap, int reset)
     return m;
 }
 
+int mmx_set_storage_scale(mmx_ctx *ctx, double sE, double sH)
+{
+    if (!ctx || !ctx->E[0]) return MMX_ERR_INVALID;
+    if (!is_fp16(ctx)) return fail(ctx, MMX_ERR_INVALID, "storage scales apply to MMX_FP16 contexts");
+    if (ctx->touched) return fail(ctx, MMX_ERR_INVALID, "set the storage scales before any field or step");
+    if (!(sE > 0) || !(sH > 0) || !std::isfinite(sE) || !std::isfinite(sH))
+        return fail(ctx, MMX_ERR_INVALID, "storage scales must be positive and finite");
+    ctx->sE = sE;
+    ctx->sH = sH;
+    return MMX_OK;
+}
+
 int mmx_add_probe(mmx_ctx *ctx, int field, int i, int j, int k)
 {
     if (!ctx || !ctx->E[0]) return MMX_ERR_INVALID;
@@ -1517,7 +1590,8 @@ long long mmx_get_probes(mmx_ctx *ctx, double *out, long long max_rows, int rese
 int mmx_energy(mmx_ctx *ctx, double *out)
 {
     if (!ctx || !ctx->E[0] || !out) return MMX_ERR_INVALID;
-    int rc = is_fp64(ctx) ? energy_t<double>(ctx, out) : energy_t<float>(ctx, out);
+    int rc = is_fp64(ctx) ? energy_t<double>(ctx, out)
+             : is_fp16(ctx) ? energy_t<float, __half>(ctx, out) : energy_t<float>(ctx, out);
     return rc ? rc : read_status(ctx);
 }
 

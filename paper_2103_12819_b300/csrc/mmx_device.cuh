@@ -3,6 +3,7 @@
 // arXiv 2103.12819, Sec. 3) for sm_103a.  Everything here is templated on
 // the storage/arithmetic type T (double or float).
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -71,11 +72,32 @@ template <typename T> struct Src {
     double amp, f0, tp, t0;
 };
 
-template <typename T> struct Fields {
-    T *E[3];
-    T *H[3];
-    T *Ezp[2];          // z-derivative parts of Ex, Ey in the PML (else null)
-    T *Hzp[2];          // z-derivative parts of Hx, Hy in the PML (else null)
+// Field storage: S is the stored type of E, H and their PML split parts, T
+// the arithmetic type.  FP16 storage (S = __half, T = float) holds each value
+// divided by a per-field scale (sE for E, sH for H) so that the fields sit in
+// FP16's range; ld_s / st_s convert.  With S = T the scales are not applied.
+__device__ __forceinline__ float ld_s(const __half *p, float sc)
+{
+    return __half2float(*p) * sc;
+}
+template <typename T> __device__ __forceinline__ T ld_s(const T *p, T)
+{
+    return *p;
+}
+__device__ __forceinline__ void st_s(__half *p, float v, float isc)
+{
+    *p = __float2half_rn(v * isc);
+}
+template <typename T> __device__ __forceinline__ void st_s(T *p, T v, T)
+{
+    *p = v;
+}
+
+template <typename T, typename S = T> struct Fields {
+    S *E[3];
+    S *H[3];
+    S *Ezp[2];          // z-derivative parts of Ex, Ey in the PML (else null)
+    S *Hzp[2];          // z-derivative parts of Hx, Hy in the PML (else null)
     const T *ca[3];     // E update: E' = ca E + cb (curl H - J); ca null -> 1
     const T *cb[3];
     const T *fh[3];     // H update: H' = H - fh curl E; fh null -> fh0
@@ -86,6 +108,7 @@ template <typename T> struct Fields {
     const T *src_amp;   // g(t) of every source for the current step
     const T *prof[2];   // TE10 profile sin(pi x/W): [0] at x = i dx, [1] at (i+1/2) dx
     int *err;
+    T sE, sH, isE, isH; // storage scales and their inverses (FP16 storage only)
 };
 
 // Magnetic box: the bounding box of the magnetic faces grown by one face on
@@ -176,20 +199,20 @@ __device__ __forceinline__ void curl_h(const Geo &g, T *const H[3], const T inv_
 }
 
 // (curl E) on an H face of family d, split the same way.
-template <typename T>
-__device__ __forceinline__ void curl_e(const Geo &g, T *const E[3], const T inv_d[3], int d, int i, int j,
-                                       int k, T &rest, T &zp)
+template <typename T, typename S>
+__device__ __forceinline__ void curl_e(const Geo &g, S *const E[3], const T inv_d[3], int d, int i, int j,
+                                       int k, T &rest, T &zp, T sE = T(1))
 {
     const T idx = inv_d[0], idy = inv_d[1], idz = inv_d[2];
+    auto e = [&](int c, int a, int b2, int c2) { return ld_s(E[c] + gidx(g, a, b2, c2), sE); };
     if (d == 0) {
-        rest = (E[2][gidx(g, i, j + 1, k)] - E[2][gidx(g, i, j, k)]) * idy;
-        zp = -(E[1][gidx(g, i, j, k + 1)] - E[1][gidx(g, i, j, k)]) * idz;
+        rest = (e(2, i, j + 1, k) - e(2, i, j, k)) * idy;
+        zp = -(e(1, i, j, k + 1) - e(1, i, j, k)) * idz;
     } else if (d == 1) {
-        zp = (E[0][gidx(g, i, j, k + 1)] - E[0][gidx(g, i, j, k)]) * idz;
-        rest = -(E[2][gidx(g, i + 1, j, k)] - E[2][gidx(g, i, j, k)]) * idx;
+        zp = (e(0, i, j, k + 1) - e(0, i, j, k)) * idz;
+        rest = -(e(2, i + 1, j, k) - e(2, i, j, k)) * idx;
     } else {
-        rest = (E[1][gidx(g, i + 1, j, k)] - E[1][gidx(g, i, j, k)]) * idx
-             - (E[0][gidx(g, i, j + 1, k)] - E[0][gidx(g, i, j, k)]) * idy;
+        rest = (e(1, i + 1, j, k) - e(1, i, j, k)) * idx - (e(0, i, j + 1, k) - e(0, i, j, k)) * idy;
         zp = T(0);
     }
 }
@@ -207,8 +230,8 @@ __device__ __forceinline__ double waveform(double amp, double f0, double tp, dou
 // waveform value of each source precomputed for the step.  Indices on
 // periodic axes are compared modulo n so that a duplicate node receives the
 // same current.
-template <typename T>
-__device__ __forceinline__ T j_source(const Geo &g, const Fields<T> &f, const Src<T> *src, int nsrc, int c,
+template <typename T, typename S>
+__device__ __forceinline__ T j_source(const Geo &g, const Fields<T, S> &f, const Src<T> *src, int nsrc, int c,
                                       int i, int j, int k)
 {
     T J = T(0);
@@ -271,27 +294,27 @@ __device__ __forceinline__ void e_edge(const Geo &g, const Fields<T> &f, int c, 
 // (the same array for the streaming kernel).
 // The same with the old value hn passed in (the box kernel's second half
 // step takes it from its box-local iterate).
-template <typename T>
-__device__ __forceinline__ T h_face_nonmag_val(const Geo &g, const Fields<T> &f, int d, int i, int j, int k,
+template <typename T, typename S>
+__device__ __forceinline__ T h_face_nonmag_val(const Geo &g, const Fields<T, S> &f, int d, int i, int j, int k,
                                                T hn)
 {
     size_t q = gidx(g, i, j, k);
     int ix[3] = {i, j, k};
     if (wall_node(g, d, ix[d])) {
-        if (d < 2 && f.Hzp[d]) f.Hzp[d][q] = T(0);
+        if (d < 2 && f.Hzp[d]) st_s(f.Hzp[d] + q, T(0), f.isH);
         return T(0);
     }
     T rest, zp;
-    curl_e(g, f.E, f.inv_d, d, i, j, k, rest, zp);
+    curl_e(g, f.E, f.inv_d, d, i, j, k, rest, zp, f.sE);
     T fh = f.fh[d] ? f.fh[d][q] : f.fh0;
     T v;
     if (d < 2 && pml_h_plane(g, k)) {
         T h = f.dampH[k];
-        T hz = f.Hzp[d][q];
+        T hz = ld_s(f.Hzp[d] + q, f.sH);
         T hr = hn - hz;
         T hz1 = (hz * h - fh * zp) * h;
         T hr1 = hr - fh * rest;
-        f.Hzp[d][q] = hz1;
+        st_s(f.Hzp[d] + q, hz1, f.isH);
         v = hr1 + hz1;
     } else {
         v = hn - fh * (rest + zp);
@@ -299,11 +322,11 @@ __device__ __forceinline__ T h_face_nonmag_val(const Geo &g, const Fields<T> &f,
     return v;
 }
 
-template <typename T>
-__device__ __forceinline__ T h_face_nonmag(const Geo &g, const Fields<T> &f, int d, int i, int j, int k,
-                                           const T *Hin)
+template <typename T, typename S>
+__device__ __forceinline__ T h_face_nonmag(const Geo &g, const Fields<T, S> &f, int d, int i, int j, int k,
+                                           const S *Hin)
 {
-    return h_face_nonmag_val(g, f, d, i, j, k, Hin[gidx(g, i, j, k)]);
+    return h_face_nonmag_val(g, f, d, i, j, k, ld_s(Hin + gidx(g, i, j, k), f.sH));
 }
 
 // ------------------------------------------------ LLG: one iterate

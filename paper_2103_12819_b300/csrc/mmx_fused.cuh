@@ -4,7 +4,8 @@
 //
 // Work decomposition.  A CTA owns a strip of W = 32 V columns (V = 16 bytes /
 // sizeof(T): 4 floats or 2 doubles per lane, moved with one 16-byte load or
-// store) by BY rows, and marches its z chunk plane by plane.  Lane L of warp
+// store; with FP16 storage the same 4 columns move as 8 bytes) by BY rows,
+// and marches its z chunk plane by plane.  Lane L of warp
 // w holds columns x0 + V L ... x0 + V L + V-1 of row y0 + w.  Neighbours
 // along x come from warp shuffles; neighbours along y from double-buffered
 // shared-memory rows.  Warp BY is a halo warp: it computes E^(n+1) of row
@@ -26,13 +27,13 @@
 
 namespace mmx {
 
-template <typename T> struct FusedIO {
-    const T *Eo[3];
-    const T *Ho[3];
-    T *En[3];
-    T *Hn[3];
-    const T *Zo[2];     // PML split part of Ex, Ey (old)
-    T *Zn[2];           // (new)
+template <typename S> struct FusedIO {
+    const S *Eo[3];
+    const S *Ho[3];
+    S *En[3];
+    S *Hn[3];
+    const S *Zo[2];     // PML split part of Ex, Ey (old)
+    S *Zn[2];           // (new)
 };
 
 template <typename T> struct Lanes;
@@ -97,9 +98,55 @@ template <typename T, int V> __device__ __forceinline__ void vcopy(T (&d)[V], co
     for (int e = 0; e < V; e++) d[e] = s[e];
 }
 
-// Asynchronous global -> shared copies (cp.async): 16 bytes, or one element
-// for the halo column; a false predicate zero-fills the destination and
-// reads nothing (the source operand is then the array base, always valid).
+// V stored values (S) -> V values of T times sc, and back (times isc): 16-byte
+// moves for FP32/FP64 storage, 8-byte moves of 4 halves for FP16 storage.
+template <typename S> struct SV;
+template <> struct SV<float> {
+    __device__ static void gld(float (&r)[4], const float *p, float) { vload(r, p); }
+    __device__ static void gld_rw(float (&r)[4], const float *p, float) { vload_rw(r, p); }
+    __device__ static void sld(float (&r)[4], const float *p, float) { sload(r, p); }
+    __device__ static void gst(float *p, const float (&r)[4], float) { vstore(p, r); }
+};
+template <> struct SV<double> {
+    __device__ static void gld(double (&r)[2], const double *p, double) { vload(r, p); }
+    __device__ static void gld_rw(double (&r)[2], const double *p, double) { vload_rw(r, p); }
+    __device__ static void sld(double (&r)[2], const double *p, double) { sload(r, p); }
+    __device__ static void gst(double *p, const double (&r)[2], double) { vstore(p, r); }
+};
+template <> struct SV<__half> {
+    __device__ static void cvt(float (&r)[4], uint2 u, float sc)
+    {
+        __half2 a, b;
+        memcpy(&a, &u.x, 4);
+        memcpy(&b, &u.y, 4);
+        const float2 fa = __half22float2(a), fb = __half22float2(b);
+        r[0] = fa.x * sc; r[1] = fa.y * sc; r[2] = fb.x * sc; r[3] = fb.y * sc;
+    }
+    __device__ static void gld(float (&r)[4], const __half *p, float sc)
+    {
+        cvt(r, __ldg(reinterpret_cast<const uint2 *>(p)), sc);
+    }
+    __device__ static void gld_rw(float (&r)[4], const __half *p, float sc)
+    {
+        cvt(r, *reinterpret_cast<const uint2 *>(p), sc);
+    }
+    __device__ static void sld(float (&r)[4], const __half *p, float sc)
+    {
+        cvt(r, *reinterpret_cast<const uint2 *>(p), sc);
+    }
+    __device__ static void gst(__half *p, const float (&r)[4], float isc)
+    {
+        const __half2 a = __floats2half2_rn(r[0] * isc, r[1] * isc), b = __floats2half2_rn(r[2] * isc, r[3] * isc);
+        uint2 u;
+        memcpy(&u.x, &a, 4);
+        memcpy(&u.y, &b, 4);
+        *reinterpret_cast<uint2 *>(p) = u;
+    }
+};
+
+// Asynchronous global -> shared copies (cp.async): 16 bytes, 8 or 4 bytes;
+// a false predicate zero-fills the destination and reads nothing (the
+// source operand is then the array base, always valid).
 __device__ __forceinline__ unsigned smem_u32(const void *p)
 {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -110,11 +157,15 @@ __device__ __forceinline__ void cp16(void *dst, const void *src, const void *bas
                  "l"(on ? src : base), "r"(on ? 16 : 0)
                  : "memory");
 }
-template <typename T> __device__ __forceinline__ void cp1(T *dst, const T *src, const T *base, bool on)
+template <int N> __device__ __forceinline__ void cpn(void *dst, const void *src, const void *base, bool on)
 {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_u32(dst)), "l"(on ? src : base),
-                 "n"(sizeof(T)), "r"(on ? (int)sizeof(T) : 0)
-                 : "memory");
+    if constexpr (N == 16) {
+        cp16(dst, src, base, on);
+    } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_u32(dst)),
+                     "l"(on ? src : base), "n"(N), "r"(on ? N : 0)
+                     : "memory");
+    }
 }
 __device__ __forceinline__ void cp_commit()
 {
@@ -126,43 +177,56 @@ template <int N> __device__ __forceinline__ void cp_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Shared-memory layout of the vectorised kernel (elements of T), a ring of
-// ST plane stages:
-//   stage [ST][NF][R][W] per plane: Hx, Hy (layer k+1/2), Hz (node k), Ex, Ey,
-//                        Ez, cbx, cby, cbz [, cax, cay, caz] of rows y0..y0+BY
-//   up    [ST][2][W]     Hx, Hz of row y0-1
-//   left  [ST][2][RP]    Hy, Hz of column x0-1, one per row
-//   sEx, sEz [2][R][W]   E^(n+1) exchanged between rows
-template <typename T, int BY, bool GEN, int ST> struct VecLayout {
+// Shared-memory layout of the vectorised kernel, a ring of ST plane stages
+// (byte offsets, every region a multiple of 16 bytes):
+//   sst [ST][6][R][W] of S  per plane: Hx, Hy (layer k+1/2), Hz (node k),
+//                           Ex, Ey, Ez of rows y0..y0+BY
+//   cst [ST][NC][R][W] of T cbx, cby, cbz [, cax, cay, caz]
+//   up  [ST][2][W] of S     Hx, Hz of row y0-1
+//   left [ST][2][R][LW] of S  Hy, Hz of column x0-1 (FP16: the 4-byte pair
+//                           ending there), one entry per row
+//   sEx, sEz [2][R][W] of T E^(n+1) exchanged between rows
+template <typename T, typename S, int BY, bool GEN, int ST> struct VecLayout {
     static constexpr int V = Lanes<T>::V;
     static constexpr int W = 32 * V;
     static constexpr int R = BY + 1;
-    static constexpr int RP = (R + 3) / 4 * 4;
-    static constexpr int NF = GEN ? 12 : 9;
-    static constexpr int stage = 0;
-    static constexpr int up = stage + ST * NF * R * W;
-    static constexpr int left = up + ST * 2 * W;
-    static constexpr int ex = left + ST * 2 * RP;
-    static constexpr int ez = ex + 2 * R * W;
-    static constexpr int total = ez + 2 * R * W;
-    static constexpr size_t bytes = (size_t)total * sizeof(T);
+    static constexpr int NC = GEN ? 6 : 3;
+    static constexpr int LW = sizeof(S) >= 4 ? 1 : 4 / (int)sizeof(S);
+    static constexpr size_t al(size_t x) { return (x + 15) / 16 * 16; }
+    static constexpr size_t sst = 0;
+    static constexpr size_t cst = sst + al((size_t)ST * 6 * R * W * sizeof(S));
+    static constexpr size_t up = cst + al((size_t)ST * NC * R * W * sizeof(T));
+    static constexpr size_t left = up + al((size_t)ST * 2 * W * sizeof(S));
+    static constexpr size_t ex = left + al((size_t)ST * 2 * R * LW * sizeof(S));
+    static constexpr size_t ez = ex + al((size_t)2 * R * W * sizeof(T));
+    static constexpr size_t bytes = ez + al((size_t)2 * R * W * sizeof(T));
 };
 
-template <typename T, int BY, int ST, int NH, bool PMLK, bool GEN>
+template <typename T, typename S, int BY, int ST, int NH, bool PMLK, bool GEN>
 __global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
-    k_fused_vec(const __grid_constant__ Geo g, const __grid_constant__ Fields<T> f,
-                const __grid_constant__ FusedIO<T> io, const Src<T> *__restrict__ src, int nsrc, int chunk,
+    k_fused_vec(const __grid_constant__ Geo g, const __grid_constant__ Fields<T, S> f,
+                const __grid_constant__ FusedIO<S> io, const Src<T> *__restrict__ src, int nsrc, int chunk,
                 int xstride)
 {
-    using L = VecLayout<T, BY, GEN, ST>;
-    constexpr int V = L::V, W = L::W, R = L::R, RP = L::RP, NF = L::NF;
+    using L = VecLayout<T, S, BY, GEN, ST>;
+    using P = SV<S>;
+    constexpr int V = L::V, W = L::W, R = L::R, NC = L::NC, LW = L::LW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *const sm = reinterpret_cast<T *>(smem_raw);
-    auto S = [&](int st, int fld, int row) -> T * { return sm + L::stage + ((st * NF + fld) * R + row) * W; };
-    auto U = [&](int st, int fld) -> T * { return sm + L::up + (st * 2 + fld) * W; };
-    auto Lf = [&](int st, int fld) -> T * { return sm + L::left + (st * 2 + fld) * RP; };
-    auto SEx = [&](int bb, int row) -> T * { return sm + L::ex + (bb * R + row) * W; };
-    auto SEz = [&](int bb, int row) -> T * { return sm + L::ez + (bb * R + row) * W; };
+    // S-typed stage fields 0-5: Hx Hy Hz Ex Ey Ez; T-typed 0-5: cb, ca
+    auto SS = [&](int st, int fld, int row) -> S * {
+        return reinterpret_cast<S *>(smem_raw + L::sst) + ((st * 6 + fld) * R + row) * W;
+    };
+    auto SC = [&](int st, int fld, int row) -> T * {
+        return reinterpret_cast<T *>(smem_raw + L::cst) + ((st * NC + fld) * R + row) * W;
+    };
+    auto U = [&](int st, int fld) -> S * { return reinterpret_cast<S *>(smem_raw + L::up) + (st * 2 + fld) * W; };
+    auto Lf = [&](int st, int fld) -> S * {
+        return reinterpret_cast<S *>(smem_raw + L::left) + (st * 2 + fld) * R * LW;
+    };
+    auto SEx = [&](int bb, int row) -> T * { return reinterpret_cast<T *>(smem_raw + L::ex) + (bb * R + row) * W; };
+    auto SEz = [&](int bb, int row) -> T * { return reinterpret_cast<T *>(smem_raw + L::ez) + (bb * R + row) * W; };
+    const T sE = f.sE, sH = f.sH, isE = f.isE, isH = f.isH;
+    constexpr int VB = V * (int)sizeof(S);      // bytes of one lane's S values
 
     const int lane = threadIdx.x, w = threadIdx.y;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
@@ -207,22 +271,25 @@ __global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
         const int ck = cell_nb(g, 2, k);
         const unsigned kn = (unsigned)k * XY, kc = (unsigned)max(ck, 0) * XY;
         const bool lay = ck >= 0;
-        cp16(S(st, 0, w) + col, io.Ho[0] + rb + kc, io.Ho[0], lane_on && lay);
-        cp16(S(st, 1, w) + col, io.Ho[1] + rb + kc, io.Ho[1], lane_on && lay);
-        cp16(S(st, 2, w) + col, io.Ho[2] + rb + kn, io.Ho[2], lane_on);
+        cpn<VB>(SS(st, 0, w) + col, io.Ho[0] + rb + kc, io.Ho[0], lane_on && lay);
+        cpn<VB>(SS(st, 1, w) + col, io.Ho[1] + rb + kc, io.Ho[1], lane_on && lay);
+        cpn<VB>(SS(st, 2, w) + col, io.Ho[2] + rb + kn, io.Ho[2], lane_on);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            cp16(S(st, 3 + c, w) + col, io.Eo[c] + rb + kn, io.Eo[c], lane_on);
-            cp16(S(st, 6 + c, w) + col, f.cb[c] + rb + kn, f.cb[c], lane_on);
-            if (GEN && f.ca[c]) cp16(S(st, 9 + c, w) + col, f.ca[c] + rb + kn, f.ca[c], lane_on);
+            cpn<VB>(SS(st, 3 + c, w) + col, io.Eo[c] + rb + kn, io.Eo[c], lane_on);
+            cp16(SC(st, c, w) + col, f.cb[c] + rb + kn, f.cb[c], lane_on);
+            if (GEN && f.ca[c]) cp16(SC(st, 3 + c, w) + col, f.ca[c] + rb + kn, f.ca[c], lane_on);
         }
         if (w == 0) {
-            cp16(U(st, 0) + col, io.Ho[0] + rbu + kc, io.Ho[0], up_on && lay);
-            cp16(U(st, 1) + col, io.Ho[2] + rbu + kn, io.Ho[2], up_on);
+            cpn<VB>(U(st, 0) + col, io.Ho[0] + rbu + kc, io.Ho[0], up_on && lay);
+            cpn<VB>(U(st, 1) + col, io.Ho[2] + rbu + kn, io.Ho[2], up_on);
         }
         if (lane == 0) {
-            cp1(Lf(st, 0) + w, io.Ho[1] + rbl + kc, io.Ho[1], left_on && lay);
-            cp1(Lf(st, 1) + w, io.Ho[2] + rbl + kn, io.Ho[2], left_on);
+            // the LW-element group ending at column x0-1 (one element unless
+            // the element is narrower than the 4-byte minimum copy)
+            constexpr int CB = LW * (int)sizeof(S);
+            cpn<CB>(Lf(st, 0) + w * LW, io.Ho[1] + rbl + kc - (LW - 1), io.Ho[1], left_on && lay);
+            cpn<CB>(Lf(st, 1) + w * LW, io.Ho[2] + rbl + kn - (LW - 1), io.Ho[2], left_on);
         }
         cp_commit();
     };
@@ -235,8 +302,8 @@ __global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
     {
         const int ckm = cell_nb(g, 2, k0 - 1);
         if (lane_on && ckm >= 0) {
-            vload(hxp, io.Ho[0] + rb + (unsigned)ckm * XY);
-            vload(hyp, io.Ho[1] + rb + (unsigned)ckm * XY);
+            P::gld(hxp, io.Ho[0] + rb + (unsigned)ckm * XY, sH);
+            P::gld(hyp, io.Ho[1] + rb + (unsigned)ckm * XY, sH);
         } else {
             vzero<T, V>(hxp);
             vzero<T, V>(hyp);
@@ -266,22 +333,22 @@ __global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
         }
 
         T hx[V], hy[V], hz[V], hzu[V], hxu[V];
-        sload(hx, S(st, 0, w) + col);
-        sload(hy, S(st, 1, w) + col);
-        sload(hz, S(st, 2, w) + col);
+        P::sld(hx, SS(st, 0, w) + col, sH);
+        P::sld(hy, SS(st, 1, w) + col, sH);
+        P::sld(hz, SS(st, 2, w) + col, sH);
         if (w == 0) {
-            sload(hxu, U(st, 0) + col);
-            sload(hzu, U(st, 1) + col);
+            P::sld(hxu, U(st, 0) + col, sH);
+            P::sld(hzu, U(st, 1) + col, sH);
         } else {
-            sload(hxu, S(st, 0, w - 1) + col);
-            sload(hzu, S(st, 2, w - 1) + col);
+            P::sld(hxu, SS(st, 0, w - 1) + col, sH);
+            P::sld(hzu, SS(st, 2, w - 1) + col, sH);
         }
         // column i-1 of element 0: previous lane's last element, or the halo
         T hzl = __shfl_up_sync(0xffffffffu, hz[V - 1], 1);
         T hyl = __shfl_up_sync(0xffffffffu, hy[V - 1], 1);
         if (lane == 0) {
-            hyl = Lf(st, 0)[w];
-            hzl = Lf(st, 1)[w];
+            hyl = ld_s(Lf(st, 0) + w * LW + (LW - 1), sH);
+            hzl = ld_s(Lf(st, 1) + w * LW + (LW - 1), sH);
         }
 
         // ---- E^(n+1) at plane k
@@ -294,17 +361,17 @@ __global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
             T eo[3][V], cb[3][V], ca[3][V];
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                sload(eo[c], S(st, 3 + c, w) + col);
-                sload(cb[c], S(st, 6 + c, w) + col);
+                P::sld(eo[c], SS(st, 3 + c, w) + col, sE);
+                sload(cb[c], SC(st, c, w) + col);
                 if (GEN && f.ca[c])
-                    sload(ca[c], S(st, 9 + c, w) + col);
+                    sload(ca[c], SC(st, 3 + c, w) + col);
                 else
                     vfill<T, V>(ca[c], T(1));
             }
             T zo0[V], zo1[V];
             if (pml && lane_on) {
-                vload(zo0, io.Zo[0] + q);
-                vload(zo1, io.Zo[1] + q);
+                P::gld(zo0, io.Zo[0] + q, sE);
+                P::gld(zo1, io.Zo[1] + q, sE);
             } else {
                 vzero<T, V>(zo0);
                 vzero<T, V>(zo1);
@@ -370,12 +437,12 @@ __global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
             }
         }
         if (store && own_plane) {
-            vstore(io.En[0] + q, ex);
-            vstore(io.En[1] + q, ey);
-            if (k < nz) vstore(io.En[2] + q, ez);
+            P::gst(io.En[0] + q, ex, isE);
+            P::gst(io.En[1] + q, ey, isE);
+            if (k < nz) P::gst(io.En[2] + q, ez, isE);
             if (pml) {
-                vstore(io.Zn[0] + q, zn0);
-                vstore(io.Zn[1] + q, zn1);
+                P::gst(io.Zn[0] + q, zn0, isE);
+                P::gst(io.Zn[1] + q, zn1, isE);
             }
 #pragma unroll
             for (int e = 0; e < V; e++) acc += ex[e] + ey[e] + ez[e];
@@ -403,7 +470,7 @@ __global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
                     hn[e] = (cin[e] && !wz) ? v : T(0);
                     acc += hn[e];
                 }
-                vstore(io.Hn[2] + q, hn);
+                P::gst(io.Hn[2] + q, hn, isH);
             }
             if (store && k > k0) {
                 const int kl = k - 1;
@@ -420,8 +487,8 @@ __global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
                 else
                     vfill<T, V>(fhy, fh0);
                 if (hp) {
-                    vload_rw(sx, f.Hzp[0] + ql);
-                    vload_rw(sy, f.Hzp[1] + ql);
+                    P::gld_rw(sx, f.Hzp[0] + ql, sH);
+                    P::gld_rw(sy, f.Hzp[1] + ql, sH);
                 } else {
                     vzero<T, V>(sx);
                     vzero<T, V>(sy);
@@ -475,11 +542,11 @@ __global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
                     }
                     acc += hxn[e] + hyn[e];
                 }
-                vstore(io.Hn[0] + ql, hxn);
-                vstore(io.Hn[1] + ql, hyn);
+                P::gst(io.Hn[0] + ql, hxn, isH);
+                P::gst(io.Hn[1] + ql, hyn, isH);
                 if (hp) {
-                    vstore(f.Hzp[0] + ql, sx);
-                    vstore(f.Hzp[1] + ql, sy);
+                    P::gst(f.Hzp[0] + ql, sx, isH);
+                    P::gst(f.Hzp[1] + ql, sy, isH);
                 }
             }
         }

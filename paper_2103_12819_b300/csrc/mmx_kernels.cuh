@@ -240,12 +240,13 @@ template <typename T> __global__ void k_box_m_sync(Box<T> b, int to_rec)
 }
 
 // Point probes: row[p] = E component probe[p].x at padded index probe[p].y.
-template <typename T> __global__ void k_probe(Ptr3<T> E, const int2 *__restrict__ probe, int np, double *row)
+template <typename S, typename T>
+__global__ void k_probe(Ptr3<S> E, T sE, const int2 *__restrict__ probe, int np, double *row)
 {
     const int p = threadIdx.x;
     if (p < np) {
         const int2 q = probe[p];
-        row[p] = (double)E.p[q.x][q.y];
+        row[p] = (double)ld_s(E.p[q.x] + q.y, sE);
     }
 }
 
@@ -276,6 +277,23 @@ __global__ void k_copy_field(const Geo g, T *dev, const Box<T> b, int boxed, int
     } else if (in) {
         dev[bidx(b.lo, b.bx, b.by, i, j, k)] = (T)host_like[t];
     }
+}
+
+// The same for an FP16-stored E/H field: value = stored * scale.
+__global__ void k_copy_field_h(const Geo g, __half *dev, float scale, int e0, int e1, int e2, double *host_like,
+                               int dir)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long N = (long long)e0 * e1 * e2;
+    if (t >= N) return;
+    int i = (int)(t % e0);
+    int j = (int)((t / e0) % e1);
+    int k = (int)(t / ((long long)e0 * e1));
+    size_t q = gidx(g, i, j, k);
+    if (dir == 0)
+        host_like[t] = (double)__half2float(dev[q]) * (double)scale;
+    else
+        dev[q] = __float2half_rn((float)(host_like[t] / (double)scale));
 }
 
 // On a periodic axis the node index n repeats node index 0 (padded arrays).
@@ -318,9 +336,9 @@ __global__ void __launch_bounds__(256) k_e_update(const __grid_constant__ Geo g,
 
 // Steps 1/3 on every face outside the magnetic box (those are all
 // non-magnetic); in place.
-template <typename T>
+template <typename T, typename S = T>
 __global__ void __launch_bounds__(256) k_h_update(const __grid_constant__ Geo g,
-                                                  const __grid_constant__ Fields<T> f, int blo0, int blo1,
+                                                  const __grid_constant__ Fields<T, S> f, int blo0, int blo1,
                                                   int blo2, int bhi0, int bhi1, int bhi2)
 {
     int i, j, k;
@@ -332,7 +350,7 @@ __global__ void __launch_bounds__(256) k_h_update(const __grid_constant__ Geo g,
         if (!face_valid(g, d, i, j, k)) continue;
         size_t q = gidx(g, i, j, k);
         T v = h_face_nonmag(g, f, d, i, j, k, f.H[d]);
-        f.H[d][q] = v;
+        st_s(f.H[d] + q, v, f.isH);
         if (!isfinite(v)) atomicOr(f.err, kErrNonFinite);
     }
 }
@@ -440,12 +458,12 @@ __device__ __forceinline__ FaceOf face_of(int4 e)
 // four-point means of the two transverse families (Sec. 3.1), from the padded
 // global H (mode 0) or from box-local iterates (mode 1).  The family is a
 // template argument so that every index below is in registers.
-template <int D, typename T>
-__device__ __forceinline__ void h_vector(const Geo &g, const Box<T> &b, T *const Hg[3], T *const Hb[3],
-                                         int mode, int i, int j, int k, T h[3])
+template <int D, typename T, typename SG>
+__device__ __forceinline__ void h_vector(const Geo &g, const Box<T> &b, SG *const Hg[3], T *const Hb[3],
+                                         int mode, int i, int j, int k, T h[3], T sH = T(1))
 {
     const int ix[3] = {i, j, k};
-    h[D] = mode == 0 ? Hg[D][gidx32(g, i, j, k)] : Hb[D][bidx32(b.lo, b.bx, b.by, i, j, k)];
+    h[D] = mode == 0 ? ld_s(Hg[D] + gidx32(g, i, j, k), sH) : Hb[D][bidx32(b.lo, b.bx, b.by, i, j, k)];
 #pragma unroll
     for (int t = 0; t < 3; t++) {
         if (t == D) continue;
@@ -460,7 +478,7 @@ __device__ __forceinline__ void h_vector(const Geo &g, const Box<T> &b, T *const
                 int q[3] = {ix[0], ix[1], ix[2]};
                 q[D] = nd;
                 q[t] = ix[t] + ot;
-                sum += mode == 0 ? Hg[t][gidx32(g, q[0], q[1], q[2])]
+                sum += mode == 0 ? ld_s(Hg[t] + gidx32(g, q[0], q[1], q[2]), sH)
                                  : Hb[t][bidx32(b.lo, b.bx, b.by, q[0], q[1], q[2])];
                 cnt++;
             }
@@ -496,13 +514,13 @@ template <typename T> struct FirstIn {
 // the global H (SECOND false) or the previous half step's box-local iterate
 // Hp (SECOND true); M^n is the face record, plus the previous half step's
 // converged increment dmp when SECOND.
-template <int D, bool SECOND, typename T>
-__device__ __forceinline__ void first_load(const Geo &g, const Fields<T> &f, const Box<T> &b, T *const Hin[3],
+template <int D, bool SECOND, typename T, typename S>
+__device__ __forceinline__ void first_load(const Geo &g, const Fields<T, S> &f, const Box<T> &b, S *const Hin[3],
                                            T *const Hp[3], const Q4<T> *dmp, const FaceOf &fo, int t,
                                            FirstIn<T> &in)
 {
     in.cs = q4_load(b.cst + t);
-    curl_e(g, f.E, f.inv_d, D, fo.i, fo.j, fo.k, in.rest, in.zp);
+    curl_e(g, f.E, f.inv_d, D, fo.i, fo.j, fo.k, in.rest, in.zp, f.sE);
     const Q4<T> m0 = q4_load(b.mn + t);
     if (SECOND) {
         const Q4<T> d0 = q4_load(dmp + t);
@@ -510,13 +528,13 @@ __device__ __forceinline__ void first_load(const Geo &g, const Fields<T> &f, con
         in.Mn[1] = m0.y + d0.y;
         in.Mn[2] = m0.z + d0.z;
         in.hn = Hp[D][fo.l];
-        h_vector<D>(g, b, Hp, Hp, 1, fo.i, fo.j, fo.k, in.h);
+        h_vector<D>(g, b, Hin, Hp, 1, fo.i, fo.j, fo.k, in.h);
     } else {
         in.Mn[0] = m0.x;
         in.Mn[1] = m0.y;
         in.Mn[2] = m0.z;
-        in.hn = Hin[D][gidx32(g, fo.i, fo.j, fo.k)];
-        h_vector<D>(g, b, Hin, Hin, 0, fo.i, fo.j, fo.k, in.h);
+        in.hn = ld_s(Hin[D] + gidx32(g, fo.i, fo.j, fo.k), f.sH);
+        h_vector<D>(g, b, Hin, Hp, 0, fo.i, fo.j, fo.k, in.h, f.sH);
     }
 }
 
@@ -554,11 +572,11 @@ __device__ __forceinline__ T first_finish(const Geo &g, const Box<T> &b, T *cons
 
 // Phase 0 on a non-magnetic face of family D: its final H in both iterate
 // buffers W0, W1.
-template <int D, bool SECOND, typename T>
-__device__ __forceinline__ void non_first(const Geo &g, const Fields<T> &f, T *const Hin[3], T *const Hp[3],
+template <int D, bool SECOND, typename T, typename S>
+__device__ __forceinline__ void non_first(const Geo &g, const Fields<T, S> &f, S *const Hin[3], T *const Hp[3],
                                           T *const W0[3], T *const W1[3], const FaceOf &fo)
 {
-    const T hn = SECOND ? Hp[D][fo.l] : Hin[D][gidx32(g, fo.i, fo.j, fo.k)];
+    const T hn = SECOND ? Hp[D][fo.l] : ld_s(Hin[D] + gidx32(g, fo.i, fo.j, fo.k), f.sH);
     const T v = h_face_nonmag_val(g, f, D, fo.i, fo.j, fo.k, hn);
     W0[D][fo.l] = v;
     W1[D][fo.l] = v;
@@ -604,12 +622,12 @@ __device__ __forceinline__ T next_finish(const Geo &g, const Box<T> &b, const Fa
 // Final H and M^(n+1/2) on one magnetic face of family D: H to the global
 // Hout, M into the face record (the box M is refreshed from the records at
 // the end of every mmx_step call).  Returns false if a value is not finite.
-template <int D, typename T>
+template <int D, typename T, typename S>
 __device__ __forceinline__ bool mag_store(const Geo &g, const Box<T> &b, const FaceOf &fo, int t,
-                                          T *const Hfin[3], T *const Hout[3], int fr)
+                                          T *const Hfin[3], S *const Hout[3], int fr, T isH)
 {
     const T v = Hfin[D][fo.l];
-    Hout[D][gidx32(g, fo.i, fo.j, fo.k)] = v;
+    st_s(Hout[D] + gidx32(g, fo.i, fo.j, fo.k), v, isH);
     const Q4<T> mq = q4_load(b.mn + t);
     const Q4<T> dq = q4_load(b.dm[fr] + t);
     const T m0 = mq.x + dq.x, m1 = mq.y + dq.y, m2 = mq.z + dq.z;
@@ -635,8 +653,8 @@ __device__ __forceinline__ bool mag_store(const Geo &g, const Box<T> &b, const F
 //   WRITE true:   H^(n+1/2) goes to the global Hout and M^(n+1/2) into the
 //                 records; otherwise both stay in the iterate buffers.
 // Returns the final iterate parity, or -1 if a barrier timed out.
-template <bool SECOND, bool WRITE, typename T>
-__device__ int hm_half_step(const Geo &g, const Fields<T> &f, const Box<T> &b, T *const Hin[3], T *const Hout[3],
+template <bool SECOND, bool WRITE, typename T, typename S>
+__device__ int hm_half_step(const Geo &g, const Fields<T, S> &f, const Box<T> &b, S *const Hin[3], S *const Hout[3],
                             int fprev, unsigned long long *res)
 {
     const int stride = gridDim.x * blockDim.x;
@@ -725,15 +743,15 @@ __device__ int hm_half_step(const Geo &g, const Fields<T> &f, const Box<T> &b, T
         for (int t = t0; t < b.nnon; t += stride) {
             const FaceOf fo = face_of(b.nonmag[t]);
             const T v = Hfin[fo.d][fo.l];
-            T *const Ho = fo.d == 0 ? Hout[0] : fo.d == 1 ? Hout[1] : Hout[2];
-            Ho[gidx32(g, fo.i, fo.j, fo.k)] = v;
+            S *const Ho = fo.d == 0 ? Hout[0] : fo.d == 1 ? Hout[1] : Hout[2];
+            st_s(Ho + gidx32(g, fo.i, fo.j, fo.k), v, f.isH);
             ok &= isfinite(v);
         }
         for (int t = t0; t < b.nmag; t += stride) {
             const FaceOf fo = face_of(b.mag[t]);
-            ok &= fo.d == 0   ? mag_store<0>(g, b, fo, t, Hfin, Hout, fr)
-                  : fo.d == 1 ? mag_store<1>(g, b, fo, t, Hfin, Hout, fr)
-                              : mag_store<2>(g, b, fo, t, Hfin, Hout, fr);
+            ok &= fo.d == 0   ? mag_store<0>(g, b, fo, t, Hfin, Hout, fr, f.isH)
+                  : fo.d == 1 ? mag_store<1>(g, b, fo, t, Hfin, Hout, fr, f.isH)
+                              : mag_store<2>(g, b, fo, t, Hfin, Hout, fr, f.isH);
         }
         if (!ok) atomicOr(b.err, kErrNonFinite);
     }
@@ -752,11 +770,11 @@ __device__ int hm_half_step(const Geo &g, const Fields<T> &f, const Box<T> &b, T
 // back to back (both use the same E^(n+1)), the second reading the first's
 // result.  Residual words: launch parity `slot` uses rows 2 slot and
 // 2 slot + 1 of res and clears the other parity's rows for the next launch.
-template <typename T>
+template <typename T, typename S = T>
 __global__ void __launch_bounds__(256) k_hm_box(const __grid_constant__ Geo g,
-                                                const __grid_constant__ Fields<T> f,
+                                                const __grid_constant__ Fields<T, S> f,
                                                 const __grid_constant__ Box<T> b,
-                                                const __grid_constant__ Ptr3<T> Hout, int nsub, int slot)
+                                                const __grid_constant__ Ptr3<S> Hout, int nsub, int slot)
 {
     const int W = kMaxIter + 1;
     if (blockIdx.x == 0) {

@@ -54,9 +54,9 @@ __device__ __forceinline__ bool unique_node(const Geo &g, int a, int idx)
     return !(g.per[a] && idx == g.n[a]);
 }
 
-template <typename T>
+template <typename T, typename S = T>
 __global__ void __launch_bounds__(kMonitorThreads)
-    k_energy(const Geo g, Fields<T> f, const double *__restrict__ eps_cell, const double *__restrict__ mu_cell,
+    k_energy(const Geo g, Fields<T, S> f, const double *__restrict__ eps_cell, const double *__restrict__ mu_cell,
              const double *__restrict__ ms_cell, double2 *partial)
 {
     const double eps0 = 1.0 / (kMu0 * kC0 * kC0);
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kMonitorThreads)
             for (int b = 0; b < 3; b++)
                 if (b != a) ok = ok && unique_node(g, b, ix[b]);
             if (ok) {
-                const double e = (double)f.E[a][q];
+                const double e = (double)ld_s(f.E[a] + q, f.sE);
                 const double eps = eps0 * (eps_cell ? edge_mean(g, eps_cell, a, i, j, k) : 1.0);
                 two_sum_acc(s, c, 0.5 * eps * e * e);
             }
@@ -83,13 +83,13 @@ __global__ void __launch_bounds__(kMonitorThreads)
             for (int b = 0; b < 3; b++)
                 if (b != a) ok = ok && ix[b] < g.n[b];
             if (ok) {
-                const double h = (double)f.H[a][q];
+                const double h = (double)ld_s(f.H[a] + q, f.sH);
                 const bool mag = ms_cell && face_mean(g, ms_cell, a, i, j, k) > 0.0;
                 const double mu = kMu0 * ((mu_cell && !mag) ? face_mean(g, mu_cell, a, i, j, k) : 1.0);
                 double cu = 0.0;
                 if (!wall_node(g, a, ix[a])) {
                     T rest, zp;
-                    curl_e(g, f.E, f.inv_d, a, i, j, k, rest, zp);
+                    curl_e(g, f.E, f.inv_d, a, i, j, k, rest, zp, f.sE);
                     cu = (double)rest + (double)zp;
                 }
                 const double r = g.dt / (2.0 * mu) * cu;
@@ -102,9 +102,9 @@ __global__ void __launch_bounds__(kMonitorThreads)
 
 // Poynting power through z node plane k, H at the time level of E taken as
 // the mean of Ha and Hb (equal arrays when H is already there).
-template <typename T>
+template <typename S, typename T>
 __global__ void __launch_bounds__(kMonitorThreads)
-    k_flux_partial(const Geo g, Ptr3<T> E, Ptr3<T> Ha, Ptr3<T> Hb, int k, double2 *partial)
+    k_flux_partial(const Geo g, Ptr3<S> E, Ptr3<S> Ha, Ptr3<S> Hb, T sE, T sH, int k, double2 *partial)
 {
     const int km = cell_nb(g, 2, k - 1), kp = cell_nb(g, 2, k);
     const long long XY = (long long)g.X * g.Y;
@@ -115,18 +115,19 @@ __global__ void __launch_bounds__(kMonitorThreads)
         const int i = p % g.X, j = p / g.X;
         if (i > g.n[0]) continue;
         const long long q = (long long)i + (long long)g.X * j;
-        auto hmean = [&](const Ptr3<T> &A, const Ptr3<T> &B, int comp) {
+        auto hv = [&](const Ptr3<S> &A, int comp, long long off) { return (double)ld_s(A.p[comp] + off, sH); };
+        auto hmean = [&](const Ptr3<S> &A, const Ptr3<S> &B, int comp) {
             double v = 0.0;
-            if (km >= 0) v += 0.5 * (0.5 * ((double)A.p[comp][q + km * XY] + (double)B.p[comp][q + km * XY]));
-            if (kp >= 0) v += 0.5 * (0.5 * ((double)A.p[comp][q + kp * XY] + (double)B.p[comp][q + kp * XY]));
+            if (km >= 0) v += 0.5 * (0.5 * (hv(A, comp, q + km * XY) + hv(B, comp, q + km * XY)));
+            if (kp >= 0) v += 0.5 * (0.5 * (hv(A, comp, q + kp * XY) + hv(B, comp, q + kp * XY)));
             return v;
         };
         // Ex (i+1/2, j, k) with Hy (i+1/2, j, k+-1/2)
         if (i < g.n[0] && j < g.n[1] + (g.per[1] ? 0 : 1))
-            two_sum_acc(s, c, area * (double)E.p[0][q + (long long)k * XY] * hmean(Ha, Hb, 1));
+            two_sum_acc(s, c, area * (double)ld_s(E.p[0] + q + (long long)k * XY, sE) * hmean(Ha, Hb, 1));
         // Ey (i, j+1/2, k) with Hx (i, j+1/2, k+-1/2)
         if (j < g.n[1] && i < g.n[0] + (g.per[0] ? 0 : 1))
-            two_sum_acc(s, c, -area * (double)E.p[1][q + (long long)k * XY] * hmean(Ha, Hb, 0));
+            two_sum_acc(s, c, -area * (double)ld_s(E.p[1] + q + (long long)k * XY, sE) * hmean(Ha, Hb, 0));
     }
     block_nsum(s, c, partial + blockIdx.x);
 }
