@@ -712,7 +712,8 @@ template <> struct VecStages<float, false> { static constexpr int value = MMX_VE
 
 template <typename T, typename S, bool GEN> constexpr size_t vec_smem_bytes()
 {
-    constexpr size_t b = VecLayout<T, S, VecRows<T>::value, GEN, VecStages<T, GEN>::value>::bytes;
+    constexpr int BY = VecRows<T>::value, ST = VecStages<T, GEN>::value;
+    constexpr size_t b = VecLayout<T, S, BY, GEN, ST>::bytes;
     static_assert(b <= 227 * 1024, "vectorised kernel shared memory above the per-CTA limit");
     return b;
 }
