@@ -262,6 +262,37 @@ MMX_API int mmx_get_flux(mmx_ctx *ctx, int index, double out[2], int reset);
 MMX_API int mmx_set_profiling(mmx_ctx *ctx, int enable);
 MMX_API int mmx_get_profile(mmx_ctx *ctx, mmx_kernel_profile *out, int cap, int reset);
 
+/* Batches: independent contexts (instances, e.g. the devices of a bias
+ * sweep) advanced together.  Per time step one fused E/H launch covers every
+ * instance's tiles and one cooperative H/M launch every instance's box
+ * faces; each instance keeps its own iteration residual and stops at its
+ * own first iterate below its tolerance (Sec. 3.2.2), and the launches of a
+ * whole mmx_batch_step call are captured as one CUDA graph (re-captured when
+ * the call length changes).
+ * mmx_batch_create gathers count contexts (owned by the caller, which must
+ * keep them alive and not step them through mmx_step while a batch call is
+ * in flight).  All instances must share the precision and the PML /
+ * conductive-or-permeable variant, have PEC x and y walls, no hard sources,
+ * probes or flux planes; otherwise MMX_ERR_INVALID (with *out holding a batch
+ * usable only with mmx_batch_last_error and mmx_batch_destroy).  Between
+ * batch calls every instance can be read, written and stepped on its own.
+ * cuda_stream is the batch's stream (NULL: the batch creates and owns a
+ * non-blocking stream, since graph capture needs one); every launch of a
+ * batch call, including each instance's per-call set-up, goes there, after
+ * the work queued on the instances' own streams.
+ * mmx_batch_set_planes sets the z planes each fused CTA marches (0: a whole
+ * grid; the tuning knob of the batch).  mmx_batch_step enqueues nsteps steps
+ * of every instance and returns; mmx_batch_sync waits, reports the first
+ * instance error (or a batch-level timeout / non-finite value) and clears
+ * the latched status words. */
+typedef struct mmx_batch mmx_batch;
+MMX_API int mmx_batch_create(mmx_ctx *const *ctxs, int count, void *cuda_stream, mmx_batch **out);
+MMX_API int mmx_batch_set_planes(mmx_batch *b, int planes);
+MMX_API int mmx_batch_step(mmx_batch *b, int nsteps);
+MMX_API int mmx_batch_sync(mmx_batch *b);
+MMX_API const char *mmx_batch_last_error(mmx_batch *b);
+MMX_API int mmx_batch_destroy(mmx_batch *b);
+
 /* Edge or face mean of a cell-centred array with no memory allocation, for
  * callers that cannot call cudaMalloc: code whose device memory is all owned
  * by its own arena or pool, or that runs where an allocation (which may

@@ -52,6 +52,8 @@ EXPORTS = ("mmx_create", "mmx_set_materials", "mmx_set_bias", "mmx_set_M_cells",
            "mmx_sync", "mmx_get_stats", "mmx_get_iter_log", "mmx_get_field_device",
            "mmx_set_storage_scale", "mmx_add_probe", "mmx_get_probes", "mmx_energy", "mmx_add_flux_plane", "mmx_get_flux",
            "mmx_set_profiling", "mmx_get_profile",
+           "mmx_batch_create", "mmx_batch_set_planes", "mmx_batch_step", "mmx_batch_sync",
+           "mmx_batch_last_error", "mmx_batch_destroy",
            "mmx_material_average_noalloc", "mmx_last_error", "mmx_destroy")
 
 _lib = None
@@ -109,6 +111,18 @@ def lib():
     L.mmx_add_flux_plane.argtypes = [P, I]
     L.mmx_get_flux.restype = I
     L.mmx_get_flux.argtypes = [P, I, dp, I]
+    L.mmx_batch_create.restype = I
+    L.mmx_batch_create.argtypes = [ctypes.POINTER(P), I, P, ctypes.POINTER(P)]
+    L.mmx_batch_set_planes.restype = I
+    L.mmx_batch_set_planes.argtypes = [P, I]
+    L.mmx_batch_step.restype = I
+    L.mmx_batch_step.argtypes = [P, I]
+    L.mmx_batch_sync.restype = I
+    L.mmx_batch_sync.argtypes = [P]
+    L.mmx_batch_last_error.restype = ctypes.c_char_p
+    L.mmx_batch_last_error.argtypes = [P]
+    L.mmx_batch_destroy.restype = I
+    L.mmx_batch_destroy.argtypes = [P]
     L.mmx_get_profile.restype = I
     L.mmx_get_profile.argtypes = [P, ctypes.POINTER(KernelProfile), I, I]
     L.mmx_material_average_noalloc.restype = I
@@ -330,6 +344,52 @@ def material_average_noalloc(n, bc, location, cell_ptr, out_ptr, count, stream=N
     return lib().mmx_material_average_noalloc(ctypes.byref(desc), int(location), ctypes.c_void_p(cell_ptr),
                                               ctypes.c_void_p(out_ptr), int(count),
                                               ctypes.c_void_p(stream or 0))
+
+
+class Batch:
+    """Independent solvers advanced together (one fused and one H/M launch per
+    step for all of them, each call one CUDA graph).  The solvers stay usable
+    on their own between batch calls; keep them alive as long as the batch."""
+
+    def __init__(self, solvers, stream=None):
+        self._L = lib()
+        self.solvers = list(solvers)
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s._h.value for s in self.solvers])
+        self._h = ctypes.c_void_p()
+        rc = self._L.mmx_batch_create(arr, len(self.solvers), stream, ctypes.byref(self._h))
+        if rc < 0:
+            msg = self._L.mmx_batch_last_error(self._h).decode() if self._h.value else ""
+            self.close()
+            raise MMXError(rc, "mmx_batch_create", msg)
+
+    def _check(self, rc, where):
+        if rc < 0:
+            raise MMXError(rc, where, self._L.mmx_batch_last_error(self._h).decode())
+        return rc
+
+    def set_planes(self, planes):
+        """z planes each fused CTA marches (0: a whole grid)."""
+        self._check(self._L.mmx_batch_set_planes(self._h, int(planes)), "mmx_batch_set_planes")
+
+    def step(self, nsteps):
+        self._check(self._L.mmx_batch_step(self._h, int(nsteps)), "mmx_batch_step")
+
+    def sync(self, check=True):
+        rc = self._L.mmx_batch_sync(self._h)
+        if check:
+            self._check(rc, "mmx_batch_sync")
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.mmx_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def from_workload(w, prec=FP64, stream=None, with_sources=True, path=PATH_FUSED) -> Solver:

@@ -17,6 +17,7 @@
 #include "mmx.h"
 #include "mmx_fused.cuh"
 #include "mmx_monitor.cuh"
+#include "mmx_batch.cuh"
 
 using namespace mmx;
 
@@ -1632,6 +1633,530 @@ int mmx_get_field_device(mmx_ctx *ctx, int id, void **ptr, long long *sx, long l
     return MMX_OK;
 }
 
+
+} // extern "C"
+
+// ============================================================ batches
+//
+// A batch advances independent contexts (instances) together: per time step
+// one fused launch over every instance's tiles and one cooperative H/M launch
+// over every instance's box faces, the whole mmx_batch_step call captured as
+// one CUDA graph.  Instances are ordinary contexts, set up and read back
+// through the per-context calls; the batch only gathers their device
+// pointers into tables (rebuilt at every call, since the E/H buffers of a
+// context alternate from step to step).
+
+struct mmx_batch {
+    std::vector<mmx_ctx *> ctx;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;               // created here (graph capture needs a non-default stream)
+    int prec = MMX_FP32;
+    bool pml = false, gen = false, magnetic = false;
+    int planes = 0;                        // z planes per fused CTA (0: whole grid)
+    std::vector<int> chunk, xstride;       // per instance, from the batch's plan
+    // fused launch
+    void *vinst[2] = {};                   // VecInst<T, S>[ninst] per parity
+    int4 *work = nullptr;
+    int nwork = 0;
+    // box launch
+    void *binst[2] = {};                   // BoxInst<T, S>[ninst] per parity
+    int4 *mag = nullptr, *non = nullptr;
+    int *mag_inst = nullptr, *non_inst = nullptr;
+    int nmag = 0, nnon = 0;
+    unsigned long long *res = nullptr, *bar = nullptr;
+    int *err = nullptr;
+    int coop_blocks = 0;
+    size_t box_smem = 0;
+    // source amplitudes of every instance for one call: [inst][step][source]
+    void *amp = nullptr;
+    long long amp_cap = 0;                 // elements allocated
+    // graph of the last call length
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = -1;
+    std::vector<void *> allocs;
+    std::string errmsg;
+};
+
+static int bfail(mmx_batch *b, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    b->errmsg = buf;
+    return code;
+}
+
+#define BCK(call)                                                                                    \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return bfail(b, MMX_ERR_CUDA, "CUDA %s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                         __LINE__);                                                                  \
+    } while (0)
+
+static int balloc(mmx_batch *b, void **p, size_t bytes)
+{
+    BCK(cudaMalloc(p, bytes > 0 ? bytes : 16));
+    BCK(cudaMemsetAsync(*p, 0, bytes > 0 ? bytes : 16, b->stream));
+    b->allocs.push_back(*p);
+    return MMX_OK;
+}
+
+// Work table of the fused launch: every (instance, strip, row tile, z chunk).
+template <typename T> static int batch_plan(mmx_batch *b)
+{
+    constexpr int BY = VecRows<T>::value;
+    constexpr int W = 32 * Lanes<T>::V;
+    std::vector<int4> work;
+    b->chunk.assign(b->ctx.size(), 0);
+    b->xstride.assign(b->ctx.size(), 0);
+    for (size_t q = 0; q < b->ctx.size(); q++) {
+        mmx_ctx *c = b->ctx[q];
+        const int *n = c->desc.n;
+        const int xs = W - Lanes<T>::V;
+        const int ntx = n[0] <= W ? 1 : 1 + (n[0] - W + xs - 1) / xs;
+        const int nty = (n[1] + BY - 1) / BY;
+        const int chunk = b->planes > 0 ? std::min(b->planes, n[2]) : n[2];
+        const int nch = (n[2] + chunk - 1) / chunk;
+        b->chunk[q] = chunk;
+        b->xstride[q] = xs;
+        for (int z = 0; z < nch; z++)
+            for (int y = 0; y < nty; y++)
+                for (int x = 0; x < ntx; x++) work.push_back(make_int4((int)q, x, y, z));
+    }
+    if (b->work) {
+        cudaFree(b->work);
+        b->allocs.erase(std::find(b->allocs.begin(), b->allocs.end(), (void *)b->work));
+        b->work = nullptr;
+    }
+    int rc = balloc(b, (void **)&b->work, work.size() * sizeof(int4));
+    if (rc) return rc;
+    BCK(cudaMemcpyAsync(b->work, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    b->nwork = (int)work.size();
+    return MMX_OK;
+}
+
+// Concatenated face lists with their instance tags, per-instance residual
+// rows, the barrier word and the cooperative grid size.
+template <typename T, typename S> static int batch_box_setup(mmx_batch *b)
+{
+    const int ninst = (int)b->ctx.size();
+    std::vector<int> mi, ni;
+    long long nm = 0, nn = 0;
+    for (mmx_ctx *c : b->ctx) {
+        nm += c->magnetic ? c->nmag : 0;
+        nn += c->magnetic ? c->nnon : 0;
+    }
+    if (nm >= (1LL << 31) || nn >= (1LL << 31)) return bfail(b, MMX_ERR_INVALID, "batch has too many box faces");
+    b->nmag = (int)nm;
+    b->nnon = (int)nn;
+    int rc = balloc(b, (void **)&b->mag, (size_t)std::max(1LL, nm) * sizeof(int4));
+    if (!rc) rc = balloc(b, (void **)&b->non, (size_t)std::max(1LL, nn) * sizeof(int4));
+    if (!rc) rc = balloc(b, (void **)&b->mag_inst, (size_t)std::max(1LL, nm) * sizeof(int));
+    if (!rc) rc = balloc(b, (void **)&b->non_inst, (size_t)std::max(1LL, nn) * sizeof(int));
+    if (!rc) rc = balloc(b, (void **)&b->res, 4 * (size_t)ninst * (kMaxIter + 1) * sizeof(unsigned long long));
+    if (!rc) rc = balloc(b, (void **)&b->bar, sizeof(unsigned long long));
+    if (!rc) rc = balloc(b, (void **)&b->err, sizeof(int));
+    if (rc) return rc;
+    long long om = 0, on = 0;
+    mi.reserve(nm);
+    ni.reserve(nn);
+    for (int q = 0; q < ninst; q++) {
+        mmx_ctx *c = b->ctx[q];
+        if (!c->magnetic) continue;
+        if (c->nmag)
+            BCK(cudaMemcpyAsync(b->mag + om, c->dmag, (size_t)c->nmag * sizeof(int4), cudaMemcpyDeviceToDevice,
+                                b->stream));
+        if (c->nnon)
+            BCK(cudaMemcpyAsync(b->non + on, c->dnon, (size_t)c->nnon * sizeof(int4), cudaMemcpyDeviceToDevice,
+                                b->stream));
+        mi.insert(mi.end(), c->nmag, q);
+        ni.insert(ni.end(), c->nnon, q);
+        om += c->nmag;
+        on += c->nnon;
+    }
+    if (nm) BCK(cudaMemcpyAsync(b->mag_inst, mi.data(), mi.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    if (nn) BCK(cudaMemcpyAsync(b->non_inst, ni.data(), ni.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    b->box_smem = (size_t)ninst * (sizeof(unsigned long long) + 2 * sizeof(int));
+    if (b->box_smem > 48 * 1024)
+        BCK(cudaFuncSetAttribute(k_hm_box_batch<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)b->box_smem));
+    int dev = 0, nsm = 0, per = 0;
+    BCK(cudaGetDevice(&dev));
+    BCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hm_box_batch<T, S>, 256, b->box_smem));
+    if (per < 1) return bfail(b, MMX_ERR_CUDA, "batched H/M kernel cannot be resident");
+    const long long need = (std::max(nm, nn) + 255) / 256;
+    b->coop_blocks = (int)std::max(1LL, std::min(need, (long long)per * nsm));
+    return MMX_OK;
+}
+
+// Instance tables for parity p: p = 0 reads the contexts' current E/H and
+// writes their second set; p = 1 the other way round.
+template <typename T, typename S> static int batch_tables(mmx_batch *b, long long steps)
+{
+    const int ninst = (int)b->ctx.size();
+    std::vector<VecInst<T, S>> vi[2];
+    std::vector<BoxInst<T, S>> bi[2];
+    long long base = 0;
+    for (int p = 0; p < 2; p++) {
+        vi[p].resize(ninst);
+        bi[p].resize(ninst);
+    }
+    long long ampoff = 0;
+    for (int q = 0; q < ninst; q++) {
+        mmx_ctx *c = b->ctx[q];
+        for (int p = 0; p < 2; p++) {
+            void *const *Ea = p == 0 ? c->E : c->Ealt, *const *Eb = p == 0 ? c->Ealt : c->E;
+            void *const *Ha = p == 0 ? c->H : c->Halt, *const *Hb = p == 0 ? c->Halt : c->H;
+            void *const *Za = p == 0 ? c->Ezp : c->Ezpalt, *const *Zb = p == 0 ? c->Ezpalt : c->Ezp;
+            VecInst<T, S> &v = vi[p][q];
+            v.g = c->g;
+            v.f = make_fields<T, S>(c);
+            for (int a = 0; a < 3; a++) {
+                v.io.Eo[a] = (const S *)Ea[a];
+                v.io.Ho[a] = (const S *)Ha[a];
+                v.io.En[a] = (S *)Eb[a];
+                v.io.Hn[a] = (S *)Hb[a];
+            }
+            for (int a = 0; a < 2; a++) {
+                v.io.Zo[a] = (const S *)Za[a];
+                v.io.Zn[a] = (S *)Zb[a];
+            }
+            v.src = (const Src<T> *)c->dsrc;
+            v.nsrc = (int)c->src.size();
+            v.amp = (const T *)b->amp + ampoff;
+            v.chunk = b->chunk[q];
+            v.xstride = b->xstride[q];
+            BoxInst<T, S> &x = bi[p][q];
+            x.g = c->g;
+            x.f = make_fields<T, S>(c);
+            for (int a = 0; a < 3; a++) {
+                x.f.E[a] = (S *)Eb[a];   // E^(n+1)
+                x.f.H[a] = (S *)Ha[a];   // H^(n+1/2)
+                x.Hout.p[a] = (S *)Hb[a];
+            }
+            x.b = make_box<T>(c);
+            x.base_mag = (int)base;
+        }
+        ampoff += (long long)c->src.size() * steps;
+        base += c->magnetic ? c->nmag : 0;
+    }
+    for (int p = 0; p < 2; p++) {
+        BCK(cudaMemcpyAsync(b->vinst[p], vi[p].data(), ninst * sizeof(VecInst<T, S>), cudaMemcpyHostToDevice,
+                            b->stream));
+        BCK(cudaMemcpyAsync(b->binst[p], bi[p].data(), ninst * sizeof(BoxInst<T, S>), cudaMemcpyHostToDevice,
+                            b->stream));
+    }
+    BCK(cudaStreamSynchronize(b->stream));
+    return MMX_OK;
+}
+
+// Source amplitudes of every instance for steps [n0, n0 + steps) of its clock.
+template <typename T> static int batch_amplitudes(mmx_batch *b, long long steps)
+{
+    long long total = 0;
+    for (mmx_ctx *c : b->ctx) total += (long long)c->src.size() * steps;
+    if (total > b->amp_cap) {
+        if (b->amp) {
+            cudaFree(b->amp);
+            b->allocs.erase(std::find(b->allocs.begin(), b->allocs.end(), b->amp));
+            b->amp = nullptr;
+        }
+        int rc = balloc(b, &b->amp, (size_t)std::max(1LL, total) * sizeof(T));
+        if (rc) return rc;
+        b->amp_cap = total;
+        if (b->graph) {
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+            b->graph_steps = -1;
+        }
+    }
+    std::vector<T> v((size_t)total);
+    long long off = 0;
+    for (mmx_ctx *c : b->ctx) {
+        const size_t ns = c->src.size();
+        for (long long s = 0; s < steps; s++)
+            for (size_t q = 0; q < ns; q++) {
+                const mmx_source_desc &d = c->src[q];
+                const double t = ((double)(c->steps + s) + 0.5) * c->desc.dt;
+                v[off + s * ns + q] = (T)((d.kind == 0 || d.kind == 1) ? host_waveform(d, t) : 0.0);
+            }
+        off += (long long)ns * steps;
+    }
+    if (total) BCK(cudaMemcpyAsync(b->amp, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    return MMX_OK;
+}
+
+template <typename T, typename S, int NH, bool PMLK, bool GEN>
+static void batch_fused_v(mmx_batch *b, int parity, int step)
+{
+    constexpr int BY = VecRows<T>::value, ST = VecStages<T, GEN>::value;
+    k_fused_vec_batch<T, S, BY, ST, NH, PMLK, GEN><<<b->nwork, dim3(32, BY + 1), vec_smem_bytes<T, S, GEN>(),
+                                                     b->stream>>>((const VecInst<T, S> *)b->vinst[parity],
+                                                                  b->work, step);
+}
+
+template <typename T, typename S> static void batch_fused(mmx_batch *b, int parity, int step, int nhalf)
+{
+#define MMX_BATCH_CASE(NHV, PV, GV)                                                                  \
+    if (nhalf == NHV && b->pml == PV && b->gen == GV) {                                              \
+        batch_fused_v<T, S, NHV, PV, GV>(b, parity, step);                                           \
+        return;                                                                                      \
+    }
+    MMX_BATCH_CASE(2, true, false) MMX_BATCH_CASE(2, false, false) MMX_BATCH_CASE(2, true, true)
+    MMX_BATCH_CASE(2, false, true) MMX_BATCH_CASE(1, true, false) MMX_BATCH_CASE(1, false, false)
+    MMX_BATCH_CASE(1, true, true) MMX_BATCH_CASE(1, false, true)
+#undef MMX_BATCH_CASE
+}
+
+template <typename T, typename S, int NH, bool PMLK, bool GEN> static cudaError_t batch_smem_v()
+{
+    constexpr int BY = VecRows<T>::value, ST = VecStages<T, GEN>::value;
+    return cudaFuncSetAttribute(k_fused_vec_batch<T, S, BY, ST, NH, PMLK, GEN>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec_smem_bytes<T, S, GEN>());
+}
+
+template <typename T, typename S> static cudaError_t batch_smem()
+{
+    cudaError_t r[8] = {batch_smem_v<T, S, 1, false, false>(), batch_smem_v<T, S, 1, false, true>(),
+                        batch_smem_v<T, S, 1, true, false>(),  batch_smem_v<T, S, 1, true, true>(),
+                        batch_smem_v<T, S, 2, false, false>(), batch_smem_v<T, S, 2, false, true>(),
+                        batch_smem_v<T, S, 2, true, false>(),  batch_smem_v<T, S, 2, true, true>()};
+    for (cudaError_t x : r)
+        if (x != cudaSuccess) return x;
+    return cudaSuccess;
+}
+
+// The launches of steps [0, nsteps) on the batch stream (captured into the
+// call's graph).
+template <typename T, typename S> static int batch_enqueue(mmx_batch *b, int nsteps)
+{
+    const int ninst = (int)b->ctx.size();
+    for (int s = 0; s < nsteps; s++) {
+        const int p = s & 1, nhalf = s == nsteps - 1 ? 1 : 2;
+        batch_fused<T, S>(b, p, s, nhalf);
+        BCK(cudaGetLastError());
+        if (b->magnetic) {
+            const BoxInst<T, S> *inst = (const BoxInst<T, S> *)b->binst[p];
+            int nsub = nhalf, slot = s & 1;
+            void *args[] = {(void *)&inst,       (void *)&ninst,       (void *)&b->mag, (void *)&b->mag_inst,
+                            (void *)&b->nmag,    (void *)&b->non,      (void *)&b->non_inst, (void *)&b->nnon,
+                            (void *)&b->res,     (void *)&b->bar,      (void *)&b->err, (void *)&nsub,
+                            (void *)&slot};
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.gridDim = dim3(b->coop_blocks);
+            cfg.blockDim = dim3(256);
+            cfg.dynamicSmemBytes = b->box_smem;
+            cfg.stream = b->stream;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            BCK(cudaLaunchKernelExC(&cfg, (const void *)k_hm_box_batch<T, S>, args));
+        }
+    }
+    return MMX_OK;
+}
+
+template <typename T, typename S> static int batch_step_t(mmx_batch *b, int nsteps)
+{
+    // per-instance start of the call: M into the records, the first H half
+    // step, wall clean-up (all on the batch stream)
+    std::vector<cudaStream_t> saved;
+    for (mmx_ctx *c : b->ctx) {
+        // work already queued on the instance's own stream comes first
+        BCK(cudaStreamSynchronize(c->stream));
+        saved.push_back(c->stream);
+        c->stream = b->stream;
+    }
+    auto restore = [&]() {
+        for (size_t q = 0; q < b->ctx.size(); q++) b->ctx[q]->stream = saved[q];
+    };
+    int rc = MMX_OK;
+    for (mmx_ctx *c : b->ctx) {
+        rc = box_m_sync<T>(c, 1);
+        if (!rc) {
+            Fields<T, S> f = make_fields<T, S>(c);
+            rc = half_step<T, S>(c, f, make_box<T>(c), (c->steps + 0.5) * c->desc.dt);
+        }
+        if (!rc && c->walls_dirty) {
+            rc = zero_walls<S>(c);
+            c->walls_dirty = false;
+        }
+        if (rc) {
+            restore();
+            return bfail(b, rc, "instance setup: %s", c->err.c_str());
+        }
+    }
+    rc = batch_amplitudes<T>(b, nsteps);
+    if (!rc) rc = batch_tables<T, S>(b, nsteps);
+    if (rc) {
+        restore();
+        return rc;
+    }
+    BCK(cudaMemsetAsync(b->res, 0, 4 * b->ctx.size() * (kMaxIter + 1) * sizeof(unsigned long long), b->stream));
+    if (!b->graph || b->graph_steps != nsteps) {
+        if (b->graph) {
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        rc = batch_enqueue<T, S>(b, nsteps);
+        cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            restore();
+            return rc;
+        }
+        BCK(ec);
+        cudaError_t ei = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        BCK(ei);
+        b->graph_steps = nsteps;
+    }
+    BCK(cudaGraphLaunch(b->graph, b->stream));
+    for (mmx_ctx *c : b->ctx) {
+        if (nsteps & 1) swap_buffers<T>(c);
+        c->steps += nsteps;
+        rc = box_m_sync<T>(c, 0);
+        if (rc) break;
+    }
+    restore();
+    return rc;
+}
+
+template <typename T, typename S> static int batch_init(mmx_batch *b)
+{
+    const int ninst = (int)b->ctx.size();
+    for (int p = 0; p < 2; p++) {
+        int rc = balloc(b, &b->vinst[p], ninst * sizeof(VecInst<T, S>));
+        if (!rc) rc = balloc(b, &b->binst[p], ninst * sizeof(BoxInst<T, S>));
+        if (rc) return rc;
+    }
+    {
+        cudaError_t e = batch_smem<T, S>();
+        BCK(e);
+    }
+    int rc = batch_plan<T>(b);
+    if (!rc && b->magnetic) rc = batch_box_setup<T, S>(b);
+    return rc;
+}
+
+extern "C" {
+
+int mmx_batch_create(mmx_ctx *const *ctxs, int count, void *cuda_stream, mmx_batch **out)
+{
+    if (!out) return MMX_ERR_INVALID;
+    *out = nullptr;
+    if (!ctxs || count < 1) return MMX_ERR_INVALID;
+    mmx_batch *b = new (std::nothrow) mmx_batch;
+    if (!b) return MMX_ERR_OOM;
+    *out = b;
+    b->stream = (cudaStream_t)cuda_stream;
+    if (!b->stream) {
+        BCK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        b->own_stream = true;
+    }
+    for (int q = 0; q < count; q++) {
+        mmx_ctx *c = ctxs[q];
+        if (!c || !c->E[0]) return bfail(b, MMX_ERR_INVALID, "instance %d is not a context", q);
+        for (int r = 0; r < q; r++)
+            if (ctxs[r] == c) return bfail(b, MMX_ERR_INVALID, "instance %d appears twice", q);
+        if (q == 0) {
+            b->prec = c->desc.prec;
+            b->pml = c->g.npml > 0;
+            b->gen = c->any_sigma || c->any_mu;
+        }
+        if (c->desc.prec != b->prec) return bfail(b, MMX_ERR_INVALID, "instances mix precisions");
+        if ((c->g.npml > 0) != b->pml || (c->any_sigma || c->any_mu) != b->gen)
+            return bfail(b, MMX_ERR_INVALID, "instances mix PML or conductive/permeable material variants");
+        if (!vec_usable(c)) return bfail(b, MMX_ERR_INVALID, "instance %d needs PEC x and y walls", q);
+        for (auto &s : c->src)
+            if (s.kind >= 2) return bfail(b, MMX_ERR_INVALID, "instance %d has a hard source", q);
+        if (!c->probes.empty() || !c->flux_k.empty())
+            return bfail(b, MMX_ERR_INVALID, "instance %d has probes or flux planes (not recorded in batches)", q);
+        b->magnetic |= c->magnetic;
+        b->ctx.push_back(c);
+    }
+    return b->prec == MMX_FP64 ? batch_init<double, double>(b)
+           : b->prec == MMX_FP16 ? batch_init<float, __half>(b) : batch_init<float, float>(b);
+}
+
+int mmx_batch_set_planes(mmx_batch *b, int planes)
+{
+    if (!b || b->ctx.empty() || planes < 0) return MMX_ERR_INVALID;
+    b->planes = planes;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        b->graph_steps = -1;
+    }
+    return b->prec == MMX_FP64 ? batch_plan<double>(b) : batch_plan<float>(b);
+}
+
+int mmx_batch_step(mmx_batch *b, int nsteps)
+{
+    if (!b || b->ctx.empty() || nsteps < 0) return MMX_ERR_INVALID;
+    if (nsteps == 0) return MMX_OK;
+    for (mmx_ctx *c : b->ctx) {
+        if (!vec_usable(c) || !c->probes.empty() || !c->flux_k.empty() || (c->g.npml > 0) != b->pml ||
+            (c->any_sigma || c->any_mu) != b->gen)
+            return bfail(b, MMX_ERR_INVALID, "an instance changed since the batch was made");
+        for (auto &s : c->src)
+            if (s.kind >= 2) return bfail(b, MMX_ERR_INVALID, "an instance has a hard source");
+    }
+    BCK(cudaMemsetAsync(b->bar, 0, sizeof(unsigned long long), b->stream));
+    return b->prec == MMX_FP64 ? batch_step_t<double, double>(b, nsteps)
+           : b->prec == MMX_FP16 ? batch_step_t<float, __half>(b, nsteps) : batch_step_t<float, float>(b, nsteps);
+}
+
+int mmx_batch_sync(mmx_batch *b)
+{
+    if (!b || b->ctx.empty()) return MMX_ERR_INVALID;
+    BCK(cudaStreamSynchronize(b->stream));
+    int w = 0;
+    BCK(cudaMemcpy(&w, b->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (w) {
+        int z = 0;
+        BCK(cudaMemcpy(b->err, &z, sizeof(int), cudaMemcpyHostToDevice));
+        BCK(cudaMemset(b->bar, 0, sizeof(unsigned long long)));
+        if (w & kErrTimeout) return bfail(b, MMX_ERR_TIMEOUT, "a device-side wait gave up");
+        if (w & kErrNonFinite) return bfail(b, MMX_ERR_NONFINITE, "a field became non-finite");
+    }
+    int first = MMX_OK;
+    for (size_t q = 0; q < b->ctx.size(); q++) {
+        int rc = read_status(b->ctx[q]);
+        if (rc && first == MMX_OK) {
+            first = rc;
+            bfail(b, rc, "instance %d: %s", (int)q, b->ctx[q]->err.c_str());
+        }
+    }
+    return first;
+}
+
+const char *mmx_batch_last_error(mmx_batch *b)
+{
+    return b ? b->errmsg.c_str() : "null batch";
+}
+
+int mmx_batch_destroy(mmx_batch *b)
+{
+    if (!b) return MMX_ERR_INVALID;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (void *p : b->allocs) cudaFree(p);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return MMX_OK;
+}
 
 } // extern "C"
 

@@ -231,8 +231,20 @@ __device__ __forceinline__ double waveform(double amp, double f0, double tp, dou
 // periodic axes are compared modulo n so that a duplicate node receives the
 // same current.
 template <typename T, typename S>
+__device__ __forceinline__ T j_source_a(const Geo &g, const Fields<T, S> &f, const T *amp, const Src<T> *src,
+                                        int nsrc, int c, int i, int j, int k);
+
+template <typename T, typename S>
 __device__ __forceinline__ T j_source(const Geo &g, const Fields<T, S> &f, const Src<T> *src, int nsrc, int c,
                                       int i, int j, int k)
+{
+    return j_source_a(g, f, f.src_amp, src, nsrc, c, i, j, k);
+}
+
+// The same with this step's source amplitudes amp[s] given explicitly.
+template <typename T, typename S>
+__device__ __forceinline__ T j_source_a(const Geo &g, const Fields<T, S> &f, const T *amp, const Src<T> *src,
+                                        int nsrc, int c, int i, int j, int k)
 {
     T J = T(0);
     int ci = (g.per[0] && c != 0 && i == g.n[0]) ? 0 : i;
@@ -242,9 +254,9 @@ __device__ __forceinline__ T j_source(const Geo &g, const Fields<T, S> &f, const
         const Src<T> &q = src[s];
         if (q.comp != c) continue;
         if (q.kind == 0) {
-            if (q.i == ci && q.j == cj && q.k == ck) J += f.src_amp[s];
+            if (q.i == ci && q.j == cj && q.k == ck) J += amp[s];
         } else if (q.kind == 1) {
-            if (q.k == ck) J += f.src_amp[s] * f.prof[c == 0 ? 1 : 0][ci];
+            if (q.k == ck) J += amp[s] * f.prof[c == 0 ? 1 : 0][ci];
         }
     }
     return J;

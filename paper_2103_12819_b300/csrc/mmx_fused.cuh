@@ -202,11 +202,13 @@ template <typename T, typename S, int BY, bool GEN, int ST> struct VecLayout {
     static constexpr size_t bytes = ez + al((size_t)2 * R * W * sizeof(T));
 };
 
+// The kernel body for the CTA at tile (bx, by, bz) of one grid: the single
+// grid launch passes its block index, the batched launch the entry of its
+// work table; amp holds this step's source amplitudes.
 template <typename T, typename S, int BY, int ST, int NH, bool PMLK, bool GEN>
-__global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
-    k_fused_vec(const __grid_constant__ Geo g, const __grid_constant__ Fields<T, S> f,
-                const __grid_constant__ FusedIO<S> io, const Src<T> *__restrict__ src, int nsrc, int chunk,
-                int xstride)
+__device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> &f, const FusedIO<S> &io,
+                                               const Src<T> *__restrict__ src, int nsrc, const T *amp,
+                                               int chunk, int xstride, int bx, int by, int bz)
 {
     using L = VecLayout<T, S, BY, GEN, ST>;
     using P = SV<S>;
@@ -230,11 +232,11 @@ __global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
 
     const int lane = threadIdx.x, w = threadIdx.y;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const int x0 = blockIdx.x * xstride;
+    const int x0 = bx * xstride;
     const int i0 = x0 + V * lane;
     const int col = V * lane;
-    const int j = blockIdx.y * BY + w;
-    const int k0 = blockIdx.z * chunk;
+    const int j = by * BY + w;
+    const int k0 = bz * chunk;
     const int k1 = min(k0 + chunk, nz);
     const bool last_chunk = k1 == nz;
     const bool lane_on = j < ny && i0 < nx;
@@ -382,9 +384,9 @@ __global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
             for (int e = 0; e < V; e++) {
                 T J0 = T(0), J1 = T(0), J2 = T(0);
                 if (src_here && cin[e]) {
-                    J0 = j_source(g, f, src, nsrc, 0, i0 + e, j, k);
-                    J1 = j_source(g, f, src, nsrc, 1, i0 + e, j, k);
-                    J2 = j_source(g, f, src, nsrc, 2, i0 + e, j, k);
+                    J0 = j_source_a(g, f, amp, src, nsrc, 0, i0 + e, j, k);
+                    J1 = j_source_a(g, f, amp, src, nsrc, 1, i0 + e, j, k);
+                    J2 = j_source_a(g, f, amp, src, nsrc, 2, i0 + e, j, k);
                 }
                 const T hzm = e > 0 ? hz[e > 0 ? e - 1 : 0] : hzl;
                 const T hym = e > 0 ? hy[e > 0 ? e - 1 : 0] : hyl;
@@ -558,6 +560,39 @@ __global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
         vcopy<T, V>(ezq, ez);
     }
     if (!isfinite(acc)) atomicOr(f.err, kErrNonFinite);
+}
+
+template <typename T, typename S, int BY, int ST, int NH, bool PMLK, bool GEN>
+__global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
+    k_fused_vec(const __grid_constant__ Geo g, const __grid_constant__ Fields<T, S> f,
+                const __grid_constant__ FusedIO<S> io, const Src<T> *__restrict__ src, int nsrc, int chunk,
+                int xstride)
+{
+    fused_vec_body<T, S, BY, ST, NH, PMLK, GEN>(g, f, io, src, nsrc, f.src_amp, chunk, xstride, blockIdx.x,
+                                                blockIdx.y, blockIdx.z);
+}
+
+// One grid of a batch: what the batched fused launch needs per instance, for
+// one parity of the E/H ping-pong.
+template <typename T, typename S> struct VecInst {
+    Geo g;
+    Fields<T, S> f;
+    FusedIO<S> io;
+    const Src<T> *src;
+    const T *amp;        // source amplitudes, [step][source]
+    int nsrc;
+    int chunk, xstride;
+};
+
+// Batched fused step: CTA b takes work[b] = {instance, bx, by, bz}.
+template <typename T, typename S, int BY, int ST, int NH, bool PMLK, bool GEN>
+__global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
+    k_fused_vec_batch(const VecInst<T, S> *__restrict__ inst, const int4 *__restrict__ work, int step)
+{
+    const int4 wk = work[blockIdx.x];
+    const VecInst<T, S> &I = inst[wk.x];
+    fused_vec_body<T, S, BY, ST, NH, PMLK, GEN>(I.g, I.f, I.io, I.src, I.nsrc, I.amp + (size_t)step * I.nsrc,
+                                                I.chunk, I.xstride, wk.y, wk.z, wk.w);
 }
 
 // Zero the wall column x = nx and the wall row y = ny (all planes) of up to

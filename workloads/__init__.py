@@ -208,6 +208,41 @@ def air_guide(steps: int = 8000, nz: int = 600, f0: float = 10.5e9, tp: Optional
         m_cells=None, sources=[src], steps=steps)
 
 
+def tunable_filter(n: int, h0: float, steps: int = 2000, seed: int = 0, tol: float = 1e-6) -> Workload:
+    """One instance of the bias sweep: an n^3 PEC box of 1 um cells with a
+    centred YIG-like slab (Ms 1.4e5 A/m, alpha 0.005, |gamma| 1.76e11,
+    eps_r 15) over the middle quarter of z, bias h0 along z, M = z + 1% seeded
+    tilt, and a 5 GHz Gaussian Jx point source near one corner of the box."""
+    nn = (n, n, n)
+    dx = 1e-6
+    dt = cfl_dt((dx, dx, dx), 0.9)
+    shp = _cell_shape(nn)
+    rng = np.random.default_rng(seed)
+    slab = np.zeros(shp, dtype=bool)
+    slab[(3 * n) // 8:(5 * n) // 8, :, :] = True
+    Ms = np.where(slab, YIG_MS, 0.0)
+    tx, ty, tz = _tilted_z(rng, shp)
+    mx, my, mz = (np.where(slab, Ms * c, 0.0) for c in (tx, ty, tz))
+    f0 = 5e9
+    tp = 200 * dt
+    src = Source(SRC_POINT_J, 0, n // 4, n // 2, n // 2, amp=1e9, f0=f0, tp=tp, t0=3 * tp)
+    return Workload(
+        name=f"filter_{n}_h{h0:.0f}", n=nn, d=(dx, dx, dx), dt=dt, bc=(PEC, PEC, PEC), tol=tol, max_iter=64,
+        h0=(0.0, 0.0, float(h0)), eps_r=np.where(slab, YIG_EPS, 1.0), sigma=np.zeros(shp), mu_r=np.ones(shp),
+        Ms=Ms, alpha=np.where(slab, YIG_ALPHA, 0.0), gamma=np.where(slab, YIG_GAMMA, 0.0),
+        m_cells=(mx, my, mz), sources=[src], steps=steps)
+
+
+def bias_sweep(count: int = 256, seed: int = 3, sizes=(32, 48, 64, 96)) -> List[Tuple[int, float, int]]:
+    """The batched bias sweep as (n, h0, seed) per instance (build each with
+    tunable_filter, one at a time): sizes drawn from `sizes`, bias uniform in
+    [5e4, 2e5] A/m along z, each instance with its own seed."""
+    rng = np.random.default_rng(seed)
+    n = rng.choice(np.asarray(sizes), size=count)
+    h0 = rng.uniform(5e4, 2e5, size=count)
+    return [(int(n[q]), float(h0[q]), seed * 1000 + q) for q in range(count)]
+
+
 def stress(seed: int = 2, steps: int = 1000, n: int = 512, tol: float = 1e-6) -> Workload:
     """n^3 PEC box, dx = 1e-6 m; centred (n/2)^3 magnetic block with seeded
     uniformly random unit M directions times Ms = 1.4e5 A/m, alpha = 0.01;
