@@ -210,6 +210,24 @@ typedef struct {
     double total_ms;
 } mmx_kernel_profile;
 
+/* Discrete adjoint of the electromagnetic update (Sec. 3.2 H half step,
+ * E update with the time-centred split-field z-PML, H half step), for grids
+ * without magnetic material and without periodic axes, FP32 or FP64, soft
+ * sources only, no probes or flux planes registered.  From the current
+ * state the context runs nsteps steps (the per-update path), accumulating
+ *   loss = sum_(n=1..nsteps) dt P(E^n, H^n)
+ * with P the Poynting power through z node plane kp as in mmx_add_flux_plane,
+ * then sweeps back through the steps, recomputing each checkpoint_every-step
+ * segment from its checkpoint, and writes d loss / d eps_r of every cell
+ * (host array of nx*ny*nz doubles, x fastest) to grad_eps and the loss to
+ * *loss.  The context ends advanced by nsteps, as after mmx_step.  Device
+ * memory: about (nsteps/checkpoint_every + checkpoint_every + 1) copies of
+ * the E/H state plus 22 grid arrays.  Synchronises the context stream.
+ * MMX_ERR_INVALID for a context it does not cover, MMX_ERR_OOM when the
+ * checkpoints do not fit. */
+MMX_API int mmx_flux_gradient(mmx_ctx *ctx, int kp, int nsteps, int checkpoint_every, double *loss,
+                              double *grad_eps);
+
 /* FP16 storage scales: E is stored as E / sE and H (with its PML split part)
  * as H / sH, so that the fields of a problem sit inside FP16's range
  * (|value / scale| < 65504, full precision above 6.1e-5).  Defaults:

@@ -50,7 +50,7 @@ class KernelProfile(ctypes.Structure):
 EXPORTS = ("mmx_create", "mmx_set_materials", "mmx_set_bias", "mmx_set_M_cells", "mmx_set_field",
            "mmx_get_field", "mmx_get_material", "mmx_add_source", "mmx_set_path", "mmx_step",
            "mmx_sync", "mmx_get_stats", "mmx_get_iter_log", "mmx_get_field_device",
-           "mmx_set_storage_scale", "mmx_add_probe", "mmx_get_probes", "mmx_energy", "mmx_add_flux_plane", "mmx_get_flux",
+           "mmx_flux_gradient", "mmx_set_storage_scale", "mmx_add_probe", "mmx_get_probes", "mmx_energy", "mmx_add_flux_plane", "mmx_get_flux",
            "mmx_set_profiling", "mmx_get_profile",
            "mmx_batch_create", "mmx_batch_set_planes", "mmx_batch_step", "mmx_batch_sync",
            "mmx_batch_last_error", "mmx_batch_destroy",
@@ -99,6 +99,8 @@ def lib():
     L.mmx_get_field_device.argtypes = [P, I, ctypes.POINTER(P), ctypes.POINTER(LL), ctypes.POINTER(LL)]
     L.mmx_set_profiling.restype = I
     L.mmx_set_profiling.argtypes = [P, I]
+    L.mmx_flux_gradient.restype = I
+    L.mmx_flux_gradient.argtypes = [P, I, I, I, dp, dp]
     L.mmx_set_storage_scale.restype = I
     L.mmx_set_storage_scale.argtypes = [P, D, D]
     L.mmx_add_probe.restype = I
@@ -285,6 +287,17 @@ class Solver:
         self._check(self._L.mmx_get_field_device(self._h, int(fid), ctypes.byref(p), ctypes.byref(sx),
                                                  ctypes.byref(sy)), "mmx_get_field_device")
         return p.value, sx.value, sy.value
+
+    def flux_gradient(self, kp, nsteps, checkpoint_every=None):
+        """Run nsteps steps and return (loss, d loss / d eps_r per cell) for the
+        time-integrated Poynting flux through z node plane kp (discrete
+        adjoint, checkpointing every ~sqrt(nsteps) steps by default)."""
+        every = int(checkpoint_every or max(1, round(nsteps ** 0.5)))
+        loss = ctypes.c_double()
+        grad = np.zeros(self.n[0] * self.n[1] * self.n[2], dtype=np.float64)
+        self._check(self._L.mmx_flux_gradient(self._h, int(kp), int(nsteps), every, ctypes.byref(loss), _dp(grad)),
+                    "mmx_flux_gradient")
+        return loss.value, grad.reshape(self.n[2], self.n[1], self.n[0])
 
     def set_storage_scale(self, sE, sH):
         """FP16 contexts: store E as E/sE and H as H/sH (before any field or step)."""

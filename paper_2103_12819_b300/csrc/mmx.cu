@@ -18,6 +18,7 @@
 #include "mmx_fused.cuh"
 #include "mmx_monitor.cuh"
 #include "mmx_batch.cuh"
+#include "mmx_adjoint.cuh"
 
 using namespace mmx;
 
@@ -693,24 +694,6 @@ static void launch_fused(mmx_ctx *ctx, dim3 G, dim3 B, const Fields<T> &f, Ptr3<
 
 // ------------------------------------------- vectorised fused kernel (PEC x, y)
 
-// Rows per CTA (+1 halo warp), chosen by measurement on the 128x128x512
-// waveguide: FP32 7 rows (8 warps, 2 CTAs/SM, no spills: 110 us; 8 rows 123,
-// 15 rows 122), FP64 8 rows (1269 us; 7 rows 1316).
-#ifndef MMX_VEC_F32_ROWS
-#define MMX_VEC_F32_ROWS 7
-#endif
-#ifndef MMX_VEC_F32_STAGES
-#define MMX_VEC_F32_STAGES 2
-#endif
-template <typename T> struct VecRows;
-template <> struct VecRows<float> { static constexpr int value = MMX_VEC_F32_ROWS; };
-template <> struct VecRows<double> { static constexpr int value = 8; };
-// Plane stages in the shared-memory ring (2: two CTAs per SM; more: one CTA
-// per SM with ST-1 planes in flight).  Variants that also stage the ca
-// arrays (sigma != 0) keep two stages to fit in shared memory.
-template <typename T, bool GEN> struct VecStages { static constexpr int value = 2; };
-template <> struct VecStages<float, false> { static constexpr int value = MMX_VEC_F32_STAGES; };
-
 template <typename T, typename S, bool GEN> constexpr size_t vec_smem_bytes()
 {
     constexpr int BY = VecRows<T>::value, ST = VecStages<T, GEN>::value;
@@ -1052,6 +1035,200 @@ template <typename T, typename S = T> static int energy_t(mmx_ctx *ctx, double *
     }
     *out = s + c;
     return MMX_OK;
+}
+
+// ============================================================ adjoint
+//
+// Gradient of the time-integrated Poynting flux through a z node plane with
+// respect to eps_r of every cell, by the discrete adjoint of the per-update
+// path (mmx_adjoint.cuh), with the forward states checkpointed every C steps
+// and each segment recomputed once in the reverse sweep.
+
+// The state a step starts from: E, H and the PML split parts.
+struct AdjSnap {
+    void *a[10] = {};
+};
+
+template <typename T> static void snap_ptrs(mmx_ctx *c, void *p[10])
+{
+    for (int a = 0; a < 3; a++) {
+        p[a] = c->E[a];
+        p[3 + a] = c->H[a];
+    }
+    for (int a = 0; a < 2; a++) {
+        p[6 + a] = c->Ezp[a];
+        p[8 + a] = c->Hzp[a];
+    }
+}
+
+template <typename T> static int snap_copy(mmx_ctx *ctx, AdjSnap &s, bool save)
+{
+    mmx_ctx *const c = ctx;
+    void *live[10];
+    snap_ptrs<T>(c, live);
+    const size_t bytes = c->npad * sizeof(T);
+    for (int q = 0; q < 10; q++) {
+        if (!live[q]) continue;
+        if (save)
+            CK(cudaMemcpyAsync(s.a[q], live[q], bytes, cudaMemcpyDeviceToDevice, c->stream));
+        else
+            CK(cudaMemcpyAsync(live[q], s.a[q], bytes, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return MMX_OK;
+}
+
+template <typename T> static Ptr3<T> snap3(const AdjSnap &s, int base)
+{
+    Ptr3<T> p = {{(T *)s.a[base], (T *)s.a[base + 1], (T *)s.a[base + 2]}};
+    return p;
+}
+
+template <typename T>
+static int flux_gradient_t(mmx_ctx *ctx, int kp, int nsteps, int every, double *loss, double *grad)
+{
+    std::vector<void *> mem;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(ctx->stream);
+        for (void *p : mem) cudaFree(p);
+    };
+    auto alloc = [&](size_t bytes, void **p) {
+        if (cudaMalloc(p, bytes) != cudaSuccess) return fail(ctx, MMX_ERR_OOM, "adjoint: out of device memory");
+        mem.push_back(*p);
+        if (cudaMemsetAsync(*p, 0, bytes, ctx->stream) != cudaSuccess) return fail(ctx, MMX_ERR_CUDA, "memset");
+        return MMX_OK;
+    };
+    const size_t fb = ctx->npad * sizeof(T), db = ctx->npad * sizeof(double);
+    const bool pml = ctx->g.npml > 0;
+    const int nseg = (nsteps + every - 1) / every;
+    int rc = MMX_OK;
+    auto snap_alloc = [&](AdjSnap &sn) {
+        void *live[10];
+        snap_ptrs<T>(ctx, live);
+        for (int q = 0; q < 10 && !rc; q++)
+            if (live[q]) rc = alloc(fb, &sn.a[q]);
+    };
+    std::vector<AdjSnap> ck(nseg + 1), seg(every);
+    for (auto &sn : ck) snap_alloc(sn);
+    for (auto &sn : seg) snap_alloc(sn);
+    AdjSnap half;                     // H^(n+1/2) scratch (with its PML part)
+    snap_alloc(half);
+    AdjState<T> a = {};
+    for (int c = 0; c < 3 && !rc; c++) {
+        rc = alloc(fb, (void **)&a.lE[c]);
+        if (!rc) rc = alloc(fb, (void **)&a.lH[c]);
+        if (!rc) rc = alloc(fb, (void **)&a.fR[c]);
+        if (!rc) rc = alloc(fb, (void **)&a.fZ[c]);
+        if (!rc) rc = alloc(fb, (void **)&a.eR[c]);
+        if (!rc) rc = alloc(fb, (void **)&a.eZ[c]);
+        if (!rc) rc = alloc(db, (void **)&a.gcb[c]);
+        if (!rc) rc = alloc(db, (void **)&a.gca[c]);
+    }
+    for (int c = 0; c < 2 && !rc && pml; c++) {
+        rc = alloc(fb, (void **)&a.lEz[c]);
+        if (!rc) rc = alloc(fb, (void **)&a.lHz[c]);
+    }
+    if (rc) {
+        cleanup();
+        return rc;
+    }
+    const long long n0 = ctx->steps;
+    // ---- forward: checkpoints every `every` steps, loss by the flux monitor
+    std::vector<int> saved_flux = ctx->flux_k;
+    ctx->flux_k.assign(1, kp);
+    rc = ensure_monitor(ctx);
+    if (!rc && cudaMemsetAsync(ctx->flux_acc, 0, 4 * sizeof(double), ctx->stream) != cudaSuccess)
+        rc = fail(ctx, MMX_ERR_CUDA, "memset");
+    if (!rc) rc = snap_copy<T>(ctx, ck[0], true);
+    for (int s = 0; s < nseg && !rc; s++) {
+        rc = step_plain<T>(ctx, std::min(every, nsteps - s * every));
+        if (!rc) rc = snap_copy<T>(ctx, ck[s + 1], true);
+    }
+    double acc[4] = {0, 0, 0, 0};
+    if (!rc) {
+        CK(cudaMemcpyAsync(acc, ctx->flux_acc, sizeof acc, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    ctx->flux_k = saved_flux;
+    if (!rc) rc = read_status(ctx);
+    if (rc) {
+        cleanup();
+        return rc;
+    }
+    *loss = acc[0] + acc[1];
+    // ---- reverse sweep
+    dim3 B = node_block(), G = node_grid(ctx);
+    const int npt = ctx->g.X * (ctx->desc.n[1] + 1);
+    const T w = (T)(ctx->desc.dt * ctx->desc.d[0] * ctx->desc.d[1]);
+    const int nsrc = (int)ctx->src.size();
+    for (int s = nseg - 1; s >= 0 && !rc; s--) {
+        const int len = std::min(every, nsteps - s * every);
+        // recompute the segment, keeping the state before each step
+        rc = snap_copy<T>(ctx, ck[s], false);
+        ctx->steps = n0 + (long long)s * every;
+        for (int m = 0; m < len && !rc; m++) {
+            rc = snap_copy<T>(ctx, seg[m], true);
+            if (!rc) rc = step_plain<T>(ctx, 1);
+        }
+        for (int m = len - 1; m >= 0 && !rc; m--) {
+            const long long n = n0 + (long long)s * every + m;
+            const AdjSnap &before = seg[m];
+            const AdjSnap &after = m + 1 < len ? seg[m + 1] : ck[s + 1];
+            // loss term of time n+1
+            k_adj_flux<T><<<(npt + 255) / 256, 256, 0, ctx->stream>>>(ctx->g, snap3<T>(after, 0), snap3<T>(after, 3),
+                                                                      kp, w, a);
+            Fields<T> f = make_fields<T>(ctx);
+            // second H half step (with E^(n+1))
+            k_adj_h<T><<<G, B, 0, ctx->stream>>>(ctx->g, f, a);
+            k_adj_curl_e<T><<<G, B, 0, ctx->stream>>>(ctx->g, a);
+            // E update: needs H^(n+1/2), recomputed from the state before
+            {
+                rc = upload_amplitudes<T>(ctx, n, 1);
+                if (rc) break;
+                const size_t bytes = ctx->npad * sizeof(T);
+                for (int q = 3; q < 6; q++)
+                    CK(cudaMemcpyAsync(half.a[q], before.a[q], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+                for (int q = 8; q < 10; q++)
+                    if (before.a[q]) CK(cudaMemcpyAsync(half.a[q], before.a[q], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+                Fields<T> fh = f;
+                for (int c = 0; c < 3; c++) {
+                    fh.E[c] = (T *)before.a[c];
+                    fh.H[c] = (T *)half.a[3 + c];
+                }
+                for (int c = 0; c < 2; c++) fh.Hzp[c] = (T *)half.a[8 + c];
+                k_h_update<T><<<G, B, 0, ctx->stream>>>(ctx->g, fh, 0, 0, 0, 0, 0, 0);
+                Fields<T> fe = f;
+                fe.src_amp = (const T *)ctx->damp;
+                Ptr3<T> Z0 = {{(T *)before.a[6], (T *)before.a[7], nullptr}};
+                k_adj_e<T><<<G, B, 0, ctx->stream>>>(ctx->g, fe, snap3<T>(half, 3), snap3<T>(before, 0), Z0,
+                                                     (const Src<T> *)ctx->dsrc, nsrc, a);
+                k_adj_curl_h<T><<<G, B, 0, ctx->stream>>>(ctx->g, a);
+            }
+            // first H half step (with E^n)
+            k_adj_h<T><<<G, B, 0, ctx->stream>>>(ctx->g, f, a);
+            k_adj_curl_e<T><<<G, B, 0, ctx->stream>>>(ctx->g, a);
+            if (cudaGetLastError() != cudaSuccess) rc = fail(ctx, MMX_ERR_CUDA, "adjoint launch failed");
+        }
+    }
+    // gradient per cell, and the context back at the end of the forward run
+    if (!rc) {
+        double *dgrad = nullptr;
+        const long long ncell = (long long)ctx->desc.n[0] * ctx->desc.n[1] * ctx->desc.n[2];
+        rc = alloc((size_t)ncell * sizeof(double), (void **)&dgrad);
+        const double **gtab = nullptr;
+        if (!rc) rc = alloc(6 * sizeof(double *), (void **)&gtab);
+        if (!rc) {
+            const double *h[6] = {a.gcb[0], a.gcb[1], a.gcb[2], a.gca[0], a.gca[1], a.gca[2]};
+            CK(cudaMemcpyAsync((void *)gtab, h, sizeof h, cudaMemcpyHostToDevice, ctx->stream));
+            k_adj_eps<<<(int)((ncell + 255) / 256), 256, 0, ctx->stream>>>(ctx->g, ctx->cell[0], ctx->cell[1], gtab,
+                                                                           gtab + 3, dgrad);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(grad, dgrad, (size_t)ncell * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        if (!rc) rc = snap_copy<T>(ctx, ck[nseg], false);
+        ctx->steps = n0 + nsteps;
+    }
+    cleanup();
+    return rc ? rc : read_status(ctx);
 }
 
 extern "C" {
@@ -1550,6 +1727,23 @@ int mmx_set_storage_scale(mmx_ctx *ctx, double sE, double sH)
     ctx->sE = sE;
     ctx->sH = sH;
     return MMX_OK;
+}
+
+int mmx_flux_gradient(mmx_ctx *ctx, int kp, int nsteps, int checkpoint_every, double *loss, double *grad_eps)
+{
+    if (!ctx || !ctx->E[0] || !loss || !grad_eps) return MMX_ERR_INVALID;
+    if (ctx->magnetic) return fail(ctx, MMX_ERR_INVALID, "the adjoint covers grids without magnetic material");
+    for (int a = 0; a < 3; a++)
+        if (ctx->g.per[a]) return fail(ctx, MMX_ERR_INVALID, "the adjoint covers grids without periodic axes");
+    if (is_fp16(ctx)) return fail(ctx, MMX_ERR_INVALID, "the adjoint runs in FP32 or FP64");
+    for (auto &q : ctx->src)
+        if (q.kind >= 2) return fail(ctx, MMX_ERR_INVALID, "the adjoint covers soft sources only");
+    if (!ctx->probes.empty() || !ctx->flux_k.empty())
+        return fail(ctx, MMX_ERR_INVALID, "remove probes and flux planes before the adjoint");
+    if (kp < 0 || kp > ctx->desc.n[2]) return fail(ctx, MMX_ERR_INVALID, "flux plane k must be in [0, nz]");
+    if (nsteps < 1 || checkpoint_every < 1) return fail(ctx, MMX_ERR_INVALID, "nsteps and checkpoint_every >= 1");
+    return is_fp64(ctx) ? flux_gradient_t<double>(ctx, kp, nsteps, checkpoint_every, loss, grad_eps)
+                        : flux_gradient_t<float>(ctx, kp, nsteps, checkpoint_every, loss, grad_eps);
 }
 
 int mmx_add_probe(mmx_ctx *ctx, int field, int i, int j, int k)

@@ -595,6 +595,24 @@ __global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
                                                 I.chunk, I.xstride, wk.y, wk.z, wk.w);
 }
 
+// Rows per CTA (+1 halo warp), chosen by measurement on the 128x128x512
+// waveguide: FP32 7 rows (8 warps, 2 CTAs/SM, no spills: 110 us; 8 rows 123,
+// 15 rows 122), FP64 8 rows (1269 us; 7 rows 1316).
+#ifndef MMX_VEC_F32_ROWS
+#define MMX_VEC_F32_ROWS 7
+#endif
+#ifndef MMX_VEC_F32_STAGES
+#define MMX_VEC_F32_STAGES 2
+#endif
+template <typename T> struct VecRows;
+template <> struct VecRows<float> { static constexpr int value = MMX_VEC_F32_ROWS; };
+template <> struct VecRows<double> { static constexpr int value = 8; };
+// Plane stages in the shared-memory ring (2: two CTAs per SM; more: one CTA
+// per SM with ST-1 planes in flight).  Variants that also stage the ca
+// arrays (sigma != 0) keep two stages to fit in shared memory.
+template <typename T, bool GEN> struct VecStages { static constexpr int value = 2; };
+template <> struct VecStages<float, false> { static constexpr int value = MMX_VEC_F32_STAGES; };
+
 // Zero the wall column x = nx and the wall row y = ny (all planes) of up to
 // 16 Yee arrays: every component there is either a PEC wall value or does
 // not exist, and the vectorised kernel never writes it.

@@ -24,7 +24,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="waveguide", choices=["waveguide", "yig_slab", "stress"])
     ap.add_argument("--n", type=int, default=0, help="stress: cube edge (default 512)")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "fp16"])
     ap.add_argument("--path", default="fused", choices=["fused", "plain"])
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
@@ -35,7 +35,7 @@ def main():
         w = workloads.yig_slab_32()
     else:
         w = workloads.stress(n=a.n or 512)
-    prec = mmx.FP32 if a.prec == "fp32" else mmx.FP64
+    prec = {"fp32": mmx.FP32, "fp64": mmx.FP64, "fp16": mmx.FP16}[a.prec]
     path = mmx.PATH_FUSED if a.path == "fused" else mmx.PATH_PLAIN
     s = mmx.from_workload(w, prec=prec, path=path)
     s.step(a.warmup)
