@@ -210,23 +210,32 @@ typedef struct {
     double total_ms;
 } mmx_kernel_profile;
 
-/* Discrete adjoint of the electromagnetic update (Sec. 3.2 H half step,
- * E update with the time-centred split-field z-PML, H half step), for grids
- * without magnetic material and without periodic axes, FP32 or FP64, soft
- * sources only, no probes or flux planes registered.  From the current
- * state the context runs nsteps steps (the per-update path), accumulating
+/* Discrete adjoint of the second-order scheme (Sec. 3.2: H/M half step,
+ * E update with the time-centred split-field z-PML, H/M half step), for
+ * grids without periodic axes, FP32 or FP64, soft sources only, no probes
+ * or flux planes registered; with magnetic material, the second-order
+ * scheme (order 2).  From the current state the context runs nsteps steps
+ * (the per-update path), accumulating
  *   loss = sum_(n=1..nsteps) dt P(E^n, H^n)
  * with P the Poynting power through z node plane kp as in mmx_add_flux_plane,
  * then sweeps back through the steps, recomputing each checkpoint_every-step
  * segment from its checkpoint, and writes d loss / d eps_r of every cell
- * (host array of nx*ny*nz doubles, x fastest) to grad_eps and the loss to
- * *loss.  The context ends advanced by nsteps, as after mmx_step.  Device
- * memory: about (nsteps/checkpoint_every + checkpoint_every + 1) copies of
- * the E/H state plus 22 grid arrays.  Synchronises the context stream.
+ * (host array of nx*ny*nz doubles, x fastest) to grad_eps, d loss / d H0
+ * (the uniform bias of mmx_set_bias, host array of 3 doubles; zero without
+ * magnetic material) to grad_h0 unless it is NULL, and the loss to *loss.
+ * The magnetic half steps are transposed through their converged fixed
+ * point (implicit-function adjoint of Eqs. llg_tra4-6 with N() and
+ * Eq. iterate_H), solved by the same Jacobi sweep as the forward iteration
+ * to a relative change of 1e-13 (FP64) or 1e-6 (FP32); a sweep that does not
+ * get there within the forward's largest iteration count + 8 (at most
+ * max_iter) returns MMX_ERR_NOT_CONVERGED.  The context ends advanced by
+ * nsteps, as after mmx_step.  Device memory: about (nsteps/checkpoint_every
+ * + checkpoint_every + 2) copies of the E/H(/M) state plus 22 grid arrays
+ * and 63 magnetic-box arrays.  Synchronises the context stream.
  * MMX_ERR_INVALID for a context it does not cover, MMX_ERR_OOM when the
  * checkpoints do not fit. */
 MMX_API int mmx_flux_gradient(mmx_ctx *ctx, int kp, int nsteps, int checkpoint_every, double *loss,
-                              double *grad_eps);
+                              double *grad_eps, double *grad_h0);
 
 /* FP16 storage scales: E is stored as E / sE and H (with its PML split part)
  * as H / sH, so that the fields of a problem sit inside FP16's range

@@ -100,7 +100,7 @@ def lib():
     L.mmx_set_profiling.restype = I
     L.mmx_set_profiling.argtypes = [P, I]
     L.mmx_flux_gradient.restype = I
-    L.mmx_flux_gradient.argtypes = [P, I, I, I, dp, dp]
+    L.mmx_flux_gradient.argtypes = [P, I, I, I, dp, dp, dp]
     L.mmx_set_storage_scale.restype = I
     L.mmx_set_storage_scale.argtypes = [P, D, D]
     L.mmx_add_probe.restype = I
@@ -288,16 +288,19 @@ class Solver:
                                                  ctypes.byref(sy)), "mmx_get_field_device")
         return p.value, sx.value, sy.value
 
-    def flux_gradient(self, kp, nsteps, checkpoint_every=None):
+    def flux_gradient(self, kp, nsteps, checkpoint_every=None, with_h0=False):
         """Run nsteps steps and return (loss, d loss / d eps_r per cell) for the
         time-integrated Poynting flux through z node plane kp (discrete
-        adjoint, checkpointing every ~sqrt(nsteps) steps by default)."""
+        adjoint, checkpointing every ~sqrt(nsteps) steps by default); with
+        with_h0, (loss, d loss / d eps_r, d loss / d H0)."""
         every = int(checkpoint_every or max(1, round(nsteps ** 0.5)))
         loss = ctypes.c_double()
         grad = np.zeros(self.n[0] * self.n[1] * self.n[2], dtype=np.float64)
-        self._check(self._L.mmx_flux_gradient(self._h, int(kp), int(nsteps), every, ctypes.byref(loss), _dp(grad)),
-                    "mmx_flux_gradient")
-        return loss.value, grad.reshape(self.n[2], self.n[1], self.n[0])
+        gh0 = np.zeros(3, dtype=np.float64)
+        self._check(self._L.mmx_flux_gradient(self._h, int(kp), int(nsteps), every, ctypes.byref(loss), _dp(grad),
+                                              _dp(gh0)), "mmx_flux_gradient")
+        grad = grad.reshape(self.n[2], self.n[1], self.n[0])
+        return (loss.value, grad, gh0) if with_h0 else (loss.value, grad)
 
     def set_storage_scale(self, sE, sH):
         """FP16 contexts: store E as E/sE and H as H/sH (before any field or step)."""

@@ -1044,13 +1044,19 @@ template <typename T, typename S = T> static int energy_t(mmx_ctx *ctx, double *
 // path (mmx_adjoint.cuh), with the forward states checkpointed every C steps
 // and each segment recomputed once in the reverse sweep.
 
-// The state a step starts from: E, H and the PML split parts.
+// The state a step starts from: E, H, the PML split parts and, on grids
+// with magnetic material, M (the nine box arrays).
+constexpr int kSnapArrays = 19;
 struct AdjSnap {
-    void *a[10] = {};
+    void *a[kSnapArrays] = {};
 };
 
-template <typename T> static void snap_ptrs(mmx_ctx *c, void *p[10])
+template <typename T> static void snap_ptrs(mmx_ctx *c, void *p[kSnapArrays], size_t bytes[kSnapArrays])
 {
+    for (int q = 0; q < kSnapArrays; q++) {
+        p[q] = nullptr;
+        bytes[q] = c->npad * sizeof(T);
+    }
     for (int a = 0; a < 3; a++) {
         p[a] = c->E[a];
         p[3 + a] = c->H[a];
@@ -1059,20 +1065,27 @@ template <typename T> static void snap_ptrs(mmx_ctx *c, void *p[10])
         p[6 + a] = c->Ezp[a];
         p[8 + a] = c->Hzp[a];
     }
+    if (c->magnetic)
+        for (int q = 0; q < 9; q++) {
+            p[10 + q] = c->bM[q];
+            bytes[10 + q] = (size_t)c->nb * sizeof(T);
+        }
 }
 
+// Copy the live state into s (save) or back; M is taken from (and left in)
+// the box arrays.
 template <typename T> static int snap_copy(mmx_ctx *ctx, AdjSnap &s, bool save)
 {
     mmx_ctx *const c = ctx;
-    void *live[10];
-    snap_ptrs<T>(c, live);
-    const size_t bytes = c->npad * sizeof(T);
-    for (int q = 0; q < 10; q++) {
+    void *live[kSnapArrays];
+    size_t bytes[kSnapArrays];
+    snap_ptrs<T>(c, live, bytes);
+    for (int q = 0; q < kSnapArrays; q++) {
         if (!live[q]) continue;
         if (save)
-            CK(cudaMemcpyAsync(s.a[q], live[q], bytes, cudaMemcpyDeviceToDevice, c->stream));
+            CK(cudaMemcpyAsync(s.a[q], live[q], bytes[q], cudaMemcpyDeviceToDevice, c->stream));
         else
-            CK(cudaMemcpyAsync(live[q], s.a[q], bytes, cudaMemcpyDeviceToDevice, c->stream));
+            CK(cudaMemcpyAsync(live[q], s.a[q], bytes[q], cudaMemcpyDeviceToDevice, c->stream));
     }
     return MMX_OK;
 }
@@ -1083,8 +1096,48 @@ template <typename T> static Ptr3<T> snap3(const AdjSnap &s, int base)
     return p;
 }
 
+template <typename T> static MPtr<T> snapM(const AdjSnap &s)
+{
+    MPtr<T> p;
+    for (int q = 0; q < 9; q++) p.p[q] = (T *)s.a[10 + q];
+    return p;
+}
+
+// Largest iteration count among the last `count` logged H/M half steps.
+static int logged_iter_max(mmx_ctx *ctx, long long count)
+{
+    unsigned long long hs = 0;
+    if (cudaMemcpy(&hs, ctx->halfsteps, sizeof hs, cudaMemcpyDeviceToHost) != cudaSuccess) return kMaxIter;
+    const long long m = std::min<long long>(std::min<long long>((long long)hs, kIterLogCap), count);
+    std::vector<int> v(kIterLogCap);
+    if (cudaMemcpy(v.data(), ctx->iterlog, kIterLogCap * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return kMaxIter;
+    int mx = 1;
+    for (long long q = 0; q < m; q++) mx = std::max(mx, v[(hs - 1 - q) % kIterLogCap]);
+    return mx;
+}
+
+// One magnetic half step's adjoint, before its k_adj_h: the fixed-point
+// adjoint of the LLG solve from the state it started from (Hn, Mn) and the
+// H it ended with (Hs).
 template <typename T>
-static int flux_gradient_t(mmx_ctx *ctx, int kp, int nsteps, int every, double *loss, double *grad)
+static int adj_mag_half(mmx_ctx *ctx, const Box<T> &b, Ptr3<T> Hn, MPtr<T> Mn, Ptr3<T> Hs, const AdjState<T> &a,
+                        const AdjMag<T> &m)
+{
+    const int nblk = (int)((std::max<long long>(b.nb, 2LL * m.kmax) + 255) / 256);
+    k_adjm_prep<T><<<nblk, 256, 0, ctx->stream>>>(ctx->g, b, Hn, Mn, Hs, a, m);
+    for (int it = 0; it < m.kmax; it++) {
+        k_adjm_heff<T><<<nblk, 256, 0, ctx->stream>>>(b, m, it);
+        k_adjm_sweep<T><<<nblk, 256, 0, ctx->stream>>>(ctx->g, b, m, it);
+    }
+    k_adjm_heff<T><<<nblk, 256, 0, ctx->stream>>>(b, m, -1);
+    k_adjm_close<T><<<nblk, 256, 0, ctx->stream>>>(ctx->g, b, Hn, Mn, a, m);
+    CK(cudaGetLastError());
+    return MMX_OK;
+}
+
+template <typename T>
+static int flux_gradient_t(mmx_ctx *ctx, int kp, int nsteps, int every, double *loss, double *grad, double *grad_h0)
 {
     std::vector<void *> mem;
     auto cleanup = [&]() {
@@ -1098,19 +1151,20 @@ static int flux_gradient_t(mmx_ctx *ctx, int kp, int nsteps, int every, double *
         return MMX_OK;
     };
     const size_t fb = ctx->npad * sizeof(T), db = ctx->npad * sizeof(double);
-    const bool pml = ctx->g.npml > 0;
+    const bool pml = ctx->g.npml > 0, mag = ctx->magnetic && ctx->nmag > 0;
     const int nseg = (nsteps + every - 1) / every;
     int rc = MMX_OK;
     auto snap_alloc = [&](AdjSnap &sn) {
-        void *live[10];
-        snap_ptrs<T>(ctx, live);
-        for (int q = 0; q < 10 && !rc; q++)
-            if (live[q]) rc = alloc(fb, &sn.a[q]);
+        void *live[kSnapArrays];
+        size_t bytes[kSnapArrays];
+        snap_ptrs<T>(ctx, live, bytes);
+        for (int q = 0; q < kSnapArrays && !rc; q++)
+            if (live[q]) rc = alloc(bytes[q], &sn.a[q]);
     };
     std::vector<AdjSnap> ck(nseg + 1), seg(every);
     for (auto &sn : ck) snap_alloc(sn);
     for (auto &sn : seg) snap_alloc(sn);
-    AdjSnap half;                     // H^(n+1/2) scratch (with its PML part)
+    AdjSnap half;                     // the state after the first H/M half step
     snap_alloc(half);
     AdjState<T> a = {};
     for (int c = 0; c < 3 && !rc; c++) {
@@ -1127,6 +1181,19 @@ static int flux_gradient_t(mmx_ctx *ctx, int kp, int nsteps, int every, double *
         rc = alloc(fb, (void **)&a.lEz[c]);
         if (!rc) rc = alloc(fb, (void **)&a.lHz[c]);
     }
+    AdjMag<T> am = {};
+    if (mag && !rc) {
+        const size_t bb = (size_t)ctx->nb * sizeof(T);
+        T **sets[7] = {am.lM, am.gM, am.mu, am.A, am.B, am.lHe, am.lHn};
+        for (int q = 0; q < 7 && !rc; q++)
+            for (int c = 0; c < 9 && !rc; c++) rc = alloc(bb, (void **)&sets[q][c]);
+        if (!rc) rc = alloc(2 * kMaxIter * sizeof(unsigned long long), (void **)&am.res);
+        if (!rc) rc = alloc(sizeof(int), (void **)&am.nc);
+        am.eps = sizeof(T) == 8 ? 1e-13 : 1e-6;
+    }
+    double *dh0 = nullptr;
+    if (!rc) rc = alloc(3 * sizeof(double), (void **)&dh0);
+    am.gh0 = dh0;
     if (rc) {
         cleanup();
         return rc;
@@ -1138,9 +1205,13 @@ static int flux_gradient_t(mmx_ctx *ctx, int kp, int nsteps, int every, double *
     rc = ensure_monitor(ctx);
     if (!rc && cudaMemsetAsync(ctx->flux_acc, 0, 4 * sizeof(double), ctx->stream) != cudaSuccess)
         rc = fail(ctx, MMX_ERR_CUDA, "memset");
+    if (!rc && cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned long long), ctx->stream) != cudaSuccess)
+        rc = fail(ctx, MMX_ERR_CUDA, "memset");
     if (!rc) rc = snap_copy<T>(ctx, ck[0], true);
+    if (!rc) rc = box_m_sync<T>(ctx, 1);
     for (int s = 0; s < nseg && !rc; s++) {
         rc = step_plain<T>(ctx, std::min(every, nsteps - s * every));
+        if (!rc) rc = box_m_sync<T>(ctx, 0);
         if (!rc) rc = snap_copy<T>(ctx, ck[s + 1], true);
     }
     double acc[4] = {0, 0, 0, 0};
@@ -1155,47 +1226,69 @@ static int flux_gradient_t(mmx_ctx *ctx, int kp, int nsteps, int every, double *
         return rc;
     }
     *loss = acc[0] + acc[1];
+    // the fixed-point adjoint contracts like the forward iteration: allow it
+    // the forward's largest sweep count plus a margin (it stops on its own)
+    if (mag) am.kmax = std::min(ctx->desc.max_iter, logged_iter_max(ctx, 2LL * nsteps) + 8);
     // ---- reverse sweep
     dim3 B = node_block(), G = node_grid(ctx);
     const int npt = ctx->g.X * (ctx->desc.n[1] + 1);
     const T w = (T)(ctx->desc.dt * ctx->desc.d[0] * ctx->desc.d[1]);
     const int nsrc = (int)ctx->src.size();
+    const Box<T> bx = make_box<T>(ctx);
     for (int s = nseg - 1; s >= 0 && !rc; s--) {
         const int len = std::min(every, nsteps - s * every);
         // recompute the segment, keeping the state before each step
         rc = snap_copy<T>(ctx, ck[s], false);
+        if (!rc) rc = box_m_sync<T>(ctx, 1);
         ctx->steps = n0 + (long long)s * every;
         for (int m = 0; m < len && !rc; m++) {
-            rc = snap_copy<T>(ctx, seg[m], true);
+            rc = box_m_sync<T>(ctx, 0);
+            if (!rc) rc = snap_copy<T>(ctx, seg[m], true);
             if (!rc) rc = step_plain<T>(ctx, 1);
         }
         for (int m = len - 1; m >= 0 && !rc; m--) {
             const long long n = n0 + (long long)s * every + m;
             const AdjSnap &before = seg[m];
             const AdjSnap &after = m + 1 < len ? seg[m + 1] : ck[s + 1];
+            Fields<T> f = make_fields<T>(ctx);
+            // H^(n+1/2) (and M^(n+1/2)) recomputed from the state before
+            const size_t bytes = ctx->npad * sizeof(T);
+            for (int q = 3; q < 6; q++)
+                CK(cudaMemcpyAsync(half.a[q], before.a[q], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+            for (int q = 8; q < 10; q++)
+                if (before.a[q]) CK(cudaMemcpyAsync(half.a[q], before.a[q], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+            Fields<T> fh = f;
+            for (int c = 0; c < 3; c++) {
+                fh.E[c] = (T *)before.a[c];
+                fh.H[c] = (T *)half.a[3 + c];
+            }
+            for (int c = 0; c < 2; c++) fh.Hzp[c] = (T *)half.a[8 + c];
+            if (mag) {
+                const size_t mb = (size_t)ctx->nb * sizeof(T);
+                for (int q = 0; q < 9; q++)
+                    CK(cudaMemcpyAsync(ctx->bM[q], before.a[10 + q], mb, cudaMemcpyDeviceToDevice, ctx->stream));
+                rc = box_m_sync<T>(ctx, 1);
+                if (!rc) rc = half_step<T, T>(ctx, fh, bx, (n + 0.5) * ctx->desc.dt);
+                if (!rc) rc = box_m_sync<T>(ctx, 0);
+                for (int q = 0; q < 9 && !rc; q++)
+                    CK(cudaMemcpyAsync(half.a[10 + q], ctx->bM[q], mb, cudaMemcpyDeviceToDevice, ctx->stream));
+                if (rc) break;
+            } else {
+                k_h_update<T><<<G, B, 0, ctx->stream>>>(ctx->g, fh, 0, 0, 0, 0, 0, 0);
+            }
             // loss term of time n+1
             k_adj_flux<T><<<(npt + 255) / 256, 256, 0, ctx->stream>>>(ctx->g, snap3<T>(after, 0), snap3<T>(after, 3),
                                                                       kp, w, a);
-            Fields<T> f = make_fields<T>(ctx);
-            // second H half step (with E^(n+1))
+            // second H/M half step (with E^(n+1)), from the half state to after
+            if (mag) rc = adj_mag_half<T>(ctx, bx, snap3<T>(half, 3), snapM<T>(half), snap3<T>(after, 3), a, am);
+            if (rc) break;
             k_adj_h<T><<<G, B, 0, ctx->stream>>>(ctx->g, f, a);
+            if (mag) k_adjm_curl<T><<<(int)((ctx->nb + 255) / 256), 256, 0, ctx->stream>>>(ctx->g, bx, a, am);
             k_adj_curl_e<T><<<G, B, 0, ctx->stream>>>(ctx->g, a);
-            // E update: needs H^(n+1/2), recomputed from the state before
+            // E update: needs H^(n+1/2)
             {
                 rc = upload_amplitudes<T>(ctx, n, 1);
                 if (rc) break;
-                const size_t bytes = ctx->npad * sizeof(T);
-                for (int q = 3; q < 6; q++)
-                    CK(cudaMemcpyAsync(half.a[q], before.a[q], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
-                for (int q = 8; q < 10; q++)
-                    if (before.a[q]) CK(cudaMemcpyAsync(half.a[q], before.a[q], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
-                Fields<T> fh = f;
-                for (int c = 0; c < 3; c++) {
-                    fh.E[c] = (T *)before.a[c];
-                    fh.H[c] = (T *)half.a[3 + c];
-                }
-                for (int c = 0; c < 2; c++) fh.Hzp[c] = (T *)half.a[8 + c];
-                k_h_update<T><<<G, B, 0, ctx->stream>>>(ctx->g, fh, 0, 0, 0, 0, 0, 0);
                 Fields<T> fe = f;
                 fe.src_amp = (const T *)ctx->damp;
                 Ptr3<T> Z0 = {{(T *)before.a[6], (T *)before.a[7], nullptr}};
@@ -1203,8 +1296,11 @@ static int flux_gradient_t(mmx_ctx *ctx, int kp, int nsteps, int every, double *
                                                      (const Src<T> *)ctx->dsrc, nsrc, a);
                 k_adj_curl_h<T><<<G, B, 0, ctx->stream>>>(ctx->g, a);
             }
-            // first H half step (with E^n)
+            // first H/M half step (with E^n), from before to the half state
+            if (mag) rc = adj_mag_half<T>(ctx, bx, snap3<T>(before, 3), snapM<T>(before), snap3<T>(half, 3), a, am);
+            if (rc) break;
             k_adj_h<T><<<G, B, 0, ctx->stream>>>(ctx->g, f, a);
+            if (mag) k_adjm_curl<T><<<(int)((ctx->nb + 255) / 256), 256, 0, ctx->stream>>>(ctx->g, bx, a, am);
             k_adj_curl_e<T><<<G, B, 0, ctx->stream>>>(ctx->g, a);
             if (cudaGetLastError() != cudaSuccess) rc = fail(ctx, MMX_ERR_CUDA, "adjoint launch failed");
         }
@@ -1223,11 +1319,19 @@ static int flux_gradient_t(mmx_ctx *ctx, int kp, int nsteps, int every, double *
                                                                            gtab + 3, dgrad);
             CK(cudaGetLastError());
             CK(cudaMemcpyAsync(grad, dgrad, (size_t)ncell * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+            if (grad_h0) CK(cudaMemcpyAsync(grad_h0, dh0, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
         }
         if (!rc) rc = snap_copy<T>(ctx, ck[nseg], false);
         ctx->steps = n0 + nsteps;
     }
+    int nc = 0;
+    if (!rc && mag) {
+        CK(cudaMemcpyAsync(&nc, am.nc, sizeof nc, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
     cleanup();
+    if (!rc && nc)
+        rc = fail(ctx, MMX_ERR_NOT_CONVERGED, "adjoint: a fixed-point sweep of an H/M half step missed its tolerance");
     return rc ? rc : read_status(ctx);
 }
 
@@ -1729,10 +1833,12 @@ int mmx_set_storage_scale(mmx_ctx *ctx, double sE, double sH)
     return MMX_OK;
 }
 
-int mmx_flux_gradient(mmx_ctx *ctx, int kp, int nsteps, int checkpoint_every, double *loss, double *grad_eps)
+int mmx_flux_gradient(mmx_ctx *ctx, int kp, int nsteps, int checkpoint_every, double *loss, double *grad_eps,
+                      double *grad_h0)
 {
     if (!ctx || !ctx->E[0] || !loss || !grad_eps) return MMX_ERR_INVALID;
-    if (ctx->magnetic) return fail(ctx, MMX_ERR_INVALID, "the adjoint covers grids without magnetic material");
+    if (ctx->magnetic && ctx->desc.order != 2)
+        return fail(ctx, MMX_ERR_INVALID, "the adjoint of magnetic grids covers the second-order scheme");
     for (int a = 0; a < 3; a++)
         if (ctx->g.per[a]) return fail(ctx, MMX_ERR_INVALID, "the adjoint covers grids without periodic axes");
     if (is_fp16(ctx)) return fail(ctx, MMX_ERR_INVALID, "the adjoint runs in FP32 or FP64");
@@ -1742,8 +1848,9 @@ int mmx_flux_gradient(mmx_ctx *ctx, int kp, int nsteps, int checkpoint_every, do
         return fail(ctx, MMX_ERR_INVALID, "remove probes and flux planes before the adjoint");
     if (kp < 0 || kp > ctx->desc.n[2]) return fail(ctx, MMX_ERR_INVALID, "flux plane k must be in [0, nz]");
     if (nsteps < 1 || checkpoint_every < 1) return fail(ctx, MMX_ERR_INVALID, "nsteps and checkpoint_every >= 1");
-    return is_fp64(ctx) ? flux_gradient_t<double>(ctx, kp, nsteps, checkpoint_every, loss, grad_eps)
-                        : flux_gradient_t<float>(ctx, kp, nsteps, checkpoint_every, loss, grad_eps);
+    if (grad_h0) grad_h0[0] = grad_h0[1] = grad_h0[2] = 0.0;
+    return is_fp64(ctx) ? flux_gradient_t<double>(ctx, kp, nsteps, checkpoint_every, loss, grad_eps, grad_h0)
+                        : flux_gradient_t<float>(ctx, kp, nsteps, checkpoint_every, loss, grad_eps, grad_h0);
 }
 
 int mmx_add_probe(mmx_ctx *ctx, int field, int i, int j, int k)

@@ -18,6 +18,8 @@ this build:
                                TE10 soft plane source.
   * ``stress``                 512^3 PEC box, centred random 256^3 magnetic block.
   * ``convergence(N)``         the paper's periodic convergence problem (Sec. 5.1).
+  * ``filter_design``          64x64x256 ferrite-loaded guide with a random
+                               permittivity design region, for the adjoint.
 """
 from __future__ import annotations
 
@@ -72,6 +74,8 @@ class Workload:
     # optional initial Yee-located fields: field id -> flat float64 array
     fields: Dict[int, np.ndarray] = dataclasses.field(default_factory=dict)
     steps: int = 1
+    # z node plane of the flux loss (design workloads)
+    flux_k: Optional[int] = None
 
     @property
     def ncells(self) -> int:
@@ -374,3 +378,38 @@ __all__ = [
     "waveguide", "stress", "convergence", "random_small", "PERIODIC", "PEC", "PML",
     "SRC_POINT_J", "SRC_PLANE_J_TE10", "SRC_HARD_E", "SRC_HARD_H",
 ]
+
+
+def filter_design(n=(64, 64, 256), seed: int = 0, steps: int = 2000, dx: float = 4e-4, npml: int = 10,
+                  h0: float = 1e5, tol: float = 1e-10) -> Workload:
+    """Design problem of the adjoint: a PEC guide (TE10 cutoff c/(2 nx dx),
+    5.86 GHz at the default size) with npml-cell z-PML ends; a YIG-like slab
+    (eps_r 15) on z cells [3nz/8, 5nz/8) over the centred nx/2 x ny/8
+    cross-section; eps_r ~ U[1, 12] on the rest of the centred
+    nx/2 x ny/2 x nz/4 design region; bias h0 along y with M = y + 1% seeded
+    tilt; a 10 GHz TE10 soft Jy plane source at z = max(npml + 2, 20 nz/256);
+    the flux loss through z node plane min(230 nz/256, nz - npml - 2)."""
+    nx, ny, nz = n
+    shp = _cell_shape(n)
+    d = (dx, dx, dx)
+    dt = cfl_dt(d, 0.9)
+    rng = np.random.default_rng(seed)
+    z0, z1 = (3 * nz) // 8, (5 * nz) // 8
+    x0, x1 = nx // 4, (3 * nx) // 4
+    hy = max(1, ny // 16)
+    slab = np.zeros(shp, dtype=bool)
+    slab[z0:z1, ny // 2 - hy:ny // 2 + hy, x0:x1] = True
+    eps = np.ones(shp)
+    eps[z0:z1, ny // 4:(3 * ny) // 4, x0:x1] = rng.uniform(1.0, 12.0, size=(z1 - z0, (3 * ny) // 4 - ny // 4, x1 - x0))
+    eps = np.where(slab, YIG_EPS, eps)
+    Ms = np.where(slab, YIG_MS, 0.0)
+    u1, u2, _ = _tilted_z(rng, shp)
+    mx, my, mz = (np.where(slab, Ms * c, 0.0) for c in (u1, np.ones(shp), u2))
+    f0 = 10e9
+    src = Source(SRC_PLANE_J_TE10, 1, 0, 0, max(npml + 2, (20 * nz) // 256), amp=1e7, f0=f0, tp=1.0 / f0,
+                 t0=3.0 / f0)
+    return Workload(
+        name=f"filter_design_{nx}x{ny}x{nz}", n=tuple(n), d=d, dt=dt, bc=(PEC, PEC, PML), pml_cells=npml,
+        tol=tol, max_iter=64, h0=(0.0, float(h0), 0.0), eps_r=eps, sigma=np.zeros(shp), mu_r=np.ones(shp),
+        Ms=Ms, alpha=np.where(slab, YIG_ALPHA, 0.0), gamma=np.where(slab, YIG_GAMMA, 0.0), m_cells=(mx, my, mz),
+        sources=[src], steps=steps, flux_k=min((230 * nz) // 256, nz - npml - 2))
