@@ -210,7 +210,7 @@ __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const i
 // parity `slot`, rows [2 slot + h][instance][kMaxIter + 1] (h = half step);
 // the other parity's rows are cleared here for the next launch.
 template <typename T, typename S = T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, BoxMinBlocks<T>::value)
     k_hm_box_batch(const BoxInst<T, S> *__restrict__ inst, int ninst, const int4 *__restrict__ mag,
                    const int *__restrict__ mag_inst, int nmag, const int4 *__restrict__ non,
                    const int *__restrict__ non_inst, int nnon, unsigned long long *res, unsigned long long *bar,
