@@ -62,6 +62,7 @@ struct mmx_ctx {
     bool walls_dirty = false;
     // coefficients
     void *ca[3] = {}, *cb[3] = {}, *fh[3] = {};
+    void *epsc = nullptr;                  // FP32 arithmetic: eps_r per cell, padded
     void *dampE = nullptr, *dampH = nullptr;
     bool any_sigma = false, any_mu = false;
     // cell-centred materials (double, compact nx*ny*nz; null = default)
@@ -266,6 +267,8 @@ template <typename T, typename S = T> static Fields<T, S> make_fields(mmx_ctx *c
     f.prof[0] = (const T *)c->dprof[0];
     f.prof[1] = (const T *)c->dprof[1];
     f.err = c->errw;
+    f.epsc = sizeof(T) == 4 ? (const T *)c->epsc : nullptr;
+    f.kcb = (T)(4.0 * c->desc.dt * kMu0 * kC0 * kC0);
     return f;
 }
 
@@ -474,6 +477,10 @@ template <typename T, typename S = T> static int set_materials_t(mmx_ctx *ctx)
     const Geo &g = ctx->g;
     dim3 B = node_block(), G = node_grid(ctx);
     double *eps_c = ctx->cell[0], *sig_c = ctx->cell[1], *mu_c = ctx->cell[2];
+    if (ctx->epsc && sizeof(T) == 4) {
+        k_eps_cells<T><<<G, B, 0, ctx->stream>>>(g, eps_c, (T *)ctx->epsc);
+        CK(cudaGetLastError());
+    }
     for (int c = 0; c < 3; c++) {
         k_e_coef<T><<<G, B, 0, ctx->stream>>>(g, eps_c, sig_c, c, (T *)ctx->ca[c], (T *)ctx->cb[c]);
         CK(cudaGetLastError());
@@ -1393,6 +1400,7 @@ int mmx_create(const mmx_grid_desc *desc, void *cuda_stream, mmx_ctx **out)
         if (!rc) rc = dalloc(ctx, &ctx->Ealt[a], sb);
         if (!rc) rc = dalloc(ctx, &ctx->Halt[a], sb);
         if (!rc) rc = dalloc(ctx, &ctx->cb[a], fb);
+        if (!rc && a == 0 && ctx->esz == 4) rc = dalloc(ctx, &ctx->epsc, fb);
     }
     if (!rc && g.npml > 0)
         for (int a = 0; a < 2 && !rc; a++) {
@@ -1448,7 +1456,7 @@ void mmx_destroy(mmx_ctx *ctx)
     for (int a = 0; a < 2; a++) { cudaFree(ctx->Ezp[a]); cudaFree(ctx->Hzp[a]); cudaFree(ctx->Ezpalt[a]); }
     for (int a = 0; a < 6; a++) cudaFree(ctx->cell[a]);
     free_box(ctx);
-    cudaFree(ctx->dampE); cudaFree(ctx->dampH);
+    cudaFree(ctx->dampE); cudaFree(ctx->dampH); cudaFree(ctx->epsc);
     cudaFree(ctx->probe_buf); cudaFree(ctx->dprobe);
     cudaFree(ctx->mon_partial); cudaFree(ctx->flux_acc);
     cudaFree(ctx->res); cudaFree(ctx->bar); cudaFree(ctx->iterlog); cudaFree(ctx->halfsteps);

@@ -109,6 +109,9 @@ template <typename T, typename S = T> struct Fields {
     const T *prof[2];   // TE10 profile sin(pi x/W): [0] at x = i dx, [1] at (i+1/2) dx
     int *err;
     T sE, sH, isE, isH; // storage scales and their inverses (FP16 storage only)
+    const T *epsc;      // FP32 arithmetic: eps_r per cell in the padded layout (1 in
+                        // the padding), from which the vectorised kernel forms cb
+    T kcb;              // 4 dt / eps0: cb = kcb / (sum of the edge's four cells' eps_r)
 };
 
 // Magnetic box: the bounding box of the magnetic faces grown by one face on

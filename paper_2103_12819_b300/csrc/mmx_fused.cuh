@@ -181,7 +181,10 @@ template <int N> __device__ __forceinline__ void cp_wait()
 // (byte offsets, every region a multiple of 16 bytes):
 //   sst [ST][6][R][W] of S  per plane: Hx, Hy (layer k+1/2), Hz (node k),
 //                           Ex, Ey, Ez of rows y0..y0+BY
-//   cst [ST][NC][R][W] of T cbx, cby, cbz [, cax, cay, caz]
+//   cst [ST][NC][R][W] of T cbx, cby, cbz [, cax, cay, caz]; with CBF the
+//                           eps_r row of cell plane k instead
+//   (CBF) eu [ST][W], el [ST][2][R] of T  eps_r of row y0-1 and of column
+//                           x0-1 (rows y and y-1) of cell plane k
 //   up  [ST][2][W] of S     Hx, Hz of row y0-1
 //   left [ST][2][R][LW] of S  Hy, Hz of column x0-1 (FP16: the 4-byte pair
 //                           ending there), one entry per row
@@ -190,7 +193,12 @@ template <typename T, typename S, int BY, bool GEN, int ST> struct VecLayout {
     static constexpr int V = Lanes<T>::V;
     static constexpr int W = 32 * V;
     static constexpr int R = BY + 1;
-    static constexpr int NC = GEN ? 6 : 3;
+    // FP32 arithmetic without sigma or mu_r: cb is formed from staged cell
+    // eps_r (one value per cell instead of three per-edge coefficients)
+    // (FP32 storage; with FP16 storage the kernel is bound by instruction
+    // issue and the added arithmetic costs more than the bytes it saves)
+    static constexpr bool CBF = !GEN && sizeof(T) == 4 && sizeof(S) == 4;
+    static constexpr int NC = GEN ? 6 : (CBF ? 1 : 3);
     static constexpr int LW = sizeof(S) >= 4 ? 1 : 4 / (int)sizeof(S);
     static constexpr size_t al(size_t x) { return (x + 15) / 16 * 16; }
     static constexpr size_t sst = 0;
@@ -199,7 +207,9 @@ template <typename T, typename S, int BY, bool GEN, int ST> struct VecLayout {
     static constexpr size_t left = up + al((size_t)ST * 2 * W * sizeof(S));
     static constexpr size_t ex = left + al((size_t)ST * 2 * R * LW * sizeof(S));
     static constexpr size_t ez = ex + al((size_t)2 * R * W * sizeof(T));
-    static constexpr size_t bytes = ez + al((size_t)2 * R * W * sizeof(T));
+    static constexpr size_t eu = ez + al((size_t)2 * R * W * sizeof(T));
+    static constexpr size_t el = eu + (CBF ? al((size_t)ST * W * sizeof(T)) : 0);
+    static constexpr size_t bytes = el + (CBF ? al((size_t)ST * 2 * R * sizeof(T)) : 0);
 };
 
 // The kernel body for the CTA at tile (bx, by, bz) of one grid: the single
@@ -227,6 +237,9 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
     };
     auto SEx = [&](int bb, int row) -> T * { return reinterpret_cast<T *>(smem_raw + L::ex) + (bb * R + row) * W; };
     auto SEz = [&](int bb, int row) -> T * { return reinterpret_cast<T *>(smem_raw + L::ez) + (bb * R + row) * W; };
+    constexpr bool CBF = L::CBF;
+    auto EU = [&](int st) -> T * { return reinterpret_cast<T *>(smem_raw + L::eu) + st * W; };
+    auto EL = [&](int st, int r2) -> T * { return reinterpret_cast<T *>(smem_raw + L::el) + (st * 2 + r2) * R; };
     const T sE = f.sE, sH = f.sH, isE = f.isE, isH = f.isH;
     constexpr int VB = V * (int)sizeof(S);      // bytes of one lane's S values
 
@@ -279,8 +292,17 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             cpn<VB>(SS(st, 3 + c, w) + col, io.Eo[c] + rb + kn, io.Eo[c], lane_on);
-            cp16(SC(st, c, w) + col, f.cb[c] + rb + kn, f.cb[c], lane_on);
+            if (!CBF) cp16(SC(st, c, w) + col, f.cb[c] + rb + kn, f.cb[c], lane_on);
             if (GEN && f.ca[c]) cp16(SC(st, 3 + c, w) + col, f.ca[c] + rb + kn, f.ca[c], lane_on);
+        }
+        if constexpr (CBF) {
+            // eps_r of cell plane k: this row, the row below, and column x0-1
+            cp16(SC(st, 0, w) + col, f.epsc + rb + kc, f.epsc, lane_on && lay);
+            if (w == 0) cp16(EU(st) + col, f.epsc + rbu + kc, f.epsc, up_on && lay);
+            if (lane == 0) {
+                cpn<4>(EL(st, 0) + w, f.epsc + rbl + kc, f.epsc, left_on && lay);
+                cpn<4>(EL(st, 1) + w, f.epsc + rbl - (unsigned)g.X + kc, f.epsc, left_on && j > 0 && lay);
+            }
         }
         if (w == 0) {
             cpn<VB>(U(st, 0) + col, io.Ho[0] + rbu + kc, io.Ho[0], up_on && lay);
@@ -296,6 +318,28 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
         cp_commit();
     };
 
+    // CBF: eps_r pair sums of cell plane k-1 along y (cells j-1, j: Ex) and
+    // along x (cells i-1, i: Ey), carried up the z march
+    T pyxp[V], pxyp[V];
+    vfill<T, V>(pyxp, T(2));
+    vfill<T, V>(pxyp, T(2));
+    if constexpr (CBF) {
+        const int ckm = cell_nb(g, 2, k0 - 1);
+        T a[V], au[V];
+        vfill<T, V>(a, T(1));
+        vfill<T, V>(au, T(1));
+        if (lane_on && ckm >= 0) {
+            vload(a, f.epsc + rb + (unsigned)ckm * XY);
+            if (j > 0) vload(au, f.epsc + rbu + (unsigned)ckm * XY);
+        }
+        T al = __shfl_up_sync(0xffffffffu, a[V - 1], 1);
+        if (lane == 0) al = (left_on && ckm >= 0) ? f.epsc[rbl + (unsigned)ckm * XY] : T(1);
+#pragma unroll
+        for (int e = 0; e < V; e++) {
+            pyxp[e] = au[e] + a[e];
+            pxyp[e] = (e > 0 ? a[e > 0 ? e - 1 : 0] : al) + a[e];
+        }
+    }
     T hxp[V], hyp[V];                 // Hx, Hy at layer k-1/2
     T exq[V], eyq[V], ezq[V];         // E^(n+1) of plane k-1 (Ez: layer k-1/2)
     vzero<T, V>(exq);
@@ -364,11 +408,39 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
 #pragma unroll
             for (int c = 0; c < 3; c++) {
                 P::sld(eo[c], SS(st, 3 + c, w) + col, sE);
-                sload(cb[c], SC(st, c, w) + col);
+                if (!CBF) sload(cb[c], SC(st, c, w) + col);
                 if (GEN && f.ca[c])
                     sload(ca[c], SC(st, 3 + c, w) + col);
                 else
                     vfill<T, V>(ca[c], T(1));
+            }
+            if constexpr (CBF) {
+                // cb = dt/(eps0 mean eps_r) over the edge's four cells: Ex
+                // (i, j-1..j, k-1..k), Ey (i-1..i, j, k-1..k), Ez (i-1..i,
+                // j-1..j, k); only interior edges use it (walls are zeroed)
+                T er[V], eu[V];
+                sload(er, SC(st, 0, w) + col);
+                if (w == 0)
+                    sload(eu, EU(st) + col);
+                else
+                    sload(eu, SC(st, 0, w - 1) + col);
+                T el = __shfl_up_sync(0xffffffffu, er[V - 1], 1);
+                T elu = __shfl_up_sync(0xffffffffu, eu[V - 1], 1);
+                if (lane == 0) {
+                    el = EL(st, 0)[w];
+                    elu = EL(st, 1)[w];
+                }
+#pragma unroll
+                for (int e = 0; e < V; e++) {
+                    const T erl = e > 0 ? er[e > 0 ? e - 1 : 0] : el;
+                    const T eul = e > 0 ? eu[e > 0 ? e - 1 : 0] : elu;
+                    const T pyx = eu[e] + er[e], pxy = erl + er[e];
+                    cb[0][e] = __fdividef(f.kcb, pyxp[e] + pyx);
+                    cb[1][e] = __fdividef(f.kcb, pxyp[e] + pxy);
+                    cb[2][e] = __fdividef(f.kcb, pxy + eul + eu[e]);
+                    pyxp[e] = pyx;
+                    pxyp[e] = pxy;
+                }
             }
             T zo0[V], zo1[V];
             if (pml && lane_on) {
@@ -429,15 +501,8 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
                 }
             }
         }
-        {
-            T *dx = SEx(b, w) + col;
-            T *dz = SEz(b, w) + col;
-#pragma unroll
-            for (int e = 0; e < V; e++) {
-                dx[e] = ex[e];
-                dz[e] = ez[e];
-            }
-        }
+        vstore(SEx(b, w) + col, ex);
+        vstore(SEz(b, w) + col, ez);
         if (store && own_plane) {
             P::gst(io.En[0] + q, ex, isE);
             P::gst(io.En[1] + q, ey, isE);
@@ -446,6 +511,8 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
                 P::gst(io.Zn[0] + q, zn0, isE);
                 P::gst(io.Zn[1] + q, zn1, isE);
             }
+            // non-finite check on E^(n+1) only: H^(n+3/2) is formed from it,
+            // so a non-finite H shows in E one step later
 #pragma unroll
             for (int e = 0; e < V; e++) acc += ex[e] + ey[e] + ez[e];
         }
@@ -467,10 +534,9 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
                 for (int e = 0; e < V; e++) {
                     const T eyn = e < V - 1 ? ey[e < V - 1 ? e + 1 : 0] : (lane < 31 ? eyr : T(0));
                     const T cz = (eyn - ey[e]) * idx - (exd[e] - ex[e]) * idy;
-                    T v = hz[e] - fh[e] * cz;
-                    if (NH == 2) v = v - fh[e] * cz;
+                    // NH half steps of -fh curl E with the same E: one FMA
+                    const T v = hz[e] - (T(NH) * fh[e]) * cz;
                     hn[e] = (cin[e] && !wz) ? v : T(0);
-                    acc += hn[e];
                 }
                 P::gst(io.Hn[2] + q, hn, isH);
             }
@@ -515,8 +581,7 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
                             sx[e] = (cin[e] && !xw[e]) ? hzp : T(0);
                             v = hr + hzp;
                         } else {
-                            v = hxp[e] - fhx[e] * (rest + zp);
-                            if (NH == 2) v = v - fhx[e] * (rest + zp);
+                            v = hxp[e] - (T(NH) * fhx[e]) * (rest + zp);
                         }
                         hxn[e] = (cin[e] && !xw[e]) ? v : T(0);
                     }
@@ -537,12 +602,10 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
                             sy[e] = (cin[e] && !wy) ? hzp : T(0);
                             v = hr + hzp;
                         } else {
-                            v = hyp[e] - fhy[e] * (rest + zp);
-                            if (NH == 2) v = v - fhy[e] * (rest + zp);
+                            v = hyp[e] - (T(NH) * fhy[e]) * (rest + zp);
                         }
                         hyn[e] = (cin[e] && !wy) ? v : T(0);
                     }
-                    acc += hxn[e] + hyn[e];
                 }
                 P::gst(io.Hn[0] + ql, hxn, isH);
                 P::gst(io.Hn[1] + ql, hyn, isH);

@@ -105,6 +105,18 @@ __global__ void k_e_coef(const Geo g, const double *__restrict__ eps_c, const do
     if (ca) ca[q] = (T)(-keep / den);
 }
 
+// eps_r per cell in the padded layout (cell (i, j, k) at the padded index of
+// node (i, j, k)); 1 where no cell is (the padding and the i = nx, j = ny,
+// k = nz planes), eps_c NULL meaning 1 everywhere.
+template <typename T> __global__ void k_eps_cells(const Geo g, const double *__restrict__ eps_c, T *out)
+{
+    int i, j, k;
+    if (!node_of_thread(g, i, j, k)) return;
+    const bool cell = i < g.n[0] && j < g.n[1] && k < g.n[2];
+    out[gidx(g, i, j, k)] =
+        (cell && eps_c) ? (T)eps_c[(size_t)i + (size_t)g.n[0] * ((size_t)j + (size_t)g.n[1] * k)] : T(1);
+}
+
 // H coefficient fh = dt/(2 mu0 mu_r,face) of face family d.
 template <typename T>
 __global__ void k_h_coef(const Geo g, const double *__restrict__ mu_c, int d, T *fh)
@@ -766,11 +778,6 @@ __device__ int hm_half_step(const Geo &g, const Fields<T, S> &f, const Box<T> &b
     return fr;
 }
 
-// Cooperative launch over the magnetic box: nsub = 1 runs one H/M half step
-// from f.H into Hout; nsub = 2 runs Step 3 of step n and Step 1 of step n+1
-// back to back (both use the same E^(n+1)), the second reading the first's
-// result.  Residual words: launch parity `slot` uses rows 2 slot and
-// 2 slot + 1 of res and clears the other parity's rows for the next launch.
 // Resident blocks per SM the box kernels are compiled for.  The H/M phases
 // are bound by load latency and grid barriers, so FP32 trades registers for
 // occupancy: 5 blocks of 256 threads (48 registers) against 2 at the
@@ -780,6 +787,11 @@ template <typename T> struct BoxMinBlocks {
     static constexpr int value = sizeof(T) == 4 ? 5 : 1;
 };
 
+// Cooperative launch over the magnetic box: nsub = 1 runs one H/M half step
+// from f.H into Hout; nsub = 2 runs Step 3 of step n and Step 1 of step n+1
+// back to back (both use the same E^(n+1)), the second reading the first's
+// result.  Residual words: launch parity `slot` uses rows 2 slot and
+// 2 slot + 1 of res and clears the other parity's rows for the next launch.
 template <typename T, typename S = T>
 __global__ void __launch_bounds__(256, BoxMinBlocks<T>::value) k_hm_box(const __grid_constant__ Geo g,
                                                 const __grid_constant__ Fields<T, S> f,
