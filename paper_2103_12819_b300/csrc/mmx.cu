@@ -1000,7 +1000,7 @@ static int read_status(mmx_ctx *ctx)
         CK(cudaStreamSynchronize(ctx->stream));
     }
     if (w & kErrTimeout) {
-        CK(cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned long long), ctx->stream));
+        CK(cudaMemsetAsync(ctx->bar, 0, kBarWords * sizeof(unsigned long long), ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         return fail(ctx, MMX_ERR_TIMEOUT, "a device-side wait gave up");
     }
@@ -1212,7 +1212,7 @@ static int flux_gradient_t(mmx_ctx *ctx, int kp, int nsteps, int every, double *
     rc = ensure_monitor(ctx);
     if (!rc && cudaMemsetAsync(ctx->flux_acc, 0, 4 * sizeof(double), ctx->stream) != cudaSuccess)
         rc = fail(ctx, MMX_ERR_CUDA, "memset");
-    if (!rc && cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned long long), ctx->stream) != cudaSuccess)
+    if (!rc && cudaMemsetAsync(ctx->bar, 0, kBarWords * sizeof(unsigned long long), ctx->stream) != cudaSuccess)
         rc = fail(ctx, MMX_ERR_CUDA, "memset");
     if (!rc) rc = snap_copy<T>(ctx, ck[0], true);
     if (!rc) rc = box_m_sync<T>(ctx, 1);
@@ -1409,7 +1409,7 @@ int mmx_create(const mmx_grid_desc *desc, void *cuda_stream, mmx_ctx **out)
             if (!rc) rc = dalloc(ctx, &ctx->Hzp[a], sb);
         }
     if (!rc) rc = dalloc(ctx, (void **)&ctx->res, 4 * (kMaxIter + 1) * sizeof(unsigned long long));
-    if (!rc) rc = dalloc(ctx, (void **)&ctx->bar, sizeof(unsigned long long));
+    if (!rc) rc = dalloc(ctx, (void **)&ctx->bar, kBarWords * sizeof(unsigned long long));
     if (!rc) rc = dalloc(ctx, (void **)&ctx->iterlog, kIterLogCap * sizeof(int));
     if (!rc) rc = dalloc(ctx, (void **)&ctx->halfsteps, sizeof(unsigned long long));
     if (!rc) rc = dalloc(ctx, (void **)&ctx->last_res, sizeof(double));
@@ -1724,7 +1724,7 @@ int mmx_step(mmx_ctx *ctx, int nsteps)
 {
     if (!ctx || !ctx->E[0] || nsteps < 0) return MMX_ERR_INVALID;
     if (nsteps == 0) return MMX_OK;
-    CK(cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(ctx->bar, 0, kBarWords * sizeof(unsigned long long), ctx->stream));
     bool hard = false;
     for (auto &q : ctx->src) hard |= q.kind >= 2;
     const bool fp64 = is_fp64(ctx);
@@ -2067,7 +2067,7 @@ template <typename T, typename S> static int batch_box_setup(mmx_batch *b)
     if (!rc) rc = balloc(b, (void **)&b->mag_inst, (size_t)std::max(1LL, nm) * sizeof(int));
     if (!rc) rc = balloc(b, (void **)&b->non_inst, (size_t)std::max(1LL, nn) * sizeof(int));
     if (!rc) rc = balloc(b, (void **)&b->res, 4 * (size_t)ninst * (kMaxIter + 1) * sizeof(unsigned long long));
-    if (!rc) rc = balloc(b, (void **)&b->bar, sizeof(unsigned long long));
+    if (!rc) rc = balloc(b, (void **)&b->bar, kBarWords * sizeof(unsigned long long));
     if (!rc) rc = balloc(b, (void **)&b->err, sizeof(int));
     if (rc) return rc;
     long long om = 0, on = 0;
@@ -2422,7 +2422,7 @@ int mmx_batch_step(mmx_batch *b, int nsteps)
         for (auto &s : c->src)
             if (s.kind >= 2) return bfail(b, MMX_ERR_INVALID, "an instance has a hard source");
     }
-    BCK(cudaMemsetAsync(b->bar, 0, sizeof(unsigned long long), b->stream));
+    BCK(cudaMemsetAsync(b->bar, 0, kBarWords * sizeof(unsigned long long), b->stream));
     return b->prec == MMX_FP64 ? batch_step_t<double, double>(b, nsteps)
            : b->prec == MMX_FP16 ? batch_step_t<float, __half>(b, nsteps) : batch_step_t<float, float>(b, nsteps);
 }
@@ -2436,7 +2436,7 @@ int mmx_batch_sync(mmx_batch *b)
     if (w) {
         int z = 0;
         BCK(cudaMemcpy(b->err, &z, sizeof(int), cudaMemcpyHostToDevice));
-        BCK(cudaMemset(b->bar, 0, sizeof(unsigned long long)));
+        BCK(cudaMemset(b->bar, 0, kBarWords * sizeof(unsigned long long)));
         if (w & kErrTimeout) return bfail(b, MMX_ERR_TIMEOUT, "a device-side wait gave up");
         if (w & kErrNonFinite) return bfail(b, MMX_ERR_NONFINITE, "a field became non-finite");
     }

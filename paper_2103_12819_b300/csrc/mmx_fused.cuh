@@ -435,9 +435,16 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
                     const T erl = e > 0 ? er[e > 0 ? e - 1 : 0] : el;
                     const T eul = e > 0 ? eu[e > 0 ? e - 1 : 0] : elu;
                     const T pyx = eu[e] + er[e], pxy = erl + er[e];
-                    cb[0][e] = __fdividef(f.kcb, pyxp[e] + pyx);
-                    cb[1][e] = __fdividef(f.kcb, pxyp[e] + pxy);
-                    cb[2][e] = __fdividef(f.kcb, pxy + eul + eu[e]);
+                    // one reciprocal for the three edges (Montgomery's
+                    // simultaneous inversion, 1987): t = kcb/(sx sy sz), then
+                    // kcb/sx = t sy sz and so on
+                    const T sx = pyxp[e] + pyx, sy = pxyp[e] + pxy, sz = pxy + eul + eu[e];
+                    const T sxy = sx * sy;
+                    const T t = __fdividef(f.kcb, sxy * sz);
+                    const T u = t * sz;
+                    cb[0][e] = u * sy;
+                    cb[1][e] = u * sx;
+                    cb[2][e] = t * sxy;
                     pyxp[e] = pyx;
                     pxyp[e] = pxy;
                 }
@@ -625,8 +632,14 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
     if (!isfinite(acc)) atomicOr(f.err, kErrNonFinite);
 }
 
+// Resident CTAs per SM the vectorised kernel is compiled for: two when two
+// copies of its shared memory fit in the SM's 228 KB (1 KB per CTA reserved).
+template <typename T, typename S, int BY, int ST, bool GEN> struct VecMinBlocks {
+    static constexpr int value = 2 * (VecLayout<T, S, BY, GEN, ST>::bytes + 1024) <= 228 * 1024 ? 2 : 1;
+};
+
 template <typename T, typename S, int BY, int ST, int NH, bool PMLK, bool GEN>
-__global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
+__global__ void __launch_bounds__(32 * (BY + 1), (VecMinBlocks<T, S, BY, ST, GEN>::value))
     k_fused_vec(const __grid_constant__ Geo g, const __grid_constant__ Fields<T, S> f,
                 const __grid_constant__ FusedIO<S> io, const Src<T> *__restrict__ src, int nsrc, int chunk,
                 int xstride)
@@ -649,7 +662,7 @@ template <typename T, typename S> struct VecInst {
 
 // Batched fused step: CTA b takes work[b] = {instance, bx, by, bz}.
 template <typename T, typename S, int BY, int ST, int NH, bool PMLK, bool GEN>
-__global__ void __launch_bounds__(32 * (BY + 1), ST == 2 ? 2 : 1)
+__global__ void __launch_bounds__(32 * (BY + 1), (VecMinBlocks<T, S, BY, ST, GEN>::value))
     k_fused_vec_batch(const VecInst<T, S> *__restrict__ inst, const int4 *__restrict__ work, int step)
 {
     const int4 wk = work[blockIdx.x];

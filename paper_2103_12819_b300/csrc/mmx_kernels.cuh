@@ -388,6 +388,10 @@ __global__ void k_hard(const Geo g, Ptr3<T> F, const Src<T> *__restrict__ src, i
 // value its own add returned, so no reset or generation word is needed.  The
 // wait is bounded (~2^31 cycles): on expiry the block latches kErrTimeout
 // and returns false (the other blocks then time out at the next barrier).
+// (A two-level arrival over 16 group counters measured slower: the last
+// block then makes two dependent atomic round trips.)
+constexpr int kBarWords = 1;   // u64 words a barrier needs
+
 __device__ __forceinline__ bool grid_barrier(unsigned long long *bar, int *err)
 {
     __shared__ int s_ok;
