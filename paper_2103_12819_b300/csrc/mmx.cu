@@ -973,6 +973,26 @@ template <typename T> static int copy_field_t(mmx_ctx *ctx, int id, double *host
             if (host[q] != 0.0) return fail(ctx, MMX_ERR_INVALID, "M can only be set on magnetic faces");
         return MMX_OK;
     }
+    if (boxed) {
+        // M lives on the magnetic box only (values elsewhere are ignored):
+        // move just the box region, [lo, min(lo + box, e)) per axis
+        int ce[3];
+        const int bd[3] = {ctx->bx, ctx->by, ctx->bz};
+        for (int a = 0; a < 3; a++) ce[a] = std::min(ctx->lo[a] + bd[a], e[a]) - ctx->lo[a];
+        if (ce[0] <= 0 || ce[1] <= 0 || ce[2] <= 0) return MMX_OK;
+        cudaMemcpy3DParms p = {};
+        p.srcPtr = make_cudaPitchedPtr(host, (size_t)e[0] * sizeof(double), (size_t)e[0], (size_t)e[1]);
+        p.srcPos = make_cudaPos((size_t)ctx->lo[0] * sizeof(double), (size_t)ctx->lo[1], (size_t)ctx->lo[2]);
+        p.dstPtr = make_cudaPitchedPtr(ctx->stage, (size_t)ce[0] * sizeof(double), (size_t)ce[0], (size_t)ce[1]);
+        p.extent = make_cudaExtent((size_t)ce[0] * sizeof(double), (size_t)ce[1], (size_t)ce[2]);
+        p.kind = cudaMemcpyHostToDevice;
+        CK(cudaMemcpy3DAsync(&p, ctx->stream));
+        const long long nbox = (long long)ce[0] * ce[1] * ce[2];
+        k_box_region_in<T><<<(int)((nbox + 255) / 256), 256, 0, ctx->stream>>>(b, ce[0], ce[1], ce[2], ctx->stage, dev);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(ctx->stream));
+        return MMX_OK;
+    }
     CK(cudaMemcpyAsync(ctx->stage, host, (size_t)N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     k_copy_field<T><<<blocks, 256, 0, ctx->stream>>>(ctx->g, dev, b, boxed, e[0], e[1], e[2], ctx->stage, 1);
     CK(cudaGetLastError());

@@ -291,6 +291,17 @@ __global__ void k_copy_field(const Geo g, T *dev, const Box<T> b, int boxed, int
     }
 }
 
+// Scatter a compact float64 copy of the box region [lo, lo + ce) of an M
+// component (x fastest) into its box-local array.
+template <typename T>
+__global__ void k_box_region_in(const Box<T> b, int ce0, int ce1, int ce2, const double *__restrict__ src, T *dev)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)ce0 * ce1 * ce2) return;
+    const int i = (int)(t % ce0), j = (int)((t / ce0) % ce1), k = (int)(t / ((long long)ce0 * ce1));
+    dev[(size_t)i + (size_t)b.bx * ((size_t)j + (size_t)b.by * k)] = (T)src[t];
+}
+
 // The same for an FP16-stored E/H field: value = stored * scale.
 __global__ void k_copy_field_h(const Geo g, __half *dev, float scale, int e0, int e1, int e2, double *host_like,
                                int dir)

@@ -157,6 +157,27 @@ def test_fp32_error_against_oracle_yig_slab(path):
 
 # ------------------------------------------------------- error reporting
 
+def test_m_field_round_trip():
+    """set_field / get_field of the nine M components: M is stored on the
+    magnetic box only, so a round trip returns the values set on magnetic
+    faces exactly and, elsewhere, either the value set (inside the box) or
+    zero (outside it)."""
+    w = W.yig_slab_32(steps=2, n=16)
+    sim = mmx.from_workload(w, prec=mmx.FP64)
+    rng = np.random.default_rng(12)
+    for fid in range(6, 15):
+        mag = sim.get_field(fid) != 0.0
+        assert mag.any()
+        v = rng.normal(size=sim.field_size(fid)) * 1e5
+        sim.set_field(fid, v)
+        back = sim.get_field(fid)
+        np.testing.assert_array_equal(back[mag], v[mag])
+        assert np.all((back == v) | (back == 0.0)), fid
+        sim.set_field(fid, np.where(mag, v, 0.0))
+        np.testing.assert_array_equal(sim.get_field(fid), np.where(mag, v, 0.0))
+    sim.close()
+
+
 def test_iteration_cap_is_reported():
     w = W.yig_slab_32(steps=2)
     w.max_iter = 1
