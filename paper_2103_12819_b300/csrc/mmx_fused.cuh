@@ -216,6 +216,23 @@ template <int N> __device__ __forceinline__ void cpn(void *dst, const void *src,
                      : "memory");
     }
 }
+// The same with the destination given as a 32-bit shared-memory address.
+__device__ __forceinline__ void cp16a(unsigned dst, const void *src, const void *base, bool on)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(on ? src : base),
+                 "r"(on ? 16 : 0)
+                 : "memory");
+}
+template <int N> __device__ __forceinline__ void cpna(unsigned dst, const void *src, const void *base, bool on)
+{
+    if constexpr (N == 16) {
+        cp16a(dst, src, base, on);
+    } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(dst), "l"(on ? src : base), "n"(N),
+                     "r"(on ? N : 0)
+                     : "memory");
+    }
+}
 __device__ __forceinline__ void cp_commit()
 {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -336,22 +353,30 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
         }
 
     // copies of everything plane k needs into stage st
+    // this thread's copy destinations as 32-bit shared addresses of stage 0;
+    // stage st adds st times the stage stride, a field a multiple of its slab
+    constexpr unsigned SF = R * W * sizeof(S), SST = 6 * SF;    // S fields
+    constexpr unsigned CF = R * W * sizeof(T), CST = NC * CF;   // material words
+    constexpr unsigned UF = W * sizeof(S), UST = 2 * UF;        // row y0-1
+    constexpr unsigned LFB = R * LW * sizeof(S), LST = 2 * LFB; // column x0-1
+    const unsigned sS = smem_u32(SS(0, 0, w) + col), sC = smem_u32(SC(0, 0, w) + col);
     auto issue = [&](int k, int st) {
         const int ck = cell_nb(g, 2, k);
         const unsigned kn = (unsigned)k * XY, kc = (unsigned)max(ck, 0) * XY;
         const bool lay = ck >= 0;
-        cpn<VB>(SS(st, 0, w) + col, io.Ho[0] + rb + kc, io.Ho[0], lane_on && lay);
-        cpn<VB>(SS(st, 1, w) + col, io.Ho[1] + rb + kc, io.Ho[1], lane_on && lay);
-        cpn<VB>(SS(st, 2, w) + col, io.Ho[2] + rb + kn, io.Ho[2], lane_on);
+        const unsigned s0 = sS + (unsigned)st * SST, c0 = sC + (unsigned)st * CST;
+        cpna<VB>(s0, io.Ho[0] + rb + kc, io.Ho[0], lane_on && lay);
+        cpna<VB>(s0 + SF, io.Ho[1] + rb + kc, io.Ho[1], lane_on && lay);
+        cpna<VB>(s0 + 2 * SF, io.Ho[2] + rb + kn, io.Ho[2], lane_on);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            cpn<VB>(SS(st, 3 + c, w) + col, io.Eo[c] + rb + kn, io.Eo[c], lane_on);
-            if (!CBF) cp16(SC(st, c, w) + col, f.cb[c] + rb + kn, f.cb[c], lane_on);
-            if (GEN && f.ca[c]) cp16(SC(st, 3 + c, w) + col, f.ca[c] + rb + kn, f.ca[c], lane_on);
+            cpna<VB>(s0 + (3 + c) * SF, io.Eo[c] + rb + kn, io.Eo[c], lane_on);
+            if (!CBF) cp16a(c0 + c * CF, f.cb[c] + rb + kn, f.cb[c], lane_on);
+            if (GEN && f.ca[c]) cp16a(c0 + (3 + c) * CF, f.ca[c] + rb + kn, f.ca[c], lane_on);
         }
         if constexpr (CBF) {
             // eps_r of cell plane k: this row, the row below, and column x0-1
-            cp16(SC(st, 0, w) + col, f.epsc + rb + kc, f.epsc, lane_on && lay);
+            cp16a(c0, f.epsc + rb + kc, f.epsc, lane_on && lay);
             if (w == 0) cp16(EU(st) + col, f.epsc + rbu + kc, f.epsc, up_on && lay);
             if (lane == 0) {
                 cpn<4>(EL(st, 0) + w, f.epsc + rbl + kc, f.epsc, left_on && lay);
@@ -359,15 +384,17 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
             }
         }
         if (w == 0) {
-            cpn<VB>(U(st, 0) + col, io.Ho[0] + rbu + kc, io.Ho[0], up_on && lay);
-            cpn<VB>(U(st, 1) + col, io.Ho[2] + rbu + kn, io.Ho[2], up_on);
+            const unsigned u0 = smem_u32(U(0, 0) + col) + (unsigned)st * UST;
+            cpna<VB>(u0, io.Ho[0] + rbu + kc, io.Ho[0], up_on && lay);
+            cpna<VB>(u0 + UF, io.Ho[2] + rbu + kn, io.Ho[2], up_on);
         }
         if (lane == 0) {
             // the LW-element group ending at column x0-1 (one element unless
             // the element is narrower than the 4-byte minimum copy)
             constexpr int CB = LW * (int)sizeof(S);
-            cpn<CB>(Lf(st, 0) + w * LW, io.Ho[1] + rbl + kc - (LW - 1), io.Ho[1], left_on && lay);
-            cpn<CB>(Lf(st, 1) + w * LW, io.Ho[2] + rbl + kn - (LW - 1), io.Ho[2], left_on);
+            const unsigned l0 = smem_u32(Lf(0, 0) + w * LW) + (unsigned)st * LST;
+            cpna<CB>(l0, io.Ho[1] + rbl + kc - (LW - 1), io.Ho[1], left_on && lay);
+            cpna<CB>(l0 + LFB, io.Ho[2] + rbl + kn - (LW - 1), io.Ho[2], left_on);
         }
         cp_commit();
     };

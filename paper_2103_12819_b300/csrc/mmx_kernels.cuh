@@ -491,7 +491,13 @@ __device__ __forceinline__ void h_vector(const Geo &g, const Box<T> &b, SG *cons
                                          int mode, int i, int j, int k, T h[3], T sH = T(1))
 {
     const int ix[3] = {i, j, k};
-    h[D] = mode == 0 ? ld_s(Hg[D] + gidx32(g, i, j, k), sH) : Hb[D][bidx32(b.lo, b.bx, b.by, i, j, k)];
+    // the face's index and the strides of the layout read: every neighbour
+    // is the face's index plus its offsets times the strides (a periodic wrap
+    // along D is an offset of n - 1 cells; unsigned arithmetic is modular)
+    const unsigned base = mode == 0 ? gidx32(g, i, j, k) : bidx32(b.lo, b.bx, b.by, i, j, k);
+    const unsigned s1 = mode == 0 ? (unsigned)g.X : (unsigned)b.bx;
+    const unsigned st[3] = {1u, s1, s1 * (mode == 0 ? (unsigned)g.Y : (unsigned)b.by)};
+    h[D] = mode == 0 ? ld_s(Hg[D] + base, sH) : Hb[D][base];
 #pragma unroll
     for (int t = 0; t < 3; t++) {
         if (t == D) continue;
@@ -501,13 +507,11 @@ __device__ __forceinline__ void h_vector(const Geo &g, const Box<T> &b, SG *cons
         for (int od = -1; od <= 0; od++) {
             int nd = cell_nb(g, D, ix[D] + od);
             if (nd < 0) continue;
+            const unsigned qd = base + (unsigned)(nd - ix[D]) * st[D];
 #pragma unroll
             for (int ot = 0; ot <= 1; ot++) {
-                int q[3] = {ix[0], ix[1], ix[2]};
-                q[D] = nd;
-                q[t] = ix[t] + ot;
-                sum += mode == 0 ? ld_s(Hg[t] + gidx32(g, q[0], q[1], q[2]), sH)
-                                 : Hb[t][bidx32(b.lo, b.bx, b.by, q[0], q[1], q[2])];
+                const unsigned q = qd + (unsigned)ot * st[t];
+                sum += mode == 0 ? ld_s(Hg[t] + q, sH) : Hb[t][q];
                 cnt++;
             }
         }
