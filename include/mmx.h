@@ -148,7 +148,11 @@ MMX_API int mmx_set_M_cells(mmx_ctx *ctx, const double *mx, const double *my, co
 
 /* Copy a Yee-located field (ids above) from a host float64 array of exactly
  * n elements (its extent).  On periodic axes node index n is set equal to
- * node index 0.  FP32 contexts round to nearest. */
+ * node index 0.  FP32 contexts round to nearest.  M (ids 6-14) is stored on
+ * the magnetic box only (the bounding box of the magnetic faces grown by one
+ * face): only that region of the host array is read and moved, values
+ * outside it are ignored and read back as zero; without magnetic material
+ * every M value must be zero. */
 MMX_API int mmx_set_field(mmx_ctx *ctx, int field_id, const double *host, long long n);
 
 /* Copy a Yee-located field to a host float64 array of exactly n elements.
