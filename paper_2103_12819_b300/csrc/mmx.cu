@@ -60,6 +60,12 @@ struct mmx_ctx {
     dim3 vec_grid;
     int vec_xstride = 0;
     bool walls_dirty = false;
+    // bulk-tensor (TMA) staging of the vectorised kernel: -1 not planned,
+    // 0 not used, 1 used; one map set per E/H ping-pong parity, keyed by the
+    // H array it reads
+    int vec_tma = -1;
+    VecMaps vmaps[2];
+    void *vmap_key[2] = {};
     // coefficients
     void *ca[3] = {}, *cb[3] = {}, *fh[3] = {};
     void *epsc = nullptr;                  // FP32 arithmetic: eps_r per cell, padded
@@ -741,6 +747,61 @@ template <typename T, typename S> static cudaError_t set_vec_smem()
     return e;
 }
 
+#ifndef MMX_VEC_TMA
+#define MMX_VEC_TMA 1
+#endif
+
+template <typename T, typename S, int NH, bool PMLK> static cudaError_t set_vec_tma_smem_v()
+{
+    constexpr int BY = VecRows<T>::value, ST = VecStages<T, false>::value;
+    constexpr size_t b = VecLayout<T, S, BY, false, ST, true>::bytes;
+    static_assert(b <= 227 * 1024, "TMA variant shared memory above the per-CTA limit");
+    return cudaFuncSetAttribute(k_fused_vec_tma<T, S, BY, ST, NH, PMLK, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+}
+
+// Tensor maps for the TMA variant (FP32 storage, no sigma or mu_r): the
+// padded arrays as (X, Y, nz+1) float tensors, boxes of one plane of W
+// columns by BY+2 rows (H, eps_r) or BY+1 rows (E).  Returns false (and the
+// vectorised kernel keeps its cp.async staging) if the driver entry point
+// or an encoding is unavailable.
+static bool encode_vec_maps(mmx_ctx *ctx)
+{
+    using Enc = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                             const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return false;
+    Enc enc = (Enc)fn;
+    constexpr int BY = VecRows<float>::value, W = 32 * Lanes<float>::V;
+    const cuuint64_t dim[3] = {(cuuint64_t)ctx->g.X, (cuuint64_t)ctx->g.Y, (cuuint64_t)ctx->desc.n[2] + 1};
+    const cuuint64_t str[2] = {(cuuint64_t)ctx->g.X * 4, (cuuint64_t)ctx->g.X * ctx->g.Y * 4};
+    const cuuint32_t boxh[3] = {(cuuint32_t)W, (cuuint32_t)(BY + 2), 1}, boxe[3] = {(cuuint32_t)W, (cuuint32_t)(BY + 1), 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    auto one = [&](CUtensorMap *m, void *p, const cuuint32_t *box) {
+        return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p, dim, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    for (int p = 0; p < 2; p++) {
+        void *const *Eb = p == 0 ? ctx->E : ctx->Ealt, *const *Hb = p == 0 ? ctx->H : ctx->Halt;
+        VecMaps &m = ctx->vmaps[p];
+        bool ok = true;
+        for (int a = 0; a < 3; a++) {
+            ok = ok && one(&m.h[a], Hb[a], boxh);
+            ok = ok && one(&m.e[a], Eb[a], boxe);
+        }
+        ok = ok && one(&m.eps, ctx->epsc, boxh);
+        if (!ok) return false;
+        ctx->vmap_key[p] = Hb[0];
+    }
+    return true;
+}
+
 template <typename T, typename S> static int plan_vec(mmx_ctx *ctx)
 {
     constexpr int W = 32 * Lanes<T>::V;
@@ -765,6 +826,22 @@ template <typename T, typename S> static int plan_vec(mmx_ctx *ctx)
     ctx->vec_chunk = chunk;
     ctx->vec_xstride = xs;
     ctx->vec_grid = dim3(ntx, nty, (n[2] + chunk - 1) / chunk);
+    ctx->vec_tma = 0;
+    if constexpr (std::is_same<T, float>::value && std::is_same<S, float>::value) {
+        if (MMX_VEC_TMA && !(ctx->any_sigma || ctx->any_mu) && ctx->epsc && encode_vec_maps(ctx)) {
+            cudaError_t r[4] = {set_vec_tma_smem_v<T, S, 1, false>(), set_vec_tma_smem_v<T, S, 1, true>(),
+                                set_vec_tma_smem_v<T, S, 2, false>(), set_vec_tma_smem_v<T, S, 2, true>()};
+            bool ok = true;
+            for (cudaError_t x : r) ok = ok && x == cudaSuccess;
+            int pt = 0;
+            if (ok && cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                          &pt, k_fused_vec_tma<T, S, BY, ST, 2, true, false>, 32 * (BY + 1),
+                          VecLayout<T, S, BY, false, ST, true>::bytes) == cudaSuccess &&
+                pt >= per)
+                ctx->vec_tma = 1;
+            cudaGetLastError();
+        }
+    }
     return MMX_OK;
 }
 
@@ -800,6 +877,16 @@ template <typename T, typename S, int NH, bool PMLK, bool GEN>
 static void launch_vec_v(mmx_ctx *ctx, const Fields<T, S> &f, const FusedIO<S> &io, int nsrc)
 {
     constexpr int BY = VecRows<T>::value, ST = VecStages<T, GEN>::value;
+    if constexpr (std::is_same<T, float>::value && std::is_same<S, float>::value && !GEN) {
+        if (ctx->vec_tma == 1) {
+            // the map set of the buffers this step reads
+            const int p = (void *)io.Ho[0] == ctx->vmap_key[0] ? 0 : 1;
+            k_fused_vec_tma<T, S, BY, ST, NH, PMLK, GEN>
+                <<<ctx->vec_grid, dim3(32, BY + 1), VecLayout<T, S, BY, GEN, ST, true>::bytes, ctx->stream>>>(
+                    ctx->g, f, io, ctx->vmaps[p], (const Src<T> *)ctx->dsrc, nsrc, ctx->vec_chunk, ctx->vec_xstride);
+            return;
+        }
+    }
     k_fused_vec<T, S, BY, ST, NH, PMLK, GEN><<<ctx->vec_grid, dim3(32, BY + 1), vec_smem_bytes<T, S, GEN>(),
                                                ctx->stream>>>(
         ctx->g, f, io, (const Src<T> *)ctx->dsrc, nsrc, ctx->vec_chunk, ctx->vec_xstride);

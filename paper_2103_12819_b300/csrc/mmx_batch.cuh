@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(256, BoxMinBlocks<T>::value)
                    const int *__restrict__ non_inst, int nnon, unsigned long long *res, unsigned long long *bar,
                    int *berr, int nsub, int slot)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     BatchShared sh;
     sh.res = reinterpret_cast<unsigned long long *>(smem_raw);
     sh.done = reinterpret_cast<int *>(sh.res + ninst);

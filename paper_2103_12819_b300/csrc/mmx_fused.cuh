@@ -23,6 +23,7 @@
 // y = 0 and every component at z walls are written as zero; the wall column
 // x = nx and wall row y = ny are never written (the host keeps them zero).
 #pragma once
+#include <cuda.h>
 #include <type_traits>
 
 #include "mmx_kernels.cuh"
@@ -233,6 +234,46 @@ template <int N> __device__ __forceinline__ void cpna(unsigned dst, const void *
                      : "memory");
     }
 }
+// Tensor maps of the planes the TMA variant stages: the three H and three E
+// arrays it reads and the cell eps_r array, each a 3-D (x, y, z) view of the
+// padded layout whose box is one plane of the CTA's rows (H and eps_r from
+// row y0-1, E from row y0).
+struct VecMaps {
+    CUtensorMap h[3];
+    CUtensorMap e[3];
+    CUtensorMap eps;
+};
+
+// mbarrier and bulk tensor copy primitives (PTX), shared addresses 32-bit.
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// One box of a 3-D tensor map at (x, y, z) into shared memory at dst; the
+// copy's bytes complete on the mbarrier bar.  Coordinates outside the tensor
+// read zero (x is always a multiple of 16 bytes here).
+__device__ __forceinline__ void tma_load3(unsigned dst, const CUtensorMap *map, int x, int y, int z, unsigned bar)
+{
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+                 "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+                 : "memory");
+}
+
 __device__ __forceinline__ void cp_commit()
 {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -255,10 +296,13 @@ template <int N> __device__ __forceinline__ void cp_wait()
 //   left [ST][2][R][LW] of S  Hy, Hz of column x0-1 (FP16: the 4-byte pair
 //                           ending there), one entry per row
 //   sEx, sEz [2][R][W] of T E^(n+1) exchanged between rows
-template <typename T, typename S, int BY, bool GEN, int ST> struct VecLayout {
+template <typename T, typename S, int BY, bool GEN, int ST, bool TMA = false> struct VecLayout {
     static constexpr int V = Lanes<T>::V;
     static constexpr int W = 32 * V;
     static constexpr int R = BY + 1;
+    // rows per staged slab: the TMA variant also stages row y0-1 (row 0)
+    static constexpr int RR = TMA ? R + 1 : R;
+    static constexpr int OFF = TMA ? 1 : 0;   // slab row of row y0
     // FP32 arithmetic without sigma or mu_r: cb is formed from staged cell
     // eps_r (one value per cell instead of three per-edge coefficients)
     // (FP32 storage; with FP16 storage the kernel is bound by instruction
@@ -266,36 +310,42 @@ template <typename T, typename S, int BY, bool GEN, int ST> struct VecLayout {
     static constexpr bool CBF = !GEN && sizeof(T) == 4 && sizeof(S) == 4;
     static constexpr int NC = GEN ? 6 : (CBF ? 1 : 3);
     static constexpr int LW = sizeof(S) >= 4 ? 1 : 4 / (int)sizeof(S);
-    static constexpr size_t al(size_t x) { return (x + 15) / 16 * 16; }
+    // regions start on 128-byte boundaries where bulk tensor copies land
+    static constexpr size_t al(size_t x) { return TMA ? (x + 127) / 128 * 128 : (x + 15) / 16 * 16; }
     static constexpr size_t sst = 0;
-    static constexpr size_t cst = sst + al((size_t)ST * 6 * R * W * sizeof(S));
-    static constexpr size_t up = cst + al((size_t)ST * NC * R * W * sizeof(T));
-    static constexpr size_t left = up + al((size_t)ST * 2 * W * sizeof(S));
+    static constexpr size_t cst = sst + al((size_t)ST * 6 * RR * W * sizeof(S));
+    static constexpr size_t up = cst + al((size_t)ST * NC * RR * W * sizeof(T));
+    static constexpr size_t left = up + (TMA ? 0 : al((size_t)ST * 2 * W * sizeof(S)));
     static constexpr size_t ex = left + al((size_t)ST * 2 * R * LW * sizeof(S));
     static constexpr size_t ez = ex + al((size_t)2 * R * W * sizeof(T));
     static constexpr size_t eu = ez + al((size_t)2 * R * W * sizeof(T));
-    static constexpr size_t el = eu + (CBF ? al((size_t)ST * W * sizeof(T)) : 0);
-    static constexpr size_t bytes = el + (CBF ? al((size_t)ST * 2 * R * sizeof(T)) : 0);
+    static constexpr size_t el = eu + (CBF && !TMA ? al((size_t)ST * W * sizeof(T)) : 0);
+    static constexpr size_t mb = el + (CBF ? al((size_t)ST * 2 * R * sizeof(T)) : 0);
+    static constexpr size_t bytes = mb + (TMA ? al((size_t)ST * 8) : 0);
+    // bytes one stage's bulk copies deliver (H 3 and eps_r with RR rows, E 3 with R)
+    static constexpr unsigned tx = (unsigned)((3 * RR + 3 * R) * W * sizeof(S) + (CBF ? RR * W * sizeof(T) : 0));
 };
 
 // The kernel body for the CTA at tile (bx, by, bz) of one grid: the single
 // grid launch passes its block index, the batched launch the entry of its
 // work table; amp holds this step's source amplitudes.
-template <typename T, typename S, int BY, int ST, int NH, bool PMLK, bool GEN>
+template <typename T, typename S, int BY, int ST, int NH, bool PMLK, bool GEN, bool TMA = false>
 __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> &f, const FusedIO<S> &io,
                                                const Src<T> *__restrict__ src, int nsrc, const T *amp,
-                                               int chunk, int xstride, int bx, int by, int bz)
+                                               int chunk, int xstride, int bx, int by, int bz,
+                                               const VecMaps *maps = nullptr)
 {
-    using L = VecLayout<T, S, BY, GEN, ST>;
+    using L = VecLayout<T, S, BY, GEN, ST, TMA>;
     using P = SV<S>;
-    constexpr int V = L::V, W = L::W, R = L::R, NC = L::NC, LW = L::LW;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    // S-typed stage fields 0-5: Hx Hy Hz Ex Ey Ez; T-typed 0-5: cb, ca
+    constexpr int V = L::V, W = L::W, R = L::R, NC = L::NC, LW = L::LW, RR = L::RR, OFF = L::OFF;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // S-typed stage fields 0-5: Hx Hy Hz Ex Ey Ez; T-typed 0-5: cb, ca (or
+    // eps_r); row r of the CTA (r = -1 the row below y0 in the TMA variant)
     auto SS = [&](int st, int fld, int row) -> S * {
-        return reinterpret_cast<S *>(smem_raw + L::sst) + ((st * 6 + fld) * R + row) * W;
+        return reinterpret_cast<S *>(smem_raw + L::sst) + ((st * 6 + fld) * RR + row + OFF) * W;
     };
     auto SC = [&](int st, int fld, int row) -> T * {
-        return reinterpret_cast<T *>(smem_raw + L::cst) + ((st * NC + fld) * R + row) * W;
+        return reinterpret_cast<T *>(smem_raw + L::cst) + ((st * NC + fld) * RR + row + OFF) * W;
     };
     auto U = [&](int st, int fld) -> S * { return reinterpret_cast<S *>(smem_raw + L::up) + (st * 2 + fld) * W; };
     auto Lf = [&](int st, int fld) -> S * {
@@ -355,15 +405,57 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
     // copies of everything plane k needs into stage st
     // this thread's copy destinations as 32-bit shared addresses of stage 0;
     // stage st adds st times the stage stride, a field a multiple of its slab
-    constexpr unsigned SF = R * W * sizeof(S), SST = 6 * SF;    // S fields
-    constexpr unsigned CF = R * W * sizeof(T), CST = NC * CF;   // material words
+    constexpr unsigned SF = RR * W * sizeof(S), SST = 6 * SF;   // S fields
+    constexpr unsigned CF = RR * W * sizeof(T), CST = NC * CF;  // material words
     constexpr unsigned UF = W * sizeof(S), UST = 2 * UF;        // row y0-1
     constexpr unsigned LFB = R * LW * sizeof(S), LST = 2 * LFB; // column x0-1
     const unsigned sS = smem_u32(SS(0, 0, w) + col), sC = smem_u32(SC(0, 0, w) + col);
+    // TMA variant: one mbarrier per stage, armed by thread (0, 0) with the
+    // stage's byte count; every thread waits on its phase
+    const unsigned mbar0 = TMA ? smem_u32(smem_raw + L::mb) : 0u;
+    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    if constexpr (TMA) {
+        if (leader) {
+#pragma unroll
+            for (int q = 0; q < ST; q++) mbar_init(mbar0 + 8 * q, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    }
     auto issue = [&](int k, int st) {
         const int ck = cell_nb(g, 2, k);
         const unsigned kn = (unsigned)k * XY, kc = (unsigned)max(ck, 0) * XY;
         const bool lay = ck >= 0;
+        if constexpr (TMA) {
+            if (leader) {
+                // planes of H (rows y0-1 .. y0+BY; cell plane ck or node k),
+                // E (rows y0 .. y0+BY, node k) and eps_r (cell plane ck); a
+                // missing cell plane (ck < 0) is read as zero
+                const unsigned bar = mbar0 + 8 * st;
+                const unsigned s0 = smem_u32(smem_raw + L::sst) + (unsigned)st * SST;
+                const unsigned c0 = smem_u32(smem_raw + L::cst) + (unsigned)st * CST;
+                const int yh = by * BY - 1, ye = by * BY, zc = ck;
+                mbar_expect_tx(bar, L::tx);
+                tma_load3(s0, &maps->h[0], x0, yh, zc, bar);
+                tma_load3(s0 + SF, &maps->h[1], x0, yh, zc, bar);
+                tma_load3(s0 + 2 * SF, &maps->h[2], x0, yh, k, bar);
+#pragma unroll
+                for (int c = 0; c < 3; c++) tma_load3(s0 + (3 + c) * SF + W * sizeof(S), &maps->e[c], x0, ye, k, bar);
+                if constexpr (CBF) tma_load3(c0, &maps->eps, x0, yh, zc, bar);
+            }
+            if (lane == 0) {
+                constexpr int CB = LW * (int)sizeof(S);
+                const unsigned l0 = smem_u32(Lf(0, 0) + w * LW) + (unsigned)st * LST;
+                cpna<CB>(l0, io.Ho[1] + rbl + kc - (LW - 1), io.Ho[1], left_on && lay);
+                cpna<CB>(l0 + LFB, io.Ho[2] + rbl + kn - (LW - 1), io.Ho[2], left_on);
+                if constexpr (CBF) {
+                    cpn<4>(EL(st, 0) + w, f.epsc + rbl + kc, f.epsc, left_on && lay);
+                    cpn<4>(EL(st, 1) + w, f.epsc + rbl - (unsigned)g.X + kc, f.epsc, left_on && j > 0 && lay);
+                }
+            }
+            cp_commit();
+            return;
+        }
         const unsigned s0 = sS + (unsigned)st * SST, c0 = sC + (unsigned)st * CST;
         cpna<VB>(s0, io.Ho[0] + rb + kc, io.Ho[0], lane_on && lay);
         cpna<VB>(s0 + SF, io.Ho[1] + rb + kc, io.Ho[1], lane_on && lay);
@@ -446,8 +538,23 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
             cp_commit();
     }
     T acc = T(0);
+    bool tma_bad = false;
     int b = 0, st = 0;
     for (int k = k0; k <= k1; k++, b ^= 1, st = st + 1 == ST ? 0 : st + 1) {
+        if constexpr (TMA) {
+            // bounded wait for plane k's bulk copies (stage st, use (k-k0)/ST)
+            if (!tma_bad) {
+                const unsigned par = (unsigned)((k - k0) / ST) & 1u;
+                const long long t0 = clock64();
+                while (!mbar_try_wait(mbar0 + 8 * st, par)) {
+                    if (clock64() - t0 > (1LL << 31)) {
+                        tma_bad = true;
+                        atomicOr(f.err, kErrTimeout);
+                        break;
+                    }
+                }
+            }
+        }
         cp_wait<ST - 2>();
         __syncthreads();          // plane k staged; every thread is done with plane k-1
         {
@@ -463,7 +570,7 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
         P::sld(hx, SS(st, 0, w) + col, sH);
         P::sld(hy, SS(st, 1, w) + col, sH);
         P::sld(hz, SS(st, 2, w) + col, sH);
-        if (w == 0) {
+        if (w == 0 && !TMA) {
             P::sld(hxu, U(st, 0) + col, sH);
             P::sld(hzu, U(st, 1) + col, sH);
         } else {
@@ -501,7 +608,7 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
                 // j-1..j, k); only interior edges use it (walls are zeroed)
                 T er[V], eu[V];
                 sload(er, SC(st, 0, w) + col);
-                if (w == 0)
+                if (w == 0 && !TMA)
                     sload(eu, EU(st) + col);
                 else
                     sload(eu, SC(st, 0, w - 1) + col);
@@ -816,8 +923,8 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
 
 // Resident CTAs per SM the vectorised kernel is compiled for: two when two
 // copies of its shared memory fit in the SM's 228 KB (1 KB per CTA reserved).
-template <typename T, typename S, int BY, int ST, bool GEN> struct VecMinBlocks {
-    static constexpr int value = 2 * (VecLayout<T, S, BY, GEN, ST>::bytes + 1024) <= 228 * 1024 ? 2 : 1;
+template <typename T, typename S, int BY, int ST, bool GEN, bool TMA = false> struct VecMinBlocks {
+    static constexpr int value = 2 * (VecLayout<T, S, BY, GEN, ST, TMA>::bytes + 1024) <= 228 * 1024 ? 2 : 1;
 };
 
 template <typename T, typename S, int BY, int ST, int NH, bool PMLK, bool GEN>
@@ -828,6 +935,20 @@ __global__ void __launch_bounds__(32 * (BY + 1), (VecMinBlocks<T, S, BY, ST, GEN
 {
     fused_vec_body<T, S, BY, ST, NH, PMLK, GEN>(g, f, io, src, nsrc, f.src_amp, chunk, xstride, blockIdx.x,
                                                 blockIdx.y, blockIdx.z);
+}
+
+// The same pass with the planes staged by bulk tensor copies (TMA): one
+// thread per CTA issues each plane's tiles against a per-stage mbarrier, so
+// the other threads spend no instructions on copy addresses.  FP32 storage
+// without sigma or mu_r; maps are the tensor maps of the buffers read.
+template <typename T, typename S, int BY, int ST, int NH, bool PMLK, bool GEN>
+__global__ void __launch_bounds__(32 * (BY + 1), (VecMinBlocks<T, S, BY, ST, GEN, true>::value))
+    k_fused_vec_tma(const __grid_constant__ Geo g, const __grid_constant__ Fields<T, S> f,
+                    const __grid_constant__ FusedIO<S> io, const __grid_constant__ VecMaps maps,
+                    const Src<T> *__restrict__ src, int nsrc, int chunk, int xstride)
+{
+    fused_vec_body<T, S, BY, ST, NH, PMLK, GEN, true>(g, f, io, src, nsrc, f.src_amp, chunk, xstride, blockIdx.x,
+                                                      blockIdx.y, blockIdx.z, &maps);
 }
 
 // One grid of a batch: what the batched fused launch needs per instance, for
