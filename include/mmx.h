@@ -191,6 +191,16 @@ MMX_API int mmx_sync(mmx_ctx *ctx);
 /* Statistics since creation; synchronises. */
 MMX_API int mmx_get_stats(mmx_ctx *ctx, mmx_stats *out);
 
+/* Check of the bounded device waits (failure detection without a fault):
+ * launches a two-block grid barrier, the same wait the H/M kernels use, in
+ * which one block leaves without arriving.  The other block gives up after
+ * its wait budget (about 2^31 clock cycles, one second at the B300's clock),
+ * latches the timeout and returns.  Returns MMX_ERR_TIMEOUT when the wait
+ * gave up as designed (any other code means it did not); the barrier and
+ * error words are then reset, so the context stays usable.  Synchronises;
+ * a status pending from earlier work is returned first, without the check. */
+MMX_API int mmx_check_bounded_wait(mmx_ctx *ctx);
+
 /* Iteration count of each H/M half step, oldest first (up to cap entries of
  * the most recent 65536 half steps).  Returns the number written (>= 0) or a
  * negative error.  Synchronises. */

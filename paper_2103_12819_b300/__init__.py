@@ -49,7 +49,7 @@ class KernelProfile(ctypes.Structure):
 
 EXPORTS = ("mmx_create", "mmx_set_materials", "mmx_set_bias", "mmx_set_M_cells", "mmx_set_field",
            "mmx_get_field", "mmx_get_material", "mmx_add_source", "mmx_set_path", "mmx_step",
-           "mmx_sync", "mmx_get_stats", "mmx_get_iter_log", "mmx_get_field_device",
+           "mmx_sync", "mmx_get_stats", "mmx_get_iter_log", "mmx_get_field_device", "mmx_check_bounded_wait",
            "mmx_flux_gradient", "mmx_set_storage_scale", "mmx_add_probe", "mmx_get_probes", "mmx_energy", "mmx_add_flux_plane", "mmx_get_flux",
            "mmx_set_profiling", "mmx_get_profile",
            "mmx_batch_create", "mmx_batch_set_planes", "mmx_batch_step", "mmx_batch_sync",
@@ -99,6 +99,8 @@ def lib():
     L.mmx_get_field_device.argtypes = [P, I, ctypes.POINTER(P), ctypes.POINTER(LL), ctypes.POINTER(LL)]
     L.mmx_set_profiling.restype = I
     L.mmx_set_profiling.argtypes = [P, I]
+    L.mmx_check_bounded_wait.restype = I
+    L.mmx_check_bounded_wait.argtypes = [P]
     L.mmx_flux_gradient.restype = I
     L.mmx_flux_gradient.argtypes = [P, I, I, I, dp, dp, dp]
     L.mmx_set_storage_scale.restype = I
@@ -268,6 +270,11 @@ class Solver:
         if check:
             self._check(rc, "mmx_sync")
         return rc
+
+    def check_bounded_wait(self):
+        """Run the device-wait check (mmx_check_bounded_wait); returns its code,
+        -6 (TIMEOUT) when the bounded wait gave up as designed."""
+        return self._L.mmx_check_bounded_wait(self._h)
 
     def get_stats(self):
         s = Stats()

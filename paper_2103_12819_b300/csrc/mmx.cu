@@ -1449,6 +1449,15 @@ static int flux_gradient_t(mmx_ctx *ctx, int kp, int nsteps, int every, double *
     return rc ? rc : read_status(ctx);
 }
 
+// Failure-detection probe: two blocks meet at a grid barrier and block
+// `absent` returns without arriving, so the other one waits out the bounded
+// wait and latches kErrTimeout (nothing faults, nothing hangs).
+__global__ void k_barrier_probe(unsigned long long *bar, int *err, int absent)
+{
+    if ((int)blockIdx.x == absent) return;
+    grid_barrier(bar, err);
+}
+
 extern "C" {
 
 int mmx_create(const mmx_grid_desc *desc, void *cuda_stream, mmx_ctx **out)
@@ -1857,6 +1866,17 @@ int mmx_sync(mmx_ctx *ctx)
 {
     if (!ctx || !ctx->E[0]) return MMX_ERR_INVALID;
     CK(cudaStreamSynchronize(ctx->stream));
+    return read_status(ctx);
+}
+
+int mmx_check_bounded_wait(mmx_ctx *ctx)
+{
+    if (!ctx || !ctx->E[0]) return MMX_ERR_INVALID;
+    int rc = read_status(ctx);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(ctx->bar, 0, kBarWords * sizeof(unsigned long long), ctx->stream));
+    k_barrier_probe<<<2, 32, 0, ctx->stream>>>(ctx->bar, ctx->errw, 1);
+    CK(cudaGetLastError());
     return read_status(ctx);
 }
 

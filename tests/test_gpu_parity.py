@@ -157,6 +157,26 @@ def test_fp32_error_against_oracle_yig_slab(path):
 
 # ------------------------------------------------------- error reporting
 
+def test_bounded_wait_gives_up_and_context_stays_usable():
+    """Failure detection without a fault: a grid barrier that one block never
+    reaches gives up after its wait budget (about a second), the host reads
+    MMX_ERR_TIMEOUT, and the same context then steps and matches the oracle."""
+    import time
+    w = W.yig_slab_32(steps=4, n=16)
+    sim = mmx.from_workload(w, prec=mmx.FP64)
+    t0 = time.perf_counter()
+    assert sim.check_bounded_wait() == -6
+    assert time.perf_counter() - t0 < 30
+    assert sim.check_bounded_wait() == -6            # repeatable
+    sim.step(4)
+    assert sim.sync(check=False) == 0
+    ref = oracle.from_workload(w)
+    ref.step(4)
+    _compare(sim, ref, label="after the wait check")
+    ref.close()
+    sim.close()
+
+
 def test_m_field_round_trip():
     """set_field / get_field of the nine M components: M is stored on the
     magnetic box only, so a round trip returns the values set on magnetic
