@@ -270,6 +270,26 @@ def test_vectorised_fused_equals_plain(prec, n):
     np.testing.assert_array_equal(a.get_iter_log(), b.get_iter_log())
 
 
+@pytest.mark.parametrize("bcz,n", [(W.PERIODIC, (140, 9, 12)), (W.PEC, (37, 11, 10))], ids=["periodic-z", "pec-z"])
+def test_bulk_copy_staging_equals_plain_fp32(bcz, n):
+    """FP32 storage without sigma or mu_r stages the fused kernel's planes with
+    bulk tensor copies: on a periodic z axis (the staged cell plane wraps, node
+    nz repeats node 0) over two strips, and on a ragged PEC box, it matches the
+    per-update kernels to FP32 rounding."""
+    w = W.random_small(31, n=n, bc=(W.PEC, W.PEC, bcz), tol=1e-6)
+    w.sigma = np.zeros_like(w.sigma)
+    w.mu_r = np.ones_like(w.mu_r)
+    w.sources = [q for q in w.sources if q.kind < 2]
+    a = mmx.from_workload(w, prec=mmx.FP32, path=mmx.PATH_PLAIN)
+    b = mmx.from_workload(w, prec=mmx.FP32, path=mmx.PATH_FUSED)
+    a.step(6)
+    prof = _kernels_seen(b, 6)
+    assert "fused_eh_vec" in prof, prof
+    assert a.sync(check=False) == 0 and b.sync(check=False) == 0
+    for fid in range(15):
+        assert _rel_to_scale(b, a, fid) <= 1e-5, fid
+
+
 def test_vectorised_fused_after_set_field_keeps_walls():
     """Nonzero values written onto the x = nx / y = ny PEC walls by set_field
     are cleared before the vectorised kernel runs, as the per-update path
