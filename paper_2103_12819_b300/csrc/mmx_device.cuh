@@ -132,7 +132,7 @@ template <typename T> struct Box {
     T *Hit[2][3];       // H iterates (box layout; neighbours read them)
     T *Hit2[2][3];      // H iterates of the second half step of a launch
     // per magnetic face, in the order of the magnetic-face list:
-    const Q4<T> *cst;   // Ms, k1, k2
+    const Q4<T> *cst;   // Ms, k1, k2, 1/Ms
     Q4<T> *mn;          // M^n, e0 = Ms^2 - |M^n|^2
     Q4<T> *bc;          // beta = -kappa M^n x Heff^n, C' = H^n - dt/(2 mu0) curl E
     Q4<T> *dm[2];       // iterates of DeltaM = M^r - M^n
@@ -216,6 +216,27 @@ __device__ __forceinline__ void curl_e(const Geo &g, S *const E[3], const T inv_
         rest = -(e(2, i + 1, j, k) - e(2, i, j, k)) * idx;
     } else {
         rest = (e(1, i + 1, j, k) - e(1, i, j, k)) * idx - (e(0, i, j + 1, k) - e(0, i, j, k)) * idy;
+        zp = T(0);
+    }
+}
+
+// The same for the face at 32-bit padded index q (grids below 2^32
+// elements): its four edges are q plus one-element, row or plane offsets,
+// with the operations of curl_e in the same order.
+template <typename T, typename S>
+__device__ __forceinline__ void curl_e32(const Geo &g, S *const E[3], const T inv_d[3], int d, unsigned q, T &rest,
+                                         T &zp, T sE = T(1))
+{
+    const unsigned X = (unsigned)g.X, XY = (unsigned)g.X * (unsigned)g.Y;
+    const T idx = inv_d[0], idy = inv_d[1], idz = inv_d[2];
+    if (d == 0) {
+        rest = (ld_s(E[2] + q + X, sE) - ld_s(E[2] + q, sE)) * idy;
+        zp = -(ld_s(E[1] + q + XY, sE) - ld_s(E[1] + q, sE)) * idz;
+    } else if (d == 1) {
+        zp = (ld_s(E[0] + q + XY, sE) - ld_s(E[0] + q, sE)) * idz;
+        rest = -(ld_s(E[2] + q + 1u, sE) - ld_s(E[2] + q, sE)) * idx;
+    } else {
+        rest = (ld_s(E[1] + q + 1u, sE) - ld_s(E[1] + q, sE)) * idx - (ld_s(E[0] + q + X, sE) - ld_s(E[0] + q, sE)) * idy;
         zp = T(0);
     }
 }

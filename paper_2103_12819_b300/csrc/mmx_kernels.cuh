@@ -210,7 +210,8 @@ __global__ void k_box_init_m(const Geo g, Box<T> b, int d, const double *__restr
     for (int c = 0; c < 3; c++) b.M[3 * d + c][l] = (T)m[c];
 }
 
-// Per-magnetic-face constants in list order: Ms, k1, k2 from the box arrays.
+// Per-magnetic-face constants in list order: Ms, k1, k2 from the box arrays
+// and 1/Ms, which scales the iteration residual.
 template <typename T> __global__ void k_box_cst(Box<T> b)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -222,7 +223,7 @@ template <typename T> __global__ void k_box_cst(Box<T> b)
     c.x = b.ms[d][l];
     c.y = b.k1[d][l];
     c.z = b.k2[d][l];
-    c.w = T(0);
+    c.w = c.x > T(0) ? T(1) / c.x : T(0);   // the residual's 1/Ms
     const_cast<Q4<T> *>(b.cst)[t] = c;
 }
 
@@ -552,7 +553,8 @@ __device__ __forceinline__ void first_load(const Geo &g, const Fields<T, S> &f, 
                                            FirstIn<T> &in)
 {
     in.cs = q4_load(b.cst + t);
-    curl_e(g, f.E, f.inv_d, D, fo.i, fo.j, fo.k, in.rest, in.zp, f.sE);
+    const unsigned q = gidx32(g, fo.i, fo.j, fo.k);
+    curl_e32(g, f.E, f.inv_d, D, q, in.rest, in.zp, f.sE);
     const Q4<T> m0 = q4_load(b.mn + t);
     if (SECOND) {
         const Q4<T> d0 = q4_load(dmp + t);
@@ -565,7 +567,7 @@ __device__ __forceinline__ void first_load(const Geo &g, const Fields<T, S> &f, 
         in.Mn[0] = m0.x;
         in.Mn[1] = m0.y;
         in.Mn[2] = m0.z;
-        in.hn = ld_s(Hin[D] + gidx32(g, fo.i, fo.j, fo.k), f.sH);
+        in.hn = ld_s(Hin[D] + q, f.sH);
         h_vector<D>(g, b, Hin, Hp, 0, fo.i, fo.j, fo.k, in.h, f.sH);
     }
 }
@@ -599,7 +601,7 @@ __device__ __forceinline__ T first_finish(const Geo &g, const Box<T> &b, T *cons
     b.dm[1][t] = q4(dM[0], dM[1], dM[2], T(0));
     const bool wall = wall_node(g, D, D == 0 ? fo.i : D == 1 ? fo.j : fo.k);
     Hw[D][fo.l] = wall ? T(0) : cp - dMh;
-    return max(abs(dM[0]), max(abs(dM[1]), abs(dM[2]))) / Ms;
+    return max(abs(dM[0]), max(abs(dM[1]), abs(dM[2]))) * in.cs.w;
 }
 
 // Phase 0 on a non-magnetic face of family D: its final H in both iterate
@@ -648,7 +650,7 @@ __device__ __forceinline__ T next_finish(const Geo &g, const Box<T> &b, const Fa
     const bool wall = wall_node(g, D, D == 0 ? fo.i : D == 1 ? fo.j : fo.k);
     Hcur[D][fo.l] = wall ? T(0) : in.bq.w - dMh;
     b.dm[cr][t] = q4(dM[0], dM[1], dM[2], T(0));
-    return max(abs(dM[0] - in.pq.x), max(abs(dM[1] - in.pq.y), abs(dM[2] - in.pq.z))) / Ms;
+    return max(abs(dM[0] - in.pq.x), max(abs(dM[1] - in.pq.y), abs(dM[2] - in.pq.z))) * in.cs.w;
 }
 
 // Final H and M^(n+1/2) on one magnetic face of family D: H to the global
