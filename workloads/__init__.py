@@ -11,8 +11,7 @@ Arrays are float64 with shape (nz, ny, nx) in C order, i.e. x is the fastest
 index, matching the flat "x fastest" layout of the C entry points.
 
 Workloads follow the paper's test problems (Sec. 5: convergence test,
-air-filled waveguide, magnetically tunable filter) with the sizes fixed for
-this build:
+air-filled waveguide, magnetically tunable filter) at fixed sizes:
   * ``yig_slab_32``            32^3 PEC box with a YIG-like slab, point Jx source.
   * ``waveguide``              128x128x512 PEC guide, z-PML ends, YIG slab,
                                TE10 soft plane source.
