@@ -30,6 +30,7 @@
 
 namespace mmx {
 
+
 template <typename S> struct FusedIO {
     const S *Eo[3];
     const S *Ho[3];
@@ -538,6 +539,7 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
             cp_commit();
     }
     T acc = T(0);
+    bool nonfin = false;
     bool tma_bad = false;
     int b = 0, st = 0;
     for (int k = k0; k <= k1; k++, b ^= 1, st = st + 1 == ST ? 0 : st + 1) {
@@ -703,11 +705,13 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
                     paired = true;
                 }
             }
-            if (!paired) {
+            // one copy without source terms (J = 0 folds away) and one with
+            auto e_cols = [&](auto with_src) {
+                constexpr bool SRC = decltype(with_src)::value;
 #pragma unroll
             for (int e = 0; e < V; e++) {
                 T J0 = T(0), J1 = T(0), J2 = T(0);
-                if (src_here && cin[e]) {
+                if (SRC && cin[e]) {
                     J0 = j_source_a(g, f, amp, src, nsrc, 0, i0 + e, j, k);
                     J1 = j_source_a(g, f, amp, src, nsrc, 1, i0 + e, j, k);
                     J2 = j_source_a(g, f, amp, src, nsrc, 2, i0 + e, j, k);
@@ -752,6 +756,15 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
                     ez[e] = on ? v : T(0);
                 }
             }
+            };
+            if (!paired) {
+                // FP32 arithmetic: a copy without source terms on the planes
+                // that have none; FP64 keeps one copy (the second copy's
+                // registers cost it more than the subtractions it saves)
+                if (sizeof(T) == 8 || src_here)
+                    e_cols(std::true_type{});
+                else
+                    e_cols(std::false_type{});
             }
         }
         vstore(SEx(b, w) + col, ex);
@@ -767,7 +780,18 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
             // non-finite check on E^(n+1) only: H^(n+3/2) is formed from it,
             // so a non-finite H shows in E one step later
 #pragma unroll
-            for (int e = 0; e < V; e++) acc += ex[e] + ey[e] + ez[e];
+            for (int e = 0; e < V; e++) {
+                if constexpr (sizeof(T) == 8) {
+                    // FP64 (bound by the FP64 pipe): test the exponent bits
+                    // on the integer pipe instead of summing
+                    const unsigned a0 = (unsigned)__double2hiint((double)ex[e]) & 0x7ff00000u;
+                    const unsigned a1 = (unsigned)__double2hiint((double)ey[e]) & 0x7ff00000u;
+                    const unsigned a2 = (unsigned)__double2hiint((double)ez[e]) & 0x7ff00000u;
+                    nonfin |= (a0 == 0x7ff00000u) | (a1 == 0x7ff00000u) | (a2 == 0x7ff00000u);
+                } else {
+                    acc += ex[e] + ey[e] + ez[e];
+                }
+            }
         }
         __syncthreads();          // E^(n+1) of plane k visible to the row above
 
@@ -918,7 +942,7 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
         vcopy<T, V>(eyq, ey);
         vcopy<T, V>(ezq, ez);
     }
-    if (!isfinite(acc)) atomicOr(f.err, kErrNonFinite);
+    if (!isfinite(acc) || nonfin) atomicOr(f.err, kErrNonFinite);
 }
 
 // Resident CTAs per SM the vectorised kernel is compiled for: two when two
