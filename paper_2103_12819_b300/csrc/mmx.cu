@@ -58,6 +58,7 @@ struct mmx_ctx {
     // vectorised fused kernel: plan (0 chunk = not planned) and wall state
     int vec_chunk = 0;
     dim3 vec_grid;
+    ZChunks vec_z;           // chunk bounds along z (weighted by plane cost)
     int vec_xstride = 0;
     bool walls_dirty = false;
     // bulk-tensor (TMA) staging of the vectorised kernel: -1 not planned,
@@ -802,6 +803,63 @@ static bool encode_vec_maps(mmx_ctx *ctx)
     return true;
 }
 
+// Extra cost of a fused-pass plane inside the z-PML (split-field loads,
+// stores and updates) and of a plane holding a plane source, relative to an
+// interior plane.  On the 128x128x512 waveguide (FP32) a step took 146.1 us
+// with equal chunks and 134.5 us with these weights; 0.5-3 for the PML and
+// 0-5 for the source bracket them (flat within 0.3 us from 0.8 to 1.2).
+constexpr double kZWeightPml = 1.0, kZWeightSrc = 1.0;
+
+// Chunk bounds of the fused pass along z for at most nch chunks (the count
+// that fills one resident wave): the max over chunks of the summed plane
+// weights is minimised (binary search on the bound, greedy fill), with a
+// plane weighing 1, plus kZWeightPml inside the z-PML and kZWeightSrc where
+// a plane source sits.  Every chunk keeps at least 2 planes.  Returns the
+// chunk count.
+static int plan_zchunks(mmx_ctx *ctx, int nch)
+{
+    const int nz = ctx->desc.n[2], np = ctx->g.npml;
+    nch = std::max(1, std::min({nch, kMaxZChunks, nz / 2}));
+    std::vector<double> w(nz, 1.0);
+    for (int k = 0; k < nz; k++) {
+        if (np > 0 && (k < np || k >= nz - np)) w[k] += kZWeightPml;
+    }
+    for (const mmx_source_desc &q : ctx->src)
+        if (q.kind == 1) w[std::min(q.k, nz - 1)] += kZWeightSrc;
+    // chunks a bound B needs, each closed once adding a plane would pass B
+    auto fill = [&](double B, int *b) {
+        int c = 0, k0 = 0;
+        double acc = 0.0;
+        for (int k = 0; k < nz; k++) {
+            if (k - k0 >= 2 && acc + w[k] > B) {
+                if (b) b[c] = k0;
+                c++;
+                k0 = k;
+                acc = 0.0;
+            }
+            acc += w[k];
+        }
+        if (b) {
+            b[c] = k0;
+            b[c + 1] = nz;
+        }
+        return c + 1;
+    };
+    double lo = 0.0, hi = 0.0;
+    for (double x : w) hi += x;
+    for (int it = 0; it < 60; it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (fill(mid, nullptr) <= nch) hi = mid; else lo = mid;
+    }
+    const int c = fill(hi, ctx->vec_z.b);
+    // a trailing chunk of fewer than 2 planes joins the one before it
+    if (c > 1 && ctx->vec_z.b[c] - ctx->vec_z.b[c - 1] < 2) {
+        ctx->vec_z.b[c - 1] = nz;
+        return c - 1;
+    }
+    return c;
+}
+
 template <typename T, typename S> static int plan_vec(mmx_ctx *ctx)
 {
     constexpr int W = 32 * Lanes<T>::V;
@@ -825,7 +883,7 @@ template <typename T, typename S> static int plan_vec(mmx_ctx *ctx)
     chunk = std::min(chunk, n[2]);
     ctx->vec_chunk = chunk;
     ctx->vec_xstride = xs;
-    ctx->vec_grid = dim3(ntx, nty, (n[2] + chunk - 1) / chunk);
+    ctx->vec_grid = dim3(ntx, nty, plan_zchunks(ctx, (n[2] + chunk - 1) / chunk));
     ctx->vec_tma = 0;
     if constexpr (std::is_same<T, float>::value && std::is_same<S, float>::value) {
         if (MMX_VEC_TMA && !(ctx->any_sigma || ctx->any_mu) && ctx->epsc && encode_vec_maps(ctx)) {
@@ -883,13 +941,13 @@ static void launch_vec_v(mmx_ctx *ctx, const Fields<T, S> &f, const FusedIO<S> &
             const int p = (void *)io.Ho[0] == ctx->vmap_key[0] ? 0 : 1;
             k_fused_vec_tma<T, S, BY, ST, NH, PMLK, GEN>
                 <<<ctx->vec_grid, dim3(32, BY + 1), VecLayout<T, S, BY, GEN, ST, true>::bytes, ctx->stream>>>(
-                    ctx->g, f, io, ctx->vmaps[p], (const Src<T> *)ctx->dsrc, nsrc, ctx->vec_chunk, ctx->vec_xstride);
+                    ctx->g, f, io, ctx->vmaps[p], (const Src<T> *)ctx->dsrc, nsrc, ctx->vec_z, ctx->vec_xstride);
             return;
         }
     }
     k_fused_vec<T, S, BY, ST, NH, PMLK, GEN><<<ctx->vec_grid, dim3(32, BY + 1), vec_smem_bytes<T, S, GEN>(),
                                                ctx->stream>>>(
-        ctx->g, f, io, (const Src<T> *)ctx->dsrc, nsrc, ctx->vec_chunk, ctx->vec_xstride);
+        ctx->g, f, io, (const Src<T> *)ctx->dsrc, nsrc, ctx->vec_z, ctx->vec_xstride);
 }
 
 template <typename T, typename S>
@@ -1825,6 +1883,9 @@ int mmx_add_source(mmx_ctx *ctx, const mmx_source_desc *s)
     }
     // Src<T> has the same layout for both T (only doubles and ints)
     CK(cudaMemcpyAsync(ctx->dsrc, hs.data(), hs.size() * sizeof(Src<double>), cudaMemcpyHostToDevice, ctx->stream));
+    // a plane source changes the cost of its plane: re-place the chunk bounds
+    if (s->kind == 1 && ctx->vec_chunk)
+        ctx->vec_grid.z = plan_zchunks(ctx, (ctx->desc.n[2] + ctx->vec_chunk - 1) / ctx->vec_chunk);
     CK(cudaStreamSynchronize(ctx->stream));
     return MMX_OK;
 }

@@ -327,13 +327,14 @@ template <typename T, typename S, int BY, bool GEN, int ST, bool TMA = false> st
     static constexpr unsigned tx = (unsigned)((3 * RR + 3 * R) * W * sizeof(S) + (CBF ? RR * W * sizeof(T) : 0));
 };
 
-// The kernel body for the CTA at tile (bx, by, bz) of one grid: the single
-// grid launch passes its block index, the batched launch the entry of its
-// work table; amp holds this step's source amplitudes.
+// The kernel body for the CTA at tile (bx, by) and z range [k0, k1) of one
+// grid: the single grid launch passes its block index and chunk bounds, the
+// batched launch the entry of its work table; amp holds this step's source
+// amplitudes.
 template <typename T, typename S, int BY, int ST, int NH, bool PMLK, bool GEN, bool TMA = false>
 __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> &f, const FusedIO<S> &io,
                                                const Src<T> *__restrict__ src, int nsrc, const T *amp,
-                                               int chunk, int xstride, int bx, int by, int bz,
+                                               int k0, int k1, int xstride, int bx, int by,
                                                const VecMaps *maps = nullptr)
 {
     using L = VecLayout<T, S, BY, GEN, ST, TMA>;
@@ -371,8 +372,6 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
     const int i0 = x0 + V * lane;
     const int col = V * lane;
     const int j = by * BY + w;
-    const int k0 = bz * chunk;
-    const int k1 = min(k0 + chunk, nz);
     const bool last_chunk = k1 == nz;
     const bool lane_on = j < ny && i0 < nx;
     const bool up_on = w == 0 && j > 0 && j <= ny && i0 < nx;
@@ -947,6 +946,16 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
 
 // Resident CTAs per SM the vectorised kernel is compiled for: two when two
 // copies of its shared memory fit in the SM's 228 KB (1 KB per CTA reserved).
+// z ranges of the fused pass: chunk c (blockIdx.z) marches planes
+// b[c] .. b[c+1]-1 and recomputes plane b[c+1] without storing it.  The host
+// places the bounds so the chunks carry equal work: PML planes and planes
+// holding a plane source cost more than the others, and the one resident
+// wave ends with its slowest chunk.
+constexpr int kMaxZChunks = 512;
+struct ZChunks {
+    int b[kMaxZChunks + 1];
+};
+
 template <typename T, typename S, int BY, int ST, bool GEN, bool TMA = false> struct VecMinBlocks {
     static constexpr int value = 2 * (VecLayout<T, S, BY, GEN, ST, TMA>::bytes + 1024) <= 228 * 1024 ? 2 : 1;
 };
@@ -954,11 +963,11 @@ template <typename T, typename S, int BY, int ST, bool GEN, bool TMA = false> st
 template <typename T, typename S, int BY, int ST, int NH, bool PMLK, bool GEN>
 __global__ void __launch_bounds__(32 * (BY + 1), (VecMinBlocks<T, S, BY, ST, GEN>::value))
     k_fused_vec(const __grid_constant__ Geo g, const __grid_constant__ Fields<T, S> f,
-                const __grid_constant__ FusedIO<S> io, const Src<T> *__restrict__ src, int nsrc, int chunk,
-                int xstride)
+                const __grid_constant__ FusedIO<S> io, const Src<T> *__restrict__ src, int nsrc,
+                const __grid_constant__ ZChunks zc, int xstride)
 {
-    fused_vec_body<T, S, BY, ST, NH, PMLK, GEN>(g, f, io, src, nsrc, f.src_amp, chunk, xstride, blockIdx.x,
-                                                blockIdx.y, blockIdx.z);
+    fused_vec_body<T, S, BY, ST, NH, PMLK, GEN>(g, f, io, src, nsrc, f.src_amp, zc.b[blockIdx.z],
+                                                zc.b[blockIdx.z + 1], xstride, blockIdx.x, blockIdx.y);
 }
 
 // The same pass with the planes staged by bulk tensor copies (TMA): one
@@ -969,10 +978,10 @@ template <typename T, typename S, int BY, int ST, int NH, bool PMLK, bool GEN>
 __global__ void __launch_bounds__(32 * (BY + 1), (VecMinBlocks<T, S, BY, ST, GEN, true>::value))
     k_fused_vec_tma(const __grid_constant__ Geo g, const __grid_constant__ Fields<T, S> f,
                     const __grid_constant__ FusedIO<S> io, const __grid_constant__ VecMaps maps,
-                    const Src<T> *__restrict__ src, int nsrc, int chunk, int xstride)
+                    const Src<T> *__restrict__ src, int nsrc, const __grid_constant__ ZChunks zc, int xstride)
 {
-    fused_vec_body<T, S, BY, ST, NH, PMLK, GEN, true>(g, f, io, src, nsrc, f.src_amp, chunk, xstride, blockIdx.x,
-                                                      blockIdx.y, blockIdx.z, &maps);
+    fused_vec_body<T, S, BY, ST, NH, PMLK, GEN, true>(g, f, io, src, nsrc, f.src_amp, zc.b[blockIdx.z],
+                                                      zc.b[blockIdx.z + 1], xstride, blockIdx.x, blockIdx.y, &maps);
 }
 
 // One grid of a batch: what the batched fused launch needs per instance, for
@@ -994,8 +1003,9 @@ __global__ void __launch_bounds__(32 * (BY + 1), (VecMinBlocks<T, S, BY, ST, GEN
 {
     const int4 wk = work[blockIdx.x];
     const VecInst<T, S> &I = inst[wk.x];
-    fused_vec_body<T, S, BY, ST, NH, PMLK, GEN>(I.g, I.f, I.io, I.src, I.nsrc, I.amp + (size_t)step * I.nsrc,
-                                                I.chunk, I.xstride, wk.y, wk.z, wk.w);
+    const int k0 = wk.w * I.chunk;
+    fused_vec_body<T, S, BY, ST, NH, PMLK, GEN>(I.g, I.f, I.io, I.src, I.nsrc, I.amp + (size_t)step * I.nsrc, k0,
+                                                min(k0 + I.chunk, I.g.n[2]), I.xstride, wk.y, wk.z);
 }
 
 // Rows per CTA (+1 halo warp), chosen by measurement on the 128x128x512
