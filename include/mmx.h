@@ -192,13 +192,15 @@ MMX_API int mmx_sync(mmx_ctx *ctx);
 MMX_API int mmx_get_stats(mmx_ctx *ctx, mmx_stats *out);
 
 /* Check of the bounded device waits (failure detection without a fault):
- * launches a two-block grid barrier, the same wait the H/M kernels use, in
- * which one block leaves without arriving.  The other block gives up after
- * its wait budget (about 2^31 clock cycles, one second at the B300's clock),
- * latches the timeout and returns.  Returns MMX_ERR_TIMEOUT when the wait
- * gave up as designed (any other code means it did not); the barrier and
- * error words are then reset, so the context stays usable.  Synchronises;
- * a status pending from earlier work is returned first, without the check. */
+ * launches, one after the other, the two grid-wide waits the H/M kernels
+ * use (the grid barrier, and the voting barrier that also takes the
+ * convergence decision), each in a two-block grid in which one block leaves
+ * without arriving.  The other block gives up after its wait budget (about
+ * 2^31 clock cycles, one second at the B300's clock), latches the timeout
+ * and returns.  Returns MMX_ERR_TIMEOUT when both waits gave up as designed
+ * (any other code means one did not); the barrier and error words are then
+ * reset, so the context stays usable.  Synchronises; a status pending from
+ * earlier work is returned first, without the check. */
 MMX_API int mmx_check_bounded_wait(mmx_ctx *ctx);
 
 /* Iteration count of each H/M half step, oldest first (up to cap entries of

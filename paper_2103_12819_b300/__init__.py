@@ -273,7 +273,7 @@ class Solver:
 
     def check_bounded_wait(self):
         """Run the device-wait check (mmx_check_bounded_wait); returns its code,
-        -6 (TIMEOUT) when the bounded wait gave up as designed."""
+        -6 (TIMEOUT) when both bounded waits gave up as designed."""
         return self._L.mmx_check_bounded_wait(self._h)
 
     def get_stats(self):

@@ -103,7 +103,7 @@ struct mmx_ctx {
     double *flux_acc = nullptr;
 
     // control words (device)
-    unsigned long long *res = nullptr;     // [4][kMaxIter+1]
+    unsigned long long *res = nullptr;     // [8][kMaxIter+1]: residual maxima, then decision words
     unsigned long long *bar = nullptr;     // grid-barrier arrival count
     int *iterlog = nullptr;                // [kIterLogCap]
     unsigned long long *halfsteps = nullptr;
@@ -1510,10 +1510,13 @@ static int flux_gradient_t(mmx_ctx *ctx, int kp, int nsteps, int every, double *
 // Failure-detection probe: two blocks meet at a grid barrier and block
 // `absent` returns without arriving, so the other one waits out the bounded
 // wait and latches kErrTimeout (nothing faults, nothing hangs).
-__global__ void k_barrier_probe(unsigned long long *bar, int *err, int absent)
+__global__ void k_barrier_probe(unsigned long long *bar, int *err, int absent, int vote)
 {
     if ((int)blockIdx.x == absent) return;
-    grid_barrier(bar, err);
+    if (vote)
+        grid_vote(bar + 1, false, err);
+    else
+        grid_barrier(bar, err);
 }
 
 extern "C" {
@@ -1582,7 +1585,7 @@ int mmx_create(const mmx_grid_desc *desc, void *cuda_stream, mmx_ctx **out)
             if (!rc) rc = dalloc(ctx, &ctx->Ezpalt[a], sb);
             if (!rc) rc = dalloc(ctx, &ctx->Hzp[a], sb);
         }
-    if (!rc) rc = dalloc(ctx, (void **)&ctx->res, 4 * (kMaxIter + 1) * sizeof(unsigned long long));
+    if (!rc) rc = dalloc(ctx, (void **)&ctx->res, 2 * kVoteRows * (kMaxIter + 1) * sizeof(unsigned long long));
     if (!rc) rc = dalloc(ctx, (void **)&ctx->bar, kBarWords * sizeof(unsigned long long));
     if (!rc) rc = dalloc(ctx, (void **)&ctx->iterlog, kIterLogCap * sizeof(int));
     if (!rc) rc = dalloc(ctx, (void **)&ctx->halfsteps, sizeof(unsigned long long));
@@ -1935,10 +1938,15 @@ int mmx_check_bounded_wait(mmx_ctx *ctx)
     if (!ctx || !ctx->E[0]) return MMX_ERR_INVALID;
     int rc = read_status(ctx);
     if (rc) return rc;
-    CK(cudaMemsetAsync(ctx->bar, 0, kBarWords * sizeof(unsigned long long), ctx->stream));
-    k_barrier_probe<<<2, 32, 0, ctx->stream>>>(ctx->bar, ctx->errw, 1);
-    CK(cudaGetLastError());
-    return read_status(ctx);
+    // the grid barrier, then the voting barrier of the H/M iteration
+    for (int vote = 0; vote < 2; vote++) {
+        CK(cudaMemsetAsync(ctx->bar, 0, kBarWords * sizeof(unsigned long long), ctx->stream));
+        k_barrier_probe<<<2, 32, 0, ctx->stream>>>(ctx->bar, ctx->errw, 1, vote);
+        CK(cudaGetLastError());
+        rc = read_status(ctx);
+        if (rc != MMX_ERR_TIMEOUT) return rc;
+    }
+    return rc;
 }
 
 int mmx_get_stats(mmx_ctx *ctx, mmx_stats *out)

@@ -144,7 +144,7 @@ template <typename T> struct Box {
     int max_iter;
     int order;
     T cfar;             // dt/(2 mu0)
-    unsigned long long *res;   // [2][kMaxIter+1] residual bit patterns
+    unsigned long long *res;   // [8][kMaxIter+1]: residual bit patterns, then decision words
     unsigned long long *bar;   // grid barrier: monotonic arrival count
     int *iterlog;
     unsigned long long *halfsteps;

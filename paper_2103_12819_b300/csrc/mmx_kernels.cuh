@@ -402,7 +402,8 @@ __global__ void k_hard(const Geo g, Ptr3<T> F, const Src<T> *__restrict__ src, i
 // and returns false (the other blocks then time out at the next barrier).
 // (A two-level arrival over 16 group counters measured slower: the last
 // block then makes two dependent atomic round trips.)
-constexpr int kBarWords = 1;   // u64 words a barrier needs
+constexpr int kBarWords = 2;   // u64 words: the barrier's count, a probe's decision word
+constexpr int kVoteRows = 4;   // decision words sit this many residual rows past them
 
 __device__ __forceinline__ bool grid_barrier(unsigned long long *bar, int *err)
 {
@@ -431,6 +432,46 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *bar, int *err)
     return s_ok != 0;
 }
 
+// Grid barrier that also takes the convergence decision of one iteration:
+// every block adds 2^32 plus its not-converged flag to the iteration's own
+// word (zeroed before the launch) with acquire-release semantics and polls
+// it with acquire loads, 32 ns apart, until all blocks have arrived; the low
+// half then counts the blocks that did not converge.  The decision thus comes
+// with the barrier instead of a second read of the reduced residual after it
+// (134.8 -> 133.4 us per waveguide step).  Returns 1 if no block flagged, 0
+// if some did, -1 if the bounded wait (~2^31 cycles) expired, with
+// kErrTimeout latched.
+__device__ __forceinline__ int grid_vote(unsigned long long *word, bool flag, int *err)
+{
+    __shared__ int s_v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long nb = gridDim.x;
+        const unsigned long long add = (1ull << 32) | (flag ? 1ull : 0ull);
+        unsigned long long v;
+        asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(v) : "l"(word), "l"(add) : "memory");
+        v += add;
+        const long long t0 = clock64();
+        int res;
+        for (;;) {
+            if ((v >> 32) >= nb) {
+                res = (v & 0xffffffffull) == 0 ? 1 : 0;
+                break;
+            }
+            if (clock64() - t0 > (1LL << 31)) {
+                atomicOr(err, kErrTimeout);
+                res = -1;
+                break;
+            }
+            __nanosleep(32);
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(word) : "memory");
+        }
+        s_v = res;
+    }
+    __syncthreads();
+    return s_v;
+}
+
 // Block-wide max: warp shuffle, then one warp over the per-warp maxima.
 template <typename T> __device__ __forceinline__ T block_max(T v)
 {
@@ -457,15 +498,6 @@ __device__ __forceinline__ void publish_residual(unsigned long long *slot, T rbl
         atomicMax(slot, (unsigned long long)__double_as_longlong((double)rblock));
 }
 
-// All blocks read the reduced residual after the barrier; thread 0 decides.
-__device__ __forceinline__ bool residual_below(const unsigned long long *slot, double tol)
-{
-    __shared__ int s_conv;
-    if (threadIdx.x == 0)
-        s_conv = __longlong_as_double((long long)*(volatile const unsigned long long *)slot) < tol;
-    __syncthreads();
-    return s_conv != 0;
-}
 
 struct FaceOf {
     int d, i, j, k;
@@ -735,10 +767,17 @@ __device__ int hm_half_step(const Geo &g, const Fields<T, S> &f, const Box<T> &b
     }
     rmax = block_max(rmax);
     publish_residual(&res[1], rmax);
-    if (!grid_barrier(b.bar, b.err)) return -1;
+    // the decision words of this half step: the row kVoteRows rows past res.
+    // A block votes "not converged" when its maximum is at or above tol; the
+    // maximum over blocks is below tol exactly when no block votes so.  A
+    // block whose maximum is not positive (NaN included) publishes nothing
+    // and does not vote, as it does not raise the published maximum.
+    unsigned long long *const vote = res + kVoteRows * (kMaxIter + 1);
+    const int v1 = grid_vote(&vote[1], rmax > T(0) && !((double)rmax < b.tol), b.err);
+    if (v1 < 0) return -1;
 
     int r = 1;
-    bool conv = residual_below(&res[1], b.tol) || b.order == 1;
+    bool conv = v1 == 1 || b.order == 1;
     while (!conv && r < b.max_iter) {
         r++;
         const int pr = (r - 1) & 1, cr = r & 1;
@@ -765,8 +804,9 @@ __device__ int hm_half_step(const Geo &g, const Fields<T, S> &f, const Box<T> &b
         }
         rmax = block_max(rmax);
         publish_residual(&res[r], rmax);
-        if (!grid_barrier(b.bar, b.err)) return -1;
-        conv = residual_below(&res[r], b.tol);
+        const int vr = grid_vote(&vote[r], rmax > T(0) && !((double)rmax < b.tol), b.err);
+        if (vr < 0) return -1;
+        conv = vr == 1;
     }
 
     const int fr = r & 1;
@@ -803,16 +843,18 @@ __device__ int hm_half_step(const Geo &g, const Fields<T, S> &f, const Box<T> &b
 // are bound by load latency and grid barriers, so FP32 trades registers for
 // occupancy: 5 blocks of 256 threads (48 registers) against 2 at the
 // unconstrained 99 registers, 15% faster on the 128x128x512 waveguide; FP64
-// (126 registers) is bound by FP64 arithmetic and keeps its allocation.
+// is bound by FP64 arithmetic and needs at most 128 registers for its two
+// blocks (at 130 it fell to one block and a step took 1% longer).
 template <typename T> struct BoxMinBlocks {
-    static constexpr int value = sizeof(T) == 4 ? 5 : 1;
+    static constexpr int value = sizeof(T) == 4 ? 5 : 2;
 };
 
 // Cooperative launch over the magnetic box: nsub = 1 runs one H/M half step
 // from f.H into Hout; nsub = 2 runs Step 3 of step n and Step 1 of step n+1
 // back to back (both use the same E^(n+1)), the second reading the first's
 // result.  Residual words: launch parity `slot` uses rows 2 slot and
-// 2 slot + 1 of res and clears the other parity's rows for the next launch.
+// 2 slot + 1 of res (residual maxima) and the rows kVoteRows further on
+// (decision words), and clears the other parity's rows for the next launch.
 template <typename T, typename S = T>
 __global__ void __launch_bounds__(256, BoxMinBlocks<T>::value) k_hm_box(const __grid_constant__ Geo g,
                                                 const __grid_constant__ Fields<T, S> f,
@@ -822,7 +864,10 @@ __global__ void __launch_bounds__(256, BoxMinBlocks<T>::value) k_hm_box(const __
     const int W = kMaxIter + 1;
     if (blockIdx.x == 0) {
         unsigned long long *other = b.res + 2 * (1 - slot) * W;
-        for (int r = threadIdx.x; r < 2 * W; r += blockDim.x) other[r] = 0ull;
+        for (int r = threadIdx.x; r < 2 * W; r += blockDim.x) {
+            other[r] = 0ull;
+            other[kVoteRows * W + r] = 0ull;
+        }
     }
     if (nsub == 2) {
         // two half steps with one E; the first keeps its result in the

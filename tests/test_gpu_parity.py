@@ -158,9 +158,11 @@ def test_fp32_error_against_oracle_yig_slab(path):
 # ------------------------------------------------------- error reporting
 
 def test_bounded_wait_gives_up_and_context_stays_usable():
-    """Failure detection without a fault: a grid barrier that one block never
-    reaches gives up after its wait budget (about a second), the host reads
-    MMX_ERR_TIMEOUT, and the same context then steps and matches the oracle."""
+    """Failure detection without a fault: the grid barrier and the voting
+    barrier of the H/M iteration, each in a grid where one block never
+    arrives, give up after their wait budgets (about a second each), the host
+    reads MMX_ERR_TIMEOUT, and the same context then steps and matches the
+    oracle."""
     import time
     w = W.yig_slab_32(steps=4, n=16)
     sim = mmx.from_workload(w, prec=mmx.FP64)
