@@ -318,8 +318,13 @@ template <typename T, typename S, int BY, bool GEN, int ST, bool TMA = false> st
     static constexpr size_t up = cst + al((size_t)ST * NC * RR * W * sizeof(T));
     static constexpr size_t left = up + (TMA ? 0 : al((size_t)ST * 2 * W * sizeof(S)));
     static constexpr size_t ex = left + al((size_t)ST * 2 * R * LW * sizeof(S));
+    // Ez rows of the last planes: the H update of plane k reads plane k-1's
+    // after the mid-plane barrier.  Two buffers when a barrier at the top of
+    // every plane keeps a warp from writing plane k+1's meanwhile; three in
+    // the TMA variant, which has no such barrier
+    static constexpr int NEZ = TMA ? 3 : 2;
     static constexpr size_t ez = ex + al((size_t)2 * R * W * sizeof(T));
-    static constexpr size_t eu = ez + al((size_t)2 * R * W * sizeof(T));
+    static constexpr size_t eu = ez + al((size_t)NEZ * R * W * sizeof(T));
     static constexpr size_t el = eu + (CBF && !TMA ? al((size_t)ST * W * sizeof(T)) : 0);
     static constexpr size_t mb = el + (CBF ? al((size_t)ST * 2 * R * sizeof(T)) : 0);
     static constexpr size_t bytes = mb + (TMA ? al((size_t)ST * 8) : 0);
@@ -528,10 +533,13 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
             vzero<T, V>(hyp);
         }
     }
-    // prologue: planes k0 .. k0+ST-2 in flight (one copy group per plane,
-    // empty groups past the chunk keep the group count uniform)
+    // prologue: planes k0 .. k0+ST-2 in flight (k0 .. k0+ST-1 with bulk
+    // copies, which refill a stage as soon as its plane has been read); one
+    // copy group per plane, empty groups past the chunk keep the group count
+    // uniform
+    constexpr int PRE = TMA ? ST : ST - 1;
 #pragma unroll
-    for (int s = 0; s < ST - 1; s++) {
+    for (int s = 0; s < PRE; s++) {
         if (k0 + s <= k1)
             issue(k0 + s, s);
         else
@@ -541,7 +549,8 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
     bool nonfin = false;
     bool tma_bad = false;
     int b = 0, st = 0;
-    for (int k = k0; k <= k1; k++, b ^= 1, st = st + 1 == ST ? 0 : st + 1) {
+    int ze = 0, zq = L::NEZ - 1;      // Ez buffers of planes k and k-1
+    for (int k = k0; k <= k1; k++, b ^= 1, st = st + 1 == ST ? 0 : st + 1, zq = ze, ze = ze + 1 == L::NEZ ? 0 : ze + 1) {
         if constexpr (TMA) {
             // bounded wait for plane k's bulk copies (stage st, use (k-k0)/ST)
             if (!tma_bad) {
@@ -556,9 +565,12 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
                 }
             }
         }
-        cp_wait<ST - 2>();
-        __syncthreads();          // plane k staged; every thread is done with plane k-1
-        {
+        if constexpr (TMA) {
+            // this warp's lane-0 halo copies of plane k (read by lane 0 only)
+            cp_wait<ST - 1>();
+        } else {
+            cp_wait<ST - 2>();
+            __syncthreads();      // plane k staged; every thread is done with plane k-1
             // plane k+ST-1 into the stage plane k-1 used
             const int sn = st == 0 ? ST - 1 : st - 1;
             if (k + ST - 1 <= k1)
@@ -767,7 +779,7 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
             }
         }
         vstore(SEx(b, w) + col, ex);
-        vstore(SEz(b, w) + col, ez);
+        vstore(SEz(ze, w) + col, ez);
         if (store && own_plane) {
             P::gst(io.En[0] + q, ex, isE);
             P::gst(io.En[1] + q, ey, isE);
@@ -793,6 +805,15 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
             }
         }
         __syncthreads();          // E^(n+1) of plane k visible to the row above
+        if constexpr (TMA) {
+            // every thread has read stage st (all its reads precede the
+            // barrier above): plane k+ST into it, half a plane earlier than
+            // a refill at the top of the next plane, and no barrier there
+            if (k + ST <= k1)
+                issue(k + ST, st);
+            else
+                cp_commit();
+        }
 
         // ---- H: Hz at plane k, Hx and Hy at layer k-1/2
         const T eyr = __shfl_down_sync(0xffffffffu, ey[0], 1);
@@ -852,7 +873,7 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
                     vzero<T, V>(sx);
                     vzero<T, V>(sy);
                 }
-                sload(ezd, SEz(b ^ 1, w + 1) + col);
+                sload(ezd, SEz(zq, w + 1) + col);
                 T hxn[V], hyn[V];
                 bool hpaired = false;
                 if constexpr (PAIRED) {
