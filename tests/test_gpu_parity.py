@@ -272,6 +272,27 @@ def test_vectorised_fused_equals_plain(prec, n):
     np.testing.assert_array_equal(a.get_iter_log(), b.get_iter_log())
 
 
+def test_bulk_copy_fused_pass_is_deterministic():
+    """The bulk-copy fused pass has one block barrier per plane, so warps run
+    up to a plane apart and the exchange rows they share must be buffered
+    deeply enough.  Two fresh runs of the full 128x128x512 waveguide (chunks of
+    about 34 planes, FP32) must give bit-identical fields: a warp overwriting
+    rows another still reads would show as a difference."""
+    import hashlib
+    w = W.waveguide(steps=300)
+    digests = []
+    for _ in range(2):
+        sim = mmx.from_workload(w, prec=mmx.FP32, path=mmx.PATH_FUSED)
+        prof = _kernels_seen(sim, 2)
+        assert "fused_eh_vec" in prof, prof
+        sim.step(298)
+        assert sim.sync(check=False) == 0
+        digests.append([hashlib.sha256(np.ascontiguousarray(sim.get_field(fid)).tobytes()).hexdigest()
+                        for fid in range(19)])
+        sim.close()
+    assert digests[0] == digests[1]
+
+
 @pytest.mark.parametrize("bcz,n", [(W.PERIODIC, (140, 9, 12)), (W.PEC, (37, 11, 10))], ids=["periodic-z", "pec-z"])
 def test_bulk_copy_staging_equals_plain_fp32(bcz, n):
     """FP32 storage without sigma or mu_r stages the fused kernel's planes with
