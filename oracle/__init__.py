@@ -19,30 +19,35 @@ _SRC = os.path.join(_HERE, "mmx_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libmmx_oracle.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
+
+# Build variants: "" is the oracle; "literal" evaluates Eq. iterate_H as
+# printed in FP64 (ORC_LITERAL_ITERATE_H), used only to bound the effect of
+# readings R13/R14 in a test.
+_VARIANTS = {"": [], "literal": ["-DORC_LITERAL_ITERATE_H=1"]}
 
 ERR_NAMES = {0: "OK", -1: "INVALID", -2: "OOM", -4: "NOT_CONVERGED", -5: "NONFINITE"}
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, variant: str = "") -> str:
     """Compile the oracle with gcc (-O2, no fast-math, no FMA contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
+    path = _LIB_PATH if not variant else os.path.join(_BUILD, "libmmx_oracle_%s.so" % variant)
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+        return path
+    tmp = path + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+           "-fno-fast-math"] + _VARIANTS[variant] + ["-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
-def lib():
-    global _lib
+def lib(variant: str = ""):
     with _lock:
-        if _lib is None:
-            L = ctypes.CDLL(build())
+        if variant not in _libs:
+            L = ctypes.CDLL(build(variant=variant))
             P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
             dp = ctypes.POINTER(ctypes.c_double)
             L.orc_create.restype = P
@@ -71,8 +76,8 @@ def lib():
             L.orc_last_residual.argtypes = [P]
             L.orc_steps_done.restype = LL
             L.orc_steps_done.argtypes = [P]
-            _lib = L
-    return _lib
+            _libs[variant] = L
+    return _libs[variant]
 
 
 def _dptr(a: Optional[np.ndarray]):
@@ -90,8 +95,8 @@ class OracleError(RuntimeError):
 class Sim:
     """One oracle simulation instance (cell-centred inputs, Yee-located fields)."""
 
-    def __init__(self, n, d, dt, bc, pml_cells=0, order=2, tol=1e-10, max_iter=64):
-        self._L = lib()
+    def __init__(self, n, d, dt, bc, pml_cells=0, order=2, tol=1e-10, max_iter=64, variant=""):
+        self._L = lib(variant)
         self.n = tuple(int(v) for v in n)
         bcs = (ctypes.c_int * 3)(*[int(b) for b in bc])
         self._h = self._L.orc_create(self.n[0], self.n[1], self.n[2], float(d[0]), float(d[1]),
@@ -188,9 +193,9 @@ class Sim:
         return int(self._L.orc_steps_done(self._h))
 
 
-def from_workload(w, with_sources=True) -> Sim:
+def from_workload(w, with_sources=True, variant="") -> Sim:
     """Build an oracle instance from a ``workloads.Workload``."""
-    s = Sim(w.n, w.d, w.dt, w.bc, w.pml_cells, w.order, w.tol, w.max_iter)
+    s = Sim(w.n, w.d, w.dt, w.bc, w.pml_cells, w.order, w.tol, w.max_iter, variant=variant)
     s.set_materials(w.eps_r, w.sigma, w.mu_r, w.Ms, w.alpha, w.gamma)
     s.set_bias(*w.h0)
     if w.m_cells is not None and w.Ms is not None and np.any(w.Ms > 0):

@@ -72,6 +72,12 @@
  *       through the stored M^n, x Ms_n/|x| - M^n with Ms_n = |M^n| (equal to
  *       N()'s change in exact arithmetic), so that this storage rounding does
  *       not enter H; the stored M^(n+1/2,r) is N(x) itself.
+ *
+ * Compiled with ORC_LITERAL_ITERATE_H defined, the oracle instead evaluates
+ * Eq. iterate_H as printed, H^n + M^n - M^(n+1/2,r) - dt/(2 mu0) curl E, in
+ * FP64 from left to right with the stored (rounded) N(x).  That build exists
+ * only so that a test can show that readings R13/R14 move the results at the
+ * rounding level and no more.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -104,6 +110,7 @@ typedef struct orc_sim {
     long long nmag[3], *mag[3];     /* flat indices of magnetic faces per family */
     int *magix[3];                  /* (i, j, k) of each magnetic face */
     long double *C[3], *Bv[3];      /* per magnetic face: H^n - dt/(2 mu0) curl E, b */
+    double *Hl[3], *Cl[3];          /* per magnetic face: H^n and dt/(2 mu0) curl E (FP64) */
     double *Mn[3], *Mr[3], *Hr[3];  /* per magnetic face work */
     orc_source *src;
     int nsrc;
@@ -269,7 +276,9 @@ static void free_mag(orc_sim *s)
 {
     for (int d = 0; d < 3; d++) {
         free(s->mag[d]); free(s->magix[d]); free(s->C[d]); free(s->Bv[d]); free(s->Mn[d]); free(s->Mr[d]); free(s->Hr[d]);
+        free(s->Hl[d]); free(s->Cl[d]);
         s->mag[d] = NULL; s->magix[d] = NULL; s->C[d] = s->Bv[d] = NULL;
+        s->Hl[d] = s->Cl[d] = NULL;
         s->Mn[d] = s->Mr[d] = s->Hr[d] = NULL;
         s->nmag[d] = 0;
     }
@@ -352,10 +361,14 @@ static int build_mag(orc_sim *s)
         s->magix[d] = (int *)malloc(3 * m * sizeof(int));
         s->C[d] = (long double *)malloc(m * sizeof(long double));
         s->Hr[d] = (double *)malloc(m * sizeof(double));
+        s->Hl[d] = (double *)malloc(m * sizeof(double));
+        s->Cl[d] = (double *)malloc(m * sizeof(double));
         s->Bv[d] = (long double *)malloc(3 * m * sizeof(long double));
         s->Mn[d] = (double *)malloc(3 * m * sizeof(double));
         s->Mr[d] = (double *)malloc(3 * m * sizeof(double));
-        if (!s->mag[d] || !s->magix[d] || !s->C[d] || !s->Hr[d] || !s->Bv[d] || !s->Mn[d] || !s->Mr[d]) return ORC_ERR_OOM;
+        if (!s->mag[d] || !s->magix[d] || !s->C[d] || !s->Hr[d] || !s->Bv[d] || !s->Mn[d] || !s->Mr[d] ||
+            !s->Hl[d] || !s->Cl[d])
+            return ORC_ERR_OOM;
         cnt = 0;
         for (long long q = 0; q < N; q++)
             if (s->ms[d].v[q] > 0.0) {
@@ -662,6 +675,25 @@ static double h_from_x(long double C, const long double x[3], const double Mn[3]
     return (double)(C - (x[d] * (mn / xn) - (long double)Mn[d]));
 }
 
+/* N(x) into Mr (rounded to FP64; x is left renormalised) and H^(n+1/2,r) on
+ * magnetic face m of family d from Eq. iterate_H: by default along the
+ * sphere (reading R14, h_from_x); with ORC_LITERAL_ITERATE_H as printed,
+ * ((H^n + M^n) - M^(n+1/2,r)) - dt/(2 mu0) curl E in FP64. */
+static double h_after_renorm(const orc_sim *s, int d, long long m, long double x[3], const double Mn[3],
+                             double Ms, double Mr[3])
+{
+#ifdef ORC_LITERAL_ITERATE_H
+    renorm_ld(x, Ms);
+    for (int c = 0; c < 3; c++) Mr[c] = (double)x[c];
+    return ((s->Hl[d][m] + Mn[d]) - Mr[d]) - s->Cl[d][m];
+#else
+    double hr = h_from_x(s->C[d][m], x, Mn, d);
+    renorm_ld(x, Ms);
+    for (int c = 0; c < 3; c++) Mr[c] = (double)x[c];
+    return hr;
+#endif
+}
+
 static void cross_ld(const long double a[3], const long double b[3], long double r[3])
 {
     r[0] = a[1] * b[2] - a[2] * b[1];
@@ -799,6 +831,8 @@ static int hm_half_step(orc_sim *s)
             curl_e(s, d, ix, &rest, &zp);
             double Mn[3] = {s->M[d][0].v[q], s->M[d][1].v[q], s->M[d][2].v[q]};
             s->C[d][m] = (long double)s->H[d].v[q] - (long double)(dt / (2.0 * ORC_MU0) * (rest + zp));
+            s->Hl[d][m] = s->H[d].v[q];
+            s->Cl[d][m] = dt / (2.0 * ORC_MU0) * (rest + zp);
             for (int c = 0; c < 3; c++) s->Mn[d][3 * m + c] = Mn[c];
             if (s->order == 2) {
                 double h[3];
@@ -832,9 +866,7 @@ static int hm_half_step(orc_sim *s)
                 long double c1 = (long double)(ORC_MU0 * gL), c2 = (long double)(al * ORC_MU0 * gL / Ms);
                 for (int c = 0; c < 3; c++)
                     x[c] = Mn[c] + (long double)(dt / 2.0) * (-c1 * mxh[c] - c2 * mxmxh[c]);
-                double hr = h_from_x(s->C[d][m], x, &s->Mn[d][3 * m], d);
-                renorm_ld(x, Ms);
-                for (int c = 0; c < 3; c++) s->Mr[d][3 * m + c] = (double)x[c];
+                double hr = h_after_renorm(s, d, m, x, &s->Mn[d][3 * m], Ms, &s->Mr[d][3 * m]);
                 s->Hr[d][m] = wall_face(s, d, ix) ? 0.0 : hr;
             }
         }
@@ -881,12 +913,10 @@ static int hm_half_step(orc_sim *s)
                 long double axb[3], x[3];
                 cross_ld(a, b, axb);
                 for (int c = 0; c < 3; c++) x[c] = (b[c] + ab * a[c] - axb[c]) / (1.0L + aa);
-                double hr = h_from_x(s->C[d][m], x, Mn, d);
-                renorm_ld(x, Ms);
+                double hr = h_after_renorm(s, d, m, x, Mn, Ms, &s->Mr[d][3 * m]);
                 for (int c = 0; c < 3; c++) {
                     double dm = (double)(fabsl(x[c] - (long double)s->M[d][c].v[q]) / Ms);
                     if (dm > rho) rho = dm;
-                    s->Mr[d][3 * m + c] = (double)x[c];
                 }
                 s->Hr[d][m] = wall_face(s, d, ix) ? 0.0 : hr;
             }

@@ -802,3 +802,250 @@ def test_not_converged_is_reported():
     w.max_iter = 1
     s = oracle.from_workload(w)
     assert s.step(1, check=False) == -4
+
+
+# ------------------------------------------- P9: the first-order scheme (f4)
+
+def test_p9_first_order_uniform_precession_converges_at_first_order():
+    """Sec. 3.2.1 (Steps 1/3 with Eq. LLG_scalar): forward Euler of the
+    Landau-Lifshitz form over each half step, then N().  In the uniform
+    periodic box curl E = 0, so H + M is constant per face and the exact
+    solution is the constant-field Gilbert precession about W = H0 + H^0 + M^0
+    (the closed form of P6).  The first-order scheme must converge to it with
+    error ratio ~2 per halving of dt.  A wrong gamma_L = |gamma|/(1 + alpha^2),
+    a wrong sign of the M x (M x H) damping term, or a full dt instead of
+    dt/2 per half step (reading R10) converges to a different motion, and the
+    error then stops falling."""
+    m0 = 1.4e5 * np.array([0.8, 0.0, 0.6])
+    h0 = np.array([0.0, 0.0, 2e5])
+    h_init = -m0            # W = H0
+    alpha = 0.3
+    T = 400 * 2e-13
+    errs = []
+    for dt in (2e-13, 1e-13, 5e-14):
+        N = int(round(T / dt))
+        n = (3, 4, 5)
+        shp = (n[2], n[1], n[0])
+        s = oracle.Sim(n, (1e-4, 1.1e-4, 0.9e-4), dt, (W.PERIODIC,) * 3, order=1)
+        s.set_materials(Ms=np.full(shp, 1.4e5), alpha=np.full(shp, alpha), gamma=np.full(shp, 1.76e11))
+        s.set_bias(*h0)
+        s.set_M_cells(*[np.full(shp, m0[c]) for c in range(3)])
+        for c in range(3):
+            s.set_field(3 + c, np.full(s.field_size(3 + c), h_init[c]))
+        s.step(N)
+        assert set(s.iter_log().tolist()) == {1}
+        want = _gilbert_closed_form(m0, h0, alpha, N * dt)
+        got = np.array([s.get_field(6 + c)[0] for c in range(3)])
+        errs.append(np.linalg.norm(got - want) / 1.4e5)
+    r1, r2 = math.log2(errs[0] / errs[1]), math.log2(errs[1] / errs[2])
+    assert 0.85 < r1 < 1.15 and 0.85 < r2 < 1.15, (errs, r1, r2)
+    assert errs[2] < 0.05
+
+
+@pytest.mark.slow
+def test_p9_first_order_scheme_rates_sec_5_1():
+    """Sec. 5.1, the text after Table 2: with the first-order magnetisation
+    coupling the M components fall to first order and the E and H rates drop
+    to as low as 1.74 (the draft gives a range 1.74-2.35).  Same problem and
+    restriction as P8.  The dynamic components M_y, M_z must converge at rate
+    1 +- 0.15; M_x ~ Ms carries the first-order error only through the small
+    tilt, so its rate is reported, not bounded.  Every E/H rate lies in
+    1.6-2.4 and at least one falls clearly below 2."""
+    sols = {}
+    fids = (0, 1, 2, 3, 4, 5, 6, 10, 14)
+    for nn, steps in ((32, 2), (64, 4), (128, 8)):
+        w = W.convergence(nn, order=1, tol=1e-6)
+        s = oracle.from_workload(w)
+        s.step(steps)
+        sols[nn] = {fid: s.get_field(fid) for fid in fids}
+        s.close()
+    names = {0: "Ex", 1: "Ey", 2: "Ez", 3: "Hx", 4: "Hy", 5: "Hz", 6: "Mx", 10: "My", 14: "Mz"}
+    rates = {}
+    for fid, name in names.items():
+        e1 = np.mean(np.abs(_restrict(fid, sols[64][fid], (32,) * 3) - sols[32][fid]))
+        e2 = np.mean(np.abs(_restrict(fid, sols[128][fid], (64,) * 3) - sols[64][fid]))
+        rates[name] = math.log2(e1 / e2)
+    print("first-order scheme rates:", {k: round(v, 3) for k, v in rates.items()})
+    for name in ("My", "Mz"):
+        assert abs(rates[name] - 1.0) < 0.15, (name, rates)
+    eh = [rates[k] for k in ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz")]
+    assert all(1.6 < r < 2.4 for r in eh), rates
+    assert min(eh) < 1.9, rates
+
+
+# ---------------------------------------------------- hard sources (Sec. 3.2)
+
+def _waveform(q, t):
+    """The modulated Gaussian drive of Sec. 5.2.1 (Eq. gaulssian, free t0)."""
+    return q["amp"] * math.exp(-(t - q["t0"]) ** 2 / (2 * q["tp"] ** 2)) * math.cos(2 * math.pi * q["f0"] * t)
+
+
+def test_hard_sources_overwrite_after_their_update():
+    """Sec. 3.2: a hard source overwrites the field after its update (reading
+    R9: hard E after the E update, at t^(n+1); hard H after each H half step,
+    at that half step's end time).  A textbook numpy Yee leapfrog in a PEC
+    vacuum box that writes the same values at the same points of the step
+    must give the oracle's fields to rounding, and after every step the driven
+    edge and face hold g(t^(n+1)) exactly.  Writing at t^n instead of t^(n+1),
+    or before the update instead of after it, breaks the comparison."""
+    n = (6, 5, 7)
+    d = (1.0e-6, 1.3e-6, 0.8e-6)
+    dt = W.cfl_dt(d, 0.9)
+    nx, ny, nz = n
+    qe = dict(i=2, j=3, k=4, amp=3e4, f0=4e13, tp=12 * dt, t0=20 * dt)   # hard Ex at (2.5, 3, 4)
+    qh = dict(i=3, j=2, k=3, amp=70.0, f0=3e13, tp=9 * dt, t0=15 * dt)   # hard Hz at (3.5, 2.5, 3)
+    s = _vacuum_sim(n, d, dt, (W.PEC,) * 3)
+    s.add_source(W.SRC_HARD_E, 0, qe["i"], qe["j"], qe["k"], qe["amp"], qe["f0"], qe["tp"], qe["t0"])
+    s.add_source(W.SRC_HARD_H, 2, qh["i"], qh["j"], qh["k"], qh["amp"], qh["f0"], qh["tp"], qh["t0"])
+    Ex = np.zeros((nz + 1, ny + 1, nx))
+    Ey = np.zeros((nz + 1, ny, nx + 1))
+    Ez = np.zeros((nz, ny + 1, nx + 1))
+    Hx = np.zeros((nz, ny, nx + 1))
+    Hy = np.zeros((nz, ny + 1, nx))
+    Hz = np.zeros((nz + 1, ny, nx))
+    dx, dy, dz = d
+    fh = dt / (2 * MU0)
+    fe = dt / EPS0
+
+    def h_half(t_end):
+        nonlocal Hx, Hy, Hz
+        cx = (Ez[:, 1:, :] - Ez[:, :-1, :]) / dy - (Ey[1:] - Ey[:-1]) / dz
+        cy = (Ex[1:] - Ex[:-1]) / dz - (Ez[:, :, 1:] - Ez[:, :, :-1]) / dx
+        cz = (Ey[:, :, 1:] - Ey[:, :, :-1]) / dx - (Ex[:, 1:, :] - Ex[:, :-1, :]) / dy
+        Hx = Hx - fh * cx
+        Hy = Hy - fh * cy
+        Hz = Hz - fh * cz
+        Hx[:, :, [0, -1]] = 0
+        Hy[:, [0, -1], :] = 0
+        Hz[[0, -1]] = 0
+        Hz[qh["k"], qh["j"], qh["i"]] = _waveform(qh, t_end)
+
+    def e_full(t_end):
+        nonlocal Ex, Ey, Ez
+        Ex[1:-1, 1:-1, :] += fe * ((Hz[1:-1, 1:, :] - Hz[1:-1, :-1, :]) / dy
+                                   - (Hy[1:, 1:-1, :] - Hy[:-1, 1:-1, :]) / dz)
+        Ey[1:-1, :, 1:-1] += fe * ((Hx[1:, :, 1:-1] - Hx[:-1, :, 1:-1]) / dz
+                                   - (Hz[1:-1, :, 1:] - Hz[1:-1, :, :-1]) / dx)
+        Ez[:, 1:-1, 1:-1] += fe * ((Hy[:, 1:-1, 1:] - Hy[:, 1:-1, :-1]) / dx
+                                   - (Hx[:, 1:, 1:-1] - Hx[:, :-1, 1:-1]) / dy)
+        Ex[qe["k"], qe["j"], qe["i"]] = _waveform(qe, t_end)
+
+    ex_idx = qe["i"] + nx * (qe["j"] + (ny + 1) * qe["k"])
+    hz_idx = qh["i"] + nx * (qh["j"] + ny * qh["k"])
+    for step in range(40):
+        h_half((step + 0.5) * dt)
+        e_full((step + 1.0) * dt)
+        h_half((step + 1.0) * dt)
+        s.step(1)
+        assert s.get_field(0)[ex_idx] == _waveform(qe, (step + 1.0) * dt)
+        assert s.get_field(5)[hz_idx] == _waveform(qh, (step + 1.0) * dt)
+    for fid, a in enumerate((Ex, Ey, Ez, Hx, Hy, Hz)):
+        assert rel_l2(s.get_field(fid), a.ravel()) < 1e-12, fid
+        assert np.abs(a).max() > 0
+
+
+@pytest.mark.parametrize("comp", [0, 1])
+def test_te10_plane_source_profile_and_time_level(comp):
+    """Soft J plane source (reading R9: the TE10
+    profile sin(pi x/W), x measured from the lower x wall, W = nx dx; the
+    paper's printed cos(2 pi x/(W/2)) is read as garbled).  From zero fields
+    in vacuum one step gives E^1 = -dt J(t^(1/2))/eps0 on the plane's edges
+    and zero elsewhere (Step 2 of Sec. 3.2.1 with H^(1/2) = 0).  The drive is
+    chosen so that g(t^(1/2)) = amp exactly (t0 = dt/2, f0 = 0) while
+    g(0) = amp exp(-1/8): evaluating J at t^n, shifting x by half a cell or
+    using another width fails element by element."""
+    n = (9, 4, 6)
+    d = (1.1e-6, 1.0e-6, 0.9e-6)
+    dt = W.cfl_dt(d, 0.9)
+    nx, ny, nz = n
+    ks, amp = 3, 2.5e9
+    s = _vacuum_sim(n, d, dt, (W.PEC,) * 3)
+    s.add_source(W.SRC_PLANE_J_TE10, comp, 0, 0, ks, amp, 0.0, dt, 0.5 * dt)
+    s.step(1)
+    E = s.get_field(comp)
+    ext = W.field_extent(comp, n)
+    E = E.reshape(ext[2], ext[1], ext[0])
+    W_ = nx * d[0]
+    x = (np.arange(ext[0]) + (0.5 if comp == 0 else 0.0)) * d[0]
+    want_row = -dt * amp * np.sin(np.pi * x / W_) / EPS0
+    plane = E[ks]
+    # interior edges of the plane carry the profile; PEC wall edges are zero
+    lo_t = 1
+    hi_t = ext[1] - 1
+    if comp == 0:
+        inner = plane[lo_t:hi_t, :]
+        np.testing.assert_allclose(inner, np.broadcast_to(want_row, inner.shape), rtol=1e-13, atol=0)
+    else:
+        inner = plane[:, 1:-1]
+        np.testing.assert_allclose(inner, np.broadcast_to(want_row[1:-1], inner.shape), rtol=1e-13, atol=0)
+    assert np.all(np.delete(E, ks, axis=0) == 0.0)
+    assert np.all(s.get_field(1 - comp) == 0.0) and np.all(s.get_field(2) == 0.0)
+
+
+# ---------------------------------------- R12: initial M where the mean cancels
+
+@pytest.mark.parametrize("fam", [0, 1, 2])
+def test_r12_initial_m_falls_back_to_lower_cell(fam):
+    """Reading R12: a face whose averaged cell M falls below 1e-6 Ms (here two
+    cells with opposite directions, and a pair that cancels to 1e-9) takes the
+    direction of the lower-index cell, renormalised to Ms_face.  Every other
+    face is the renormalised mean (Sec. 3.1).  Taking the upper cell's
+    direction gives the opposite vector on the tested faces."""
+    n = (4, 3, 5)
+    shp = (n[2], n[1], n[0])
+    s = oracle.Sim(n, (1e-6,) * 3, 1e-16, (W.PEC,) * 3)
+    Ms = np.full(shp, 1.4e5)
+    s.set_materials(Ms=Ms, alpha=np.full(shp, 0.01), gamma=np.full(shp, 1.76e11))
+    rng = np.random.default_rng(5)
+    m = rng.normal(size=(3,) + shp)
+    lo = [1, 1, 2]
+    hi = list(lo)
+    hi[fam] += 1
+    u = np.array([0.3, -0.5, 0.81])
+    m[:, lo[2], lo[1], lo[0]] = u
+    m[:, hi[2], hi[1], hi[0]] = -u
+    lo2 = [2, 0, 1]
+    hi2 = list(lo2)
+    hi2[fam] += 1
+    v = np.array([-0.6, 0.2, 0.4])
+    m[:, lo2[2], lo2[1], lo2[0]] = v
+    m[:, hi2[2], hi2[1], hi2[0]] = -v + 1e-9 * np.array([1.0, 0.0, 0.0])
+    s.set_M_cells(*(m[c] * 1.4e5 for c in range(3)))
+    ext = W.field_extent(6 + 3 * fam, n)
+    M = np.stack([s.get_field(6 + 3 * fam + c).reshape(ext[::-1]) for c in range(3)])
+    for pair_lo, dirv in ((lo, u), (lo2, v)):
+        f = list(pair_lo)
+        f[fam] += 1                       # the face between the pair
+        got = M[:, f[2], f[1], f[0]]
+        np.testing.assert_allclose(got, 1.4e5 * dirv / np.linalg.norm(dirv), rtol=1e-14)
+    # an ordinary face: renormalised mean of its two cells
+    f = [1, 2, 3]
+    a = list(f)
+    a[fam] -= 1
+    mean = 0.5 * (m[:, a[2], a[1], a[0]] + m[:, f[2], f[1], f[0]])
+    np.testing.assert_allclose(M[:, f[2], f[1], f[0]], 1.4e5 * mean / np.linalg.norm(mean), rtol=1e-14)
+
+
+# ------------------------------------ R13/R14: effect bounded at rounding level
+
+def test_r13_r14_readings_move_results_at_rounding_level_only():
+    """Readings R13 (extended precision in the LLG algebra) and R14 (H takes
+    the on-sphere increment) change how Eq. iterate_H is rounded, not what it
+    computes.  An oracle build that evaluates Eq. iterate_H as printed,
+    H^n + M^n - M^(n+1/2,r) - dt/(2 mu0) curl E in FP64 with the stored N(x),
+    must agree with the oracle after the 200 steps of the 32^3 slab problem:
+    H to 1e-10 relative (the rounding of M ~ Ms = 1.4e5 A/m entering H of
+    order 10 A/m), E to 1e-10, M to 1e-14, identical iteration counts.  A
+    wrong on-sphere increment (a dropped M^n, a wrong norm) moves H by orders
+    of magnitude more."""
+    w = W.yig_slab_32(steps=200)
+    a = oracle.from_workload(w)
+    b = oracle.from_workload(w, variant="literal")
+    a.step(200)
+    b.step(200)
+    np.testing.assert_array_equal(a.iter_log(), b.iter_log())
+    for fid in range(15):
+        bar = 1e-10 if fid < 6 else 1e-14
+        assert rel_l2(b.get_field(fid), a.get_field(fid)) < bar, fid
+    # the two builds are different programs: H differs above the 1e-12 bar
+    assert max(rel_l2(b.get_field(f), a.get_field(f)) for f in (3, 4, 5)) > 1e-12
