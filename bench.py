@@ -131,11 +131,19 @@ def alg_bytes_per_cell(kernel, w, esz, ssz=None):
     (per magnetic cell 6 + 9 + 3 read, 3 + 9 written).  E and H words are
     ssz bytes (the stored type), eps_r esz bytes (the arithmetic type)."""
     ssz = esz if ssz is None else ssz
-    fields = {"e_update": 9, "h_update": 9, "fused_eh": 12, "fused_eh_vec": 12}.get(kernel)
-    coef = {"e_update": 1, "h_update": 0, "fused_eh": 1, "fused_eh_vec": 1}.get(kernel)
+    fields = {"e_update": 9, "h_update": 9, "fused_eh": 12, "fused_eh_vec": 12, "fused_eh_vec_tma": 12}.get(kernel)
+    coef = {"e_update": 1, "h_update": 0, "fused_eh": 1, "fused_eh_vec": 1, "fused_eh_vec_tma": 1}.get(kernel)
     if fields is not None:
         return fields * ssz + coef * esz
     return None
+
+
+def effective_fraction(w, value_per_gpu, word, peak_gbs):
+    """Step-level HBM fraction: B_alg x cell-updates/s / peak, with
+    B_alg = (13 + 21 f) words per cell-update (E, H, eps_r in and E, H out
+    everywhere; M, Ms, alpha, gamma in and M out on the magnetic fraction f)."""
+    f = float(np.count_nonzero(w.Ms > 0)) / w.ncells if w.Ms is not None else 0.0
+    return round((13 + 21 * f) * word * value_per_gpu / (peak_gbs * 1e9), 4), f
 
 
 def replica_layout(env=None):
@@ -340,22 +348,36 @@ def e2e_leg(torch, mmx, w, prec, path, K, stream):
             "back" % K}
 
 
-def cpu_baseline(w, budget_s=15.0):
-    """The FP64 oracle as it stands, single thread, on a bounded sample of
-    the same workload (first steps of the run)."""
+def _oracle_rate(w, variant, budget_s, max_steps=50):
     import oracle
-    s = oracle.from_workload(w)
+    s = oracle.from_workload(w, variant=variant)
     s.step(1)
     n, t0 = 0, time.perf_counter()
     while True:
         s.step(1)
         n += 1
         el = time.perf_counter() - t0
-        if el > budget_s or n >= 50:
+        if el > budget_s or n >= max_steps:
             break
     s.close()
-    return {"value": w.ncells * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%s, %d oracle steps after 1 warm-up step, single thread, %.1f s" % (WORKLOAD, n, el)}
+    return w.ncells * n / el, n, el
+
+
+def cpu_baseline(w, budget_s=15.0, all_cores=True):
+    """The FP64 oracle as it stands, single thread, on a bounded sample of
+    the same workload (first steps of the run); beside it the oracle's
+    OpenMP build (bit-identical, loops over z planes and magnetic faces in
+    parallel) on all host cores, timed the same way."""
+    rate, n, el = _oracle_rate(w, "", budget_s)
+    out = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "%s, %d oracle steps after 1 warm-up step, single thread, %.1f s" % (w.name, n, el)}
+    if all_cores:
+        cores = os.cpu_count() or 1
+        r2, n2, el2 = _oracle_rate(w, "omp", budget_s / 2)
+        out["all_cores"] = {"value": r2, "unit": UNIT, "cores": cores, "kind": "oracle (OpenMP build)",
+                            "sample": "%s, %d steps after 1 warm-up step, %d threads, %.1f s"
+                                      % (w.name, n2, cores, el2)}
+    return out
 
 
 # ---------------------------------------------------------------- arms
@@ -377,6 +399,76 @@ def reference_arm(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def stress_leg(torch, mmx, stream, peak, K=10, W=3):
+    """The 512^3 throughput configuration (PEC box, centred random 256^3
+    magnetic block, no source, FP32, tol 1e-6): cell-updates/s, the
+    step-level HBM fraction and the per-kernel shares (CUDA events)."""
+    import workloads
+    w = workloads.stress()
+    sim = mmx.from_workload(w, prec=mmx.FP32, stream=stream.cuda_stream, path=mmx.PATH_FUSED)
+    sim.step(W)
+    if sim.sync(check=False):
+        raise RuntimeError("stress warm-up failed: %s" % sim.last_error())
+    ms = time_steps(torch, sim, stream, K)
+    sim.sync()
+    sim.set_profiling(True)
+    sim.get_profile(reset=True)
+    sim.step(K)
+    prof = sim.get_profile(reset=True)
+    st = sim.get_stats()
+    info = sim.get_info()
+    sim.close()
+    value = w.ncells * K / (ms * 1e-3)
+    tot = sum(v[1] for v in prof.values())
+    eff, f = effective_fraction(w, value, 4, peak)
+    return {"workload": "stress_512^3 (PEC, centred random 256^3 magnetic block, no source, tol 1e-6)",
+            "cells": w.ncells, "steps": K, "warmup": W, "value": value, "unit": UNIT,
+            "ms_per_step": ms / K, "dtype": "f32", "magnetic_fraction": round(f, 4),
+            "effective_hbm_fraction": eff, "fused_kernel": info["fused_kernel_name"],
+            "box_faces_magnetic": info["box_faces_magnetic"],
+            "kernel_shares": {k: round(v[1] / tot, 4) for k, v in prof.items()},
+            "kernel_avg_us": {k: round(1e3 * v[1] / v[0], 1) for k, v in prof.items()},
+            "iters": [st["iters_min"], st["iters_max"]]}
+
+
+def sweep_leg(torch, mmx, stream, peak, K=200, W=10):
+    """The batched bias sweep: 256 independent instances with sizes from
+    {32, 48, 64, 96}^3, bias U[5e4, 2e5] A/m, FP32, advanced together by the
+    batched launches (one CUDA graph per call)."""
+    import workloads
+    specs = workloads.bias_sweep(256)
+    sols, cells, magcells = [], 0, 0
+    for n, h0, seed in specs:
+        w = workloads.tunable_filter(n, h0, steps=2000, seed=seed)
+        sols.append(mmx.from_workload(w, prec=mmx.FP32, stream=stream.cuda_stream))
+        cells += w.ncells
+        magcells += int(np.count_nonzero(w.Ms > 0))
+    b = mmx.Batch(sols, stream=stream.cuda_stream)
+    b.step(W)
+    if b.sync(check=False):
+        raise RuntimeError("sweep warm-up failed")
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ok = b.sync(check=False) == 0
+    iters = [s.get_stats()["iters_max"] for s in sols]
+    b.close()
+    for s in sols:
+        s.close()
+    value = cells * K / (ms * 1e-3)
+    f = magcells / cells
+    return {"workload": "bias_sweep_256 (sizes {32,48,64,96}^3, centred slab, point source, tol 1e-6)",
+            "instances": len(specs), "cells": cells, "steps": K, "warmup": W, "value": value, "unit": UNIT,
+            "ms_per_step": ms / K, "dtype": "f32", "magnetic_fraction": round(f, 4),
+            "effective_hbm_fraction": round((13 + 21 * f) * 4 * value / (peak * 1e9), 4),
+            "status_ok": ok, "iters_max": max(iters)}
 
 
 def ours_arm(args):
@@ -401,6 +493,7 @@ def ours_arm(args):
         with ClockSampler(local) as clk:
             sim32, ms32, prof32, stats32 = run_path(torch, mmx, w, mmx.FP32, path, K, W, stream, dist)
         clocks = clk.summary()
+        info32 = sim32.get_info()
         roof, lps = roofline_of(prof32, K, w, 4, peak, peak_kind)
         sim64, ms64, prof64, stats64 = run_path(torch, mmx, w, mmx.FP64, path, K, W, stream, dist)
         roof64, _ = roofline_of(prof64, K, w, 8, peak, peak_kind)
@@ -415,17 +508,25 @@ def ours_arm(args):
         acc = accuracy_leg(mmx, w, stream)
         acc16 = accuracy_leg(mmx, w, stream, checkpoints=(1000,), prec=mmx.FP16)
         e2e = e2e_leg(torch, mmx, w, mmx.FP32, path, K, stream)
+        stress = None if args.no_stress else stress_leg(torch, mmx, stream, peak)
+        sweep = None if args.no_sweep else sweep_leg(torch, mmx, stream, peak)
     value = whole_job_rate(w.ncells, world, K, ms32)
-    mag_frac = float(np.count_nonzero(w.Ms > 0)) / w.ncells
+    eff, mag_frac = effective_fraction(w, value / world, 4, peak)
+    if roof:
+        # the whole step against the same peak, beside the dominant kernel's
+        # own fraction: B_alg = (13 + 21 f) words per cell-update
+        roof["step_frac"] = eff
+        roof["step_alg_bytes_per_cell"] = round((13 + 21 * mag_frac) * 4, 2)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms32 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded workload generator; no dataset)",
         "config": config_block(w, "fp32", "fused" if path == mmx.PATH_FUSED else "plain"),
+        # the step-level fraction first: the whole coupled step's algorithmic
+        # bytes over its time; roofline.frac is the dominant kernel's own
+        "effective_hbm_fraction": eff,
         "roofline": roof,
-        # B_alg = (13 + 21 f) words per cell-update (E, H, eps_r in and E, H
-        # out everywhere; M, Ms, alpha, gamma in and M out on magnetic cells)
-        "effective_hbm_fraction": round((13 + 21 * mag_frac) * 4 * value / world / (peak * 1e9), 4),
+        "fused_kernel": info32["fused_kernel_name"], "tma_fallback": info32["tma_fallback"],
         "clocks": clocks,
         "gpu_launches": int(round(lps * K)) if lps else None,
         "e2e": e2e,
@@ -437,6 +538,8 @@ def ours_arm(args):
                          "vs_fp64_rel_l2_after_steps": acc16},
         "fp32_vs_fp64_rel_l2_after_steps": acc,
         "iters": {"min": stats32["iters_min"], "max": stats32["iters_max"]},
+        "stress_512": stress,
+        "bias_sweep_256": sweep,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
@@ -455,6 +558,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-stress", action="store_true", help="skip the 512^3 sub-record")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the 256-instance sweep sub-record")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

@@ -203,6 +203,52 @@ MMX_API int mmx_get_stats(mmx_ctx *ctx, mmx_stats *out);
  * earlier work is returned first, without the check. */
 MMX_API int mmx_check_bounded_wait(mmx_ctx *ctx);
 
+/* Failure-detection test hook (the failure is made on the host, no GPU
+ * fault): the next mmx_step call starts as if a bounded wait had given up in
+ * its first launch, with MMX_ERR_TIMEOUT latched in the device status word
+ * and the grid-barrier arrival counter one arrival ahead.  Every launch of
+ * that call then returns at its entry instead of spending a wait budget at
+ * each barrier, and the next synchronising call returns MMX_ERR_TIMEOUT and
+ * resets the barrier words (the fields are then void).  Returns MMX_OK. */
+MMX_API int mmx_inject_timeout(mmx_ctx *ctx);
+
+/* Which kernels the fused path runs.
+ *   fused_kernel        kernel of the last fused step: 0 none yet (or the
+ *                       per-update path), 1 the one-column kernel (periodic x
+ *                       or y, or a magnetic box reaching into the PML), 2 the
+ *                       vectorised kernel with per-lane cp.async staging, 3
+ *                       the vectorised kernel with bulk tensor copies (TMA).
+ *   tma_fallback        1 if the bulk-copy staging applies (FP32 storage, no
+ *                       sigma or mu_r, allowed by mmx_set_fused_staging) but
+ *                       could not be set up (tensor-map encoding or its shared
+ *                       memory), so the cp.async staging runs instead.
+ *   bulk_staging        the setting of mmx_set_fused_staging (1 by default).
+ *   box_blocks          blocks of the cooperative H/M launch (0: no magnetic
+ *                       material).
+ *   box_faces_magnetic, box_faces_other   faces of the magnetic box with and
+ *                       without Ms > 0. */
+typedef struct {
+    int fused_kernel;
+    int tma_fallback;
+    int bulk_staging;
+    int box_blocks;
+    long long box_faces_magnetic;
+    long long box_faces_other;
+} mmx_info;
+MMX_API int mmx_get_info(mmx_ctx *ctx, mmx_info *out);
+
+/* Staging of the vectorised fused kernel: bulk = 1 (default) stages the planes
+ * with bulk tensor copies where they apply, bulk = 0 always with per-lane
+ * cp.async copies.  Both compute the same updates; the switch exists to
+ * compare them.  Takes effect at the next mmx_step.  MMX_ERR_INVALID for any
+ * other value. */
+MMX_API int mmx_set_fused_staging(mmx_ctx *ctx, int bulk);
+
+/* The SM architecture the library's kernels were compiled for, as the CUDA
+ * runtime reports it for the current device (major * 10 + minor: 103 for
+ * sm_103a), or MMX_ERR_CUDA if the kernels cannot run on it. */
+MMX_API int mmx_kernel_binary_version(void);
+
 /* Iteration count of each H/M half step, oldest first (up to cap entries of
  * the most recent 65536 half steps).  Returns the number written (>= 0) or a
  * negative error.  Synchronises. */
@@ -340,7 +386,7 @@ MMX_API int mmx_batch_destroy(mmx_batch *b);
  * callers that cannot call cudaMalloc: code whose device memory is all owned
  * by its own arena or pool, or that runs where an allocation (which may
  * synchronise the device) is not acceptable.  The paper has no counterpart;
- * the computation is the one mmx_get_material reads back (Sec. 3.1 means).
+ * the computation is the one mmx_get_material reads back.
  *   desc       only n[3] and bc[3] are used.
  *   location   0-2: mean over the edges of Ex, Ey, Ez (up to 4 cells);
  *              3-5: mean over the x, y, z faces (2 cells).
@@ -349,12 +395,15 @@ MMX_API int mmx_batch_destroy(mmx_batch *b);
  *   cuda_stream  cudaStream_t of the two kernel launches (NULL = default).
  * The padded intermediate lives in a fixed 8 MiB device array inside the
  * library (1,048,576 doubles; every GPU that loads the library holds it until
- * exit): grids with (round_up(nx+1, 8))(ny+1)(nz+1) > 1,048,576 return
- * MMX_ERR_INVALID, as do bad arguments; MMX_ERR_CUDA reports a failed launch.
+ * exit): grids with (round_up(nx+1, 8))(ny+1)(nz+1) > 1,048,576 or with
+ * nz + 1 > 65535 return MMX_ERR_INVALID, as do bad arguments; MMX_ERR_CUDA
+ * reports a failed launch of this call.
  * The first call on a device looks up that array's device address, so make it
- * before any stream capture.  All calls share the array: calls whose kernels
- * overlap on the GPU (other streams, other threads) race.  Asynchronous: the
- * result is ready when the stream has finished. */
+ * before any stream capture; a call after the device's context was destroyed
+ * and re-created (cudaDeviceReset) looks it up again.  All calls share the
+ * array: calls whose kernels overlap on the GPU (other streams, other
+ * threads) race.  Asynchronous: the result is ready when the stream has
+ * finished. */
 MMX_API int mmx_material_average_noalloc(const mmx_grid_desc *desc, int location, const double *cell,
                                          double *out, long long n, void *cuda_stream);
 

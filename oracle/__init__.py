@@ -24,7 +24,9 @@ _libs = {}
 # Build variants: "" is the oracle; "literal" evaluates Eq. iterate_H as
 # printed in FP64 (ORC_LITERAL_ITERATE_H), used only to bound the effect of
 # readings R13/R14 in a test.
-_VARIANTS = {"": [], "literal": ["-DORC_LITERAL_ITERATE_H=1"]}
+# "omp" parallelises the loops over z planes and magnetic faces with OpenMP,
+# bit-identical to "" and used only to time the oracle on all host cores.
+_VARIANTS = {"": [], "literal": ["-DORC_LITERAL_ITERATE_H=1"], "omp": ["-fopenmp"]}
 
 ERR_NAMES = {0: "OK", -1: "INVALID", -2: "OOM", -4: "NOT_CONVERGED", -5: "NONFINITE"}
 

@@ -42,6 +42,16 @@ class Stats(ctypes.Structure):
                 ("last_residual", ctypes.c_double), ("status", ctypes.c_int)]
 
 
+class Info(ctypes.Structure):
+    _fields_ = [("fused_kernel", ctypes.c_int), ("tma_fallback", ctypes.c_int),
+                ("bulk_staging", ctypes.c_int), ("box_blocks", ctypes.c_int),
+                ("box_faces_magnetic", ctypes.c_longlong), ("box_faces_other", ctypes.c_longlong)]
+
+
+# mmx_info.fused_kernel -> kernel name
+FUSED_KERNELS = {0: "none", 1: "k_fused", 2: "k_fused_vec", 3: "k_fused_vec_tma"}
+
+
 class KernelProfile(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong),
                 ("total_ms", ctypes.c_double)]
@@ -50,6 +60,7 @@ class KernelProfile(ctypes.Structure):
 EXPORTS = ("mmx_create", "mmx_set_materials", "mmx_set_bias", "mmx_set_M_cells", "mmx_set_field",
            "mmx_get_field", "mmx_get_material", "mmx_add_source", "mmx_set_path", "mmx_step",
            "mmx_sync", "mmx_get_stats", "mmx_get_iter_log", "mmx_get_field_device", "mmx_check_bounded_wait",
+           "mmx_inject_timeout", "mmx_get_info", "mmx_set_fused_staging", "mmx_kernel_binary_version",
            "mmx_flux_gradient", "mmx_set_storage_scale", "mmx_add_probe", "mmx_get_probes", "mmx_energy", "mmx_add_flux_plane", "mmx_get_flux",
            "mmx_set_profiling", "mmx_get_profile",
            "mmx_batch_create", "mmx_batch_set_planes", "mmx_batch_step", "mmx_batch_sync",
@@ -101,6 +112,14 @@ def lib():
     L.mmx_set_profiling.argtypes = [P, I]
     L.mmx_check_bounded_wait.restype = I
     L.mmx_check_bounded_wait.argtypes = [P]
+    L.mmx_inject_timeout.restype = I
+    L.mmx_inject_timeout.argtypes = [P]
+    L.mmx_get_info.restype = I
+    L.mmx_get_info.argtypes = [P, ctypes.POINTER(Info)]
+    L.mmx_set_fused_staging.restype = I
+    L.mmx_set_fused_staging.argtypes = [P, I]
+    L.mmx_kernel_binary_version.restype = I
+    L.mmx_kernel_binary_version.argtypes = []
     L.mmx_flux_gradient.restype = I
     L.mmx_flux_gradient.argtypes = [P, I, I, I, dp, dp, dp]
     L.mmx_set_storage_scale.restype = I
@@ -276,6 +295,24 @@ class Solver:
         -6 (TIMEOUT) when both bounded waits gave up as designed."""
         return self._L.mmx_check_bounded_wait(self._h)
 
+    def inject_timeout(self):
+        """Test hook: the next step call starts as if a bounded wait had given
+        up (mmx_inject_timeout)."""
+        self._check(self._L.mmx_inject_timeout(self._h), "mmx_inject_timeout")
+
+    def get_info(self):
+        """Which kernels the fused path runs (mmx_get_info) as a dict; adds
+        ``fused_kernel_name``."""
+        i = Info()
+        self._check(self._L.mmx_get_info(self._h, ctypes.byref(i)), "mmx_get_info")
+        d = {k: getattr(i, k) for k, _ in Info._fields_}
+        d["fused_kernel_name"] = FUSED_KERNELS.get(d["fused_kernel"], "?")
+        return d
+
+    def set_fused_staging(self, bulk):
+        """1: bulk tensor copies where they apply (default); 0: per-lane cp.async."""
+        self._check(self._L.mmx_set_fused_staging(self._h, 1 if bulk else 0), "mmx_set_fused_staging")
+
     def get_stats(self):
         s = Stats()
         self._check(self._L.mmx_get_stats(self._h, ctypes.byref(s)), "mmx_get_stats")
@@ -355,6 +392,11 @@ class Solver:
 
     def last_error(self):
         return self._L.mmx_last_error(self._h).decode()
+
+
+def kernel_binary_version() -> int:
+    """SM version the kernels were built for on the current device (103)."""
+    return int(lib().mmx_kernel_binary_version())
 
 
 def material_average_noalloc(n, bc, location, cell_ptr, out_ptr, count, stream=None) -> int:

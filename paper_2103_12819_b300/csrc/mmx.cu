@@ -26,10 +26,14 @@ namespace {
 
 // Kernel kinds timed by the optional profiler.
 enum KernelKind {
-    KK_HM_BOX = 0, KK_H_UPDATE, KK_E_UPDATE, KK_HARD, KK_FUSED, KK_FUSED_VEC, KK_ZERO_WALLS, KK_M_SYNC, KK_COUNT
+    KK_HM_BOX = 0, KK_H_UPDATE, KK_E_UPDATE, KK_HARD, KK_FUSED, KK_FUSED_VEC, KK_FUSED_VEC_TMA, KK_ZERO_WALLS,
+    KK_M_SYNC, KK_COUNT
 };
-const char *const kKernelNames[KK_COUNT] = {"hm_box",   "h_update",     "e_update",   "hard_source",
-                                            "fused_eh", "fused_eh_vec", "zero_walls", "box_m_sync"};
+// fused_eh_vec is k_fused_vec (per-lane cp.async staging), fused_eh_vec_tma
+// k_fused_vec_tma (bulk tensor copies); fused_eh the one-column kernel
+const char *const kKernelNames[KK_COUNT] = {"hm_box",       "h_update",         "e_update",
+                                            "hard_source",  "fused_eh",         "fused_eh_vec",
+                                            "fused_eh_vec_tma", "zero_walls",   "box_m_sync"};
 
 struct ProfRec {
     int kind;
@@ -65,6 +69,10 @@ struct mmx_ctx {
     // 0 not used, 1 used; one map set per E/H ping-pong parity, keyed by the
     // H array it reads
     int vec_tma = -1;
+    int bulk_staging = 1;    // caller's choice (mmx_set_fused_staging)
+    int tma_fallback = 0;    // 1: bulk copies apply but their set-up failed
+    int last_fused = 0;      // kernel of the last fused step (mmx_info.fused_kernel)
+    bool inject_timeout = false;   // test hook: see mmx_inject_timeout
     VecMaps vmaps[2];
     void *vmap_key[2] = {};
     // coefficients
@@ -885,8 +893,10 @@ template <typename T, typename S> static int plan_vec(mmx_ctx *ctx)
     ctx->vec_xstride = xs;
     ctx->vec_grid = dim3(ntx, nty, plan_zchunks(ctx, (n[2] + chunk - 1) / chunk));
     ctx->vec_tma = 0;
+    ctx->tma_fallback = 0;
     if constexpr (std::is_same<T, float>::value && std::is_same<S, float>::value) {
-        if (MMX_VEC_TMA && !(ctx->any_sigma || ctx->any_mu) && ctx->epsc && encode_vec_maps(ctx)) {
+        const bool applies = MMX_VEC_TMA && ctx->bulk_staging && !(ctx->any_sigma || ctx->any_mu) && ctx->epsc;
+        if (applies && encode_vec_maps(ctx)) {
             cudaError_t r[4] = {set_vec_tma_smem_v<T, S, 1, false>(), set_vec_tma_smem_v<T, S, 1, true>(),
                                 set_vec_tma_smem_v<T, S, 2, false>(), set_vec_tma_smem_v<T, S, 2, true>()};
             bool ok = true;
@@ -899,6 +909,8 @@ template <typename T, typename S> static int plan_vec(mmx_ctx *ctx)
                 ctx->vec_tma = 1;
             cudaGetLastError();
         }
+        // recorded, so that the caller (mmx_get_info) sees which staging runs
+        if (applies && ctx->vec_tma != 1) ctx->tma_fallback = 1;
     }
     return MMX_OK;
 }
@@ -1016,7 +1028,11 @@ template <typename T, typename S = T> static int step_fused(mmx_ctx *ctx, int ns
         Ptr3<S> Hn = {{(S *)ctx->Halt[0], (S *)ctx->Halt[1], (S *)ctx->Halt[2]}};
         Ptr3<S> Zo = {{(S *)ctx->Ezp[0], (S *)ctx->Ezp[1], nullptr}};
         Ptr3<S> Zn = {{(S *)ctx->Ezpalt[0], (S *)ctx->Ezpalt[1], nullptr}};
-        prof_begin(ctx, vec ? KK_FUSED_VEC : KK_FUSED);
+        // the same test launch_vec_v applies
+        const bool tma = vec && ctx->vec_tma == 1 && std::is_same<T, float>::value &&
+                         std::is_same<S, float>::value && !(ctx->any_sigma || ctx->any_mu);
+        ctx->last_fused = vec ? (tma ? 3 : 2) : 1;
+        prof_begin(ctx, vec ? (tma ? KK_FUSED_VEC_TMA : KK_FUSED_VEC) : KK_FUSED);
         if (vec) {
             FusedIO<S> io;
             for (int a = 0; a < 3; a++) {
@@ -1165,7 +1181,10 @@ static int read_status(mmx_ctx *ctx)
         CK(cudaStreamSynchronize(ctx->stream));
     }
     if (w & kErrTimeout) {
+        // launches after the timeout returned at entry without clearing the
+        // residual and decision rows of the next launch's parity: clear all
         CK(cudaMemsetAsync(ctx->bar, 0, kBarWords * sizeof(unsigned long long), ctx->stream));
+        CK(cudaMemsetAsync(ctx->res, 0, 2 * kVoteRows * (kMaxIter + 1) * sizeof(unsigned long long), ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         return fail(ctx, MMX_ERR_TIMEOUT, "a device-side wait gave up");
     }
@@ -1905,6 +1924,16 @@ int mmx_step(mmx_ctx *ctx, int nsteps)
     if (!ctx || !ctx->E[0] || nsteps < 0) return MMX_ERR_INVALID;
     if (nsteps == 0) return MMX_OK;
     CK(cudaMemsetAsync(ctx->bar, 0, kBarWords * sizeof(unsigned long long), ctx->stream));
+    if (ctx->inject_timeout) {
+        // the state a bounded wait leaves when it gives up at the start of
+        // this call: the timeout latched, the arrival counter one ahead
+        ctx->inject_timeout = false;
+        const int e = kErrTimeout;
+        const unsigned long long one = 1;
+        CK(cudaMemcpyAsync(ctx->errw, &e, sizeof e, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->bar, &one, sizeof one, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
     bool hard = false;
     for (auto &q : ctx->src) hard |= q.kind >= 2;
     const bool fp64 = is_fp64(ctx);
@@ -1947,6 +1976,47 @@ int mmx_check_bounded_wait(mmx_ctx *ctx)
         if (rc != MMX_ERR_TIMEOUT) return rc;
     }
     return rc;
+}
+
+int mmx_inject_timeout(mmx_ctx *ctx)
+{
+    if (!ctx || !ctx->E[0]) return MMX_ERR_INVALID;
+    ctx->inject_timeout = true;
+    return MMX_OK;
+}
+
+int mmx_set_fused_staging(mmx_ctx *ctx, int bulk)
+{
+    if (!ctx || !ctx->E[0] || (bulk != 0 && bulk != 1)) return MMX_ERR_INVALID;
+    if (ctx->bulk_staging != bulk) {
+        ctx->bulk_staging = bulk;
+        ctx->vec_chunk = 0;     // plan the vectorised pass again at the next step
+    }
+    return MMX_OK;
+}
+
+int mmx_get_info(mmx_ctx *ctx, mmx_info *out)
+{
+    if (!ctx || !ctx->E[0] || !out) return MMX_ERR_INVALID;
+    memset(out, 0, sizeof *out);
+    out->fused_kernel = ctx->last_fused;
+    out->tma_fallback = ctx->tma_fallback;
+    out->bulk_staging = ctx->bulk_staging;
+    out->box_blocks = ctx->magnetic ? ctx->coop_blocks : 0;
+    out->box_faces_magnetic = ctx->magnetic ? ctx->nmag : 0;
+    out->box_faces_other = ctx->magnetic ? ctx->nnon : 0;
+    return MMX_OK;
+}
+
+int mmx_kernel_binary_version(void)
+{
+    cudaFuncAttributes a;
+    constexpr int BY = VecRows<float>::value, ST = VecStages<float, false>::value;
+    if (cudaFuncGetAttributes(&a, k_fused_vec_tma<float, float, BY, ST, 2, true, false>) != cudaSuccess) {
+        cudaGetLastError();
+        return MMX_ERR_CUDA;
+    }
+    return a.binaryVersion;
 }
 
 int mmx_get_stats(mmx_ctx *ctx, mmx_stats *out)
@@ -2679,19 +2749,45 @@ namespace {
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 double *g_noalloc_dev_ptr[kNoAllocMaxDevices] = {};
+CUcontext g_noalloc_ctx[kNoAllocMaxDevices] = {};
 
-// Device address of the scratch array on the current device (set up on the
-// first call for that device).
+// The CUDA context current on the calling thread (driver entry point, so
+// the library needs no link against the driver library); null if unknown.
+CUcontext current_context()
+{
+    using Fn = CUresult (*)(CUcontext *);
+    static Fn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (Fn)p;
+    });
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
+
+// Device address of the scratch array on the current device.  It is looked
+// up on the first call for that device, and again whenever the device's
+// context has changed since (after cudaDeviceReset the runtime creates a new
+// primary context, and the array gets a new address in it).
 int noalloc_scratch(double **out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return MMX_ERR_CUDA;
     if (dev < 0 || dev >= kNoAllocMaxDevices) return MMX_ERR_INVALID;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_dev_ptr[dev]) {
+    // cudaGetSymbolAddress makes the device's primary context current if no
+    // context is yet, so the context is read after it on a first call
+    const CUcontext before = current_context();
+    if (!g_noalloc_dev_ptr[dev] || !before || before != g_noalloc_ctx[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MMX_ERR_CUDA;
         g_noalloc_dev_ptr[dev] = (double *)p;
+        g_noalloc_ctx[dev] = current_context();
     }
     *out = g_noalloc_dev_ptr[dev];
     return MMX_OK;
@@ -2712,6 +2808,7 @@ extern "C" int mmx_material_average_noalloc(const mmx_grid_desc *desc, int locat
     long long X = ((long long)desc->n[0] + 1 + 7) / 8 * 8;
     long long padded = X * (desc->n[1] + 1LL) * (desc->n[2] + 1LL);
     if (padded > (long long)kNoAllocMaxElems) return MMX_ERR_INVALID;   // grid too large for the scratch
+    if (desc->n[2] + 1 > 65535) return MMX_ERR_INVALID;                  // one launch row per z node
     g.X = (int)X;
     g.Y = desc->n[1] + 1;
     const int c = location % 3, kind = location < 3 ? 0 : 1;
@@ -2722,6 +2819,9 @@ extern "C" int mmx_material_average_noalloc(const mmx_grid_desc *desc, int locat
     int rc = noalloc_scratch(&scratch);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    // clear an earlier, unrelated launch error so that the checks below see
+    // only this call's launches
+    cudaGetLastError();
     dim3 B(32, 8, 1), G((desc->n[0] + 1 + 31) / 32, (desc->n[1] + 1 + 7) / 8, desc->n[2] + 1);
     // every scratch element the gather reads is written by k_mean first, so
     // nothing has to be cleared between calls

@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(256, BoxMinBlocks<T>::value)
                    const int *__restrict__ non_inst, int nnon, unsigned long long *res, unsigned long long *bar,
                    int *berr, int nsub, int slot)
 {
+    if (timeout_latched(berr)) return;   // see k_hm_box
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BatchShared sh;
     sh.res = reinterpret_cast<unsigned long long *>(smem_raw);

@@ -323,6 +323,7 @@ template <typename T, typename S, int BY, bool GEN, int ST, bool TMA = false> st
     // every plane keeps a warp from writing plane k+1's meanwhile; three in
     // the TMA variant, which has no such barrier
     static constexpr int NEZ = TMA ? 3 : 2;
+    static_assert(!TMA || NEZ >= 3, "one barrier per plane needs three Ez exchange buffers");
     static constexpr size_t ez = ex + al((size_t)2 * R * W * sizeof(T));
     static constexpr size_t eu = ez + al((size_t)NEZ * R * W * sizeof(T));
     static constexpr size_t el = eu + (CBF && !TMA ? al((size_t)ST * W * sizeof(T)) : 0);
@@ -804,7 +805,20 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
                 }
             }
         }
-        __syncthreads();          // E^(n+1) of plane k visible to the row above
+        // E^(n+1) of plane k visible to the row above.  In the TMA variant
+        // this is the only block barrier of a plane, so a warp can run at
+        // most one plane ahead of the slowest warp (it cannot pass the next
+        // plane's barrier before every warp has arrived at it).  Under that
+        // bound: (1) the refill of stage st below is safe, since every read
+        // of stage st precedes this barrier and the H part after it reads
+        // registers, the SEx/SEz exchange rows and lane-0 halos only (the
+        // halos are read by the warp that copied them, after its own
+        // cp_wait); (2) SEx rows of planes k and k-1 (b and b^1) suffice, as
+        // a warp writing plane k+1's rows waits at plane k+1's barrier
+        // before anyone reads them, while a slower warp may still read plane
+        // k-1's SEz rows after plane k's barrier: hence three SEz buffers
+        // (NEZ) for the variant without a top-of-plane barrier.
+        __syncthreads();
         if constexpr (TMA) {
             // every thread has read stage st (all its reads precede the
             // barrier above): plane k+ST into it, half a plane earlier than
@@ -987,6 +1001,7 @@ __global__ void __launch_bounds__(32 * (BY + 1), (VecMinBlocks<T, S, BY, ST, GEN
                 const __grid_constant__ FusedIO<S> io, const Src<T> *__restrict__ src, int nsrc,
                 const __grid_constant__ ZChunks zc, int xstride)
 {
+    if (timeout_latched(f.err)) return;   // the state is already void; see k_hm_box
     fused_vec_body<T, S, BY, ST, NH, PMLK, GEN>(g, f, io, src, nsrc, f.src_amp, zc.b[blockIdx.z],
                                                 zc.b[blockIdx.z + 1], xstride, blockIdx.x, blockIdx.y);
 }
@@ -1001,6 +1016,7 @@ __global__ void __launch_bounds__(32 * (BY + 1), (VecMinBlocks<T, S, BY, ST, GEN
                     const __grid_constant__ FusedIO<S> io, const __grid_constant__ VecMaps maps,
                     const Src<T> *__restrict__ src, int nsrc, const __grid_constant__ ZChunks zc, int xstride)
 {
+    if (timeout_latched(f.err)) return;
     fused_vec_body<T, S, BY, ST, NH, PMLK, GEN, true>(g, f, io, src, nsrc, f.src_amp, zc.b[blockIdx.z],
                                                       zc.b[blockIdx.z + 1], xstride, blockIdx.x, blockIdx.y, &maps);
 }

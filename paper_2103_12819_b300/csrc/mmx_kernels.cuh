@@ -403,6 +403,14 @@ __global__ void k_hard(const Geo g, Ptr3<T> F, const Src<T> *__restrict__ src, i
 // (A two-level arrival over 16 group counters measured slower: the last
 // block then makes two dependent atomic round trips.)
 constexpr int kBarWords = 2;   // u64 words: the barrier's count, a probe's decision word
+
+// True once a bounded wait has latched kErrTimeout in the status word (read
+// at kernel entry, before any barrier; the word only changes between
+// launches except through this launch's own timeouts).
+__device__ __forceinline__ bool timeout_latched(const int *err)
+{
+    return (*(const volatile int *)err & kErrTimeout) != 0;
+}
 constexpr int kVoteRows = 4;   // decision words sit this many residual rows past them
 
 __device__ __forceinline__ bool grid_barrier(unsigned long long *bar, int *err)
@@ -862,6 +870,11 @@ __global__ void __launch_bounds__(256, BoxMinBlocks<T>::value) k_hm_box(const __
                                                 const __grid_constant__ Ptr3<S> Hout, int nsub, int slot)
 {
     const int W = kMaxIter + 1;
+    // a bounded wait that gave up earlier in this mmx_step call left the
+    // barrier counter out of step: every later launch of the call returns at
+    // once instead of spending its wait budget at each barrier (the host
+    // reads the latched timeout and resets the counter)
+    if (timeout_latched(b.err)) return;
     if (blockIdx.x == 0) {
         unsigned long long *other = b.res + 2 * (1 - slot) * W;
         for (int r = threadIdx.x; r < 2 * W; r += blockDim.x) {

@@ -1,0 +1,194 @@
+"""The headline kernels checked directly against the FP64 CPU oracle, and the
+identity of the kernel that ran asserted through mmx_get_info and the
+per-kernel profile:
+
+  * the FP32 fused pass with bulk tensor copies (k_fused_vec_tma) on a
+    reduced waveguide carrying every feature of the benchmark workload
+    (z-PML, TE10 plane source, YIG slab), and the same pass with per-lane
+    cp.async staging, which must agree with it;
+  * FP16 storage and batched instances against the oracle (not only against
+    the GPU's own FP64 or standalone runs);
+  * FP32 and FP64 take the same iteration counts on the full waveguide,
+    although FP32 reduces its residual in FP32;
+  * the library's kernels are sm_103 code on this device;
+  * a timeout latched early in a step call makes every later launch of the
+    call return at once.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2103_12819_b300 as mmx
+import workloads as W
+from conftest import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+_SPLIT_PARENT = {15: 0, 16: 1, 17: 3, 18: 4}
+
+
+def _err(sim, ref, fid):
+    """Relative L2 error of field fid; the PML split parts (15-18) against
+    the norm of the component they belong to."""
+    a, b = sim.get_field(fid), ref.get_field(fid)
+    if fid in _SPLIT_PARENT:
+        scale = np.linalg.norm(ref.get_field(_SPLIT_PARENT[fid]))
+        return float(np.linalg.norm(a - b) / scale)
+    return rel_l2(a, b)
+
+
+@pytest.fixture(scope="module")
+def reduced_waveguide():
+    """128x32x96 cells (one 128-column strip, as the full guide), 10-cell
+    z-PML, TE10 plane at z node 12, YIG slab x 32-95, y 14-17, z 37-58; 300
+    steps of the oracle (about 20 s)."""
+    w = W.waveguide(n=(128, 32, 96), steps=300)
+    ref = oracle.from_workload(w)
+    ref.step(w.steps)
+    return w, ref
+
+
+def _fp32_run(w, bulk):
+    s = mmx.from_workload(w, prec=mmx.FP32, path=mmx.PATH_FUSED)
+    s.set_fused_staging(bulk)
+    s.set_profiling(True)
+    s.step(w.steps)
+    assert s.sync(check=False) == 0, s.last_error()
+    return s
+
+
+# FP32 against the FP64 oracle after 300 steps of the reduced waveguide:
+# E, H, M per component, and the PML split parts against their component.
+FP32_TOL = {"E": 1e-4, "H": 1e-4, "M": 1e-4, "PML": 1e-3}
+
+
+def _group(fid):
+    return "E" if fid < 3 else "H" if fid < 6 else "M" if fid < 15 else "PML"
+
+
+def test_fp32_bulk_copy_pass_against_oracle(reduced_waveguide):
+    w, ref = reduced_waveguide
+    s = _fp32_run(w, 1)
+    info = s.get_info()
+    assert info["fused_kernel_name"] == "k_fused_vec_tma" and info["tma_fallback"] == 0, info
+    prof = s.get_profile()
+    assert "fused_eh_vec_tma" in prof and "fused_eh_vec" not in prof, prof
+    errs = {fid: _err(s, ref, fid) for fid in range(19)}
+    print("FP32 bulk-copy pass vs oracle, 128x32x96 guide, 300 steps:",
+          {k: "%.2e" % v for k, v in errs.items()})
+    for fid, e in errs.items():
+        assert e <= FP32_TOL[_group(fid)], (fid, e)
+    np.testing.assert_array_equal(s.get_iter_log(), ref.iter_log())
+
+
+def test_cp_async_pass_agrees_with_bulk_copy_pass(reduced_waveguide):
+    """The two stagings of the vectorised pass on PML and source planes,
+    where the warps of a CTA drift furthest apart: both against the oracle,
+    and against each other to FP32 rounding."""
+    w, ref = reduced_waveguide
+    a = _fp32_run(w, 1)
+    b = _fp32_run(w, 0)
+    assert a.get_info()["fused_kernel"] == 3 and b.get_info()["fused_kernel"] == 2
+    assert "fused_eh_vec" in b.get_profile()
+    diffs = {}
+    for fid in range(19):
+        diffs[fid] = _err(b, a, fid)
+        assert _err(b, ref, fid) <= FP32_TOL[_group(fid)], fid
+    print("cp.async vs bulk-copy staging:", {k: "%.1e" % v for k, v in diffs.items()})
+    assert max(diffs.values()) <= 1e-5, diffs
+
+
+def test_fp16_storage_against_oracle():
+    """FP16 storage (FP32 arithmetic) on a 32x24x96 guide (z-PML, slab, TE10
+    drive) against the oracle after 300 steps: the error is FP16's, stated
+    per vector field (E as a whole: Ex, Ez of a TE10 guide are near zero)."""
+    w = W.waveguide(n=(32, 24, 96), steps=300)
+    ref = oracle.from_workload(w)
+    ref.step(w.steps)
+    s = mmx.from_workload(w, prec=mmx.FP16, path=mmx.PATH_FUSED)
+    s.step(w.steps)
+    assert s.sync(check=False) == 0, s.last_error()
+    assert s.get_info()["fused_kernel"] == 2
+    sq = {"E": [0.0, 0.0], "H": [0.0, 0.0], "M": [0.0, 0.0]}
+    for fid in range(15):
+        x, y = s.get_field(fid), ref.get_field(fid)
+        g = _group(fid)
+        sq[g][0] += float(np.sum((x - y) ** 2))
+        sq[g][1] += float(np.sum(y ** 2))
+    errs = {g: (e2 / n2) ** 0.5 for g, (e2, n2) in sq.items()}
+    print("FP16 storage vs oracle, 32x24x96 guide, 300 steps:", {k: "%.2e" % v for k, v in errs.items()})
+    assert errs["E"] < 2e-2 and errs["H"] < 5e-3 and errs["M"] < 2e-3, errs
+
+
+@pytest.mark.parametrize("prec,tol", [(mmx.FP64, 1e-12), (mmx.FP32, 1e-4)], ids=["fp64", "fp32"])
+def test_batched_instances_against_oracle(prec, tol):
+    """Instances of different sizes and biases (and one without magnetic
+    material) stepped together by the batched launches, each against its own
+    oracle run: FP64 to the 1e-12 parity bar with identical iteration counts,
+    FP32 to its rounding."""
+    ws = [W.tunable_filter(32, 8.0e4, steps=40, seed=1), W.tunable_filter(48, 1.9e5, steps=40, seed=2),
+          W.tunable_filter(24, 6.0e4, steps=40, seed=4)]
+    plain = W.tunable_filter(20, 1.0e5, steps=40, seed=5)
+    plain.Ms = np.zeros_like(plain.Ms)
+    plain.m_cells = None
+    ws.append(plain)
+    sols = [mmx.from_workload(w, prec=prec) for w in ws]
+    b = mmx.Batch(sols)
+    b.step(25)
+    b.step(15)
+    assert b.sync(check=False) == 0
+    for q, (w, s) in enumerate(zip(ws, sols)):
+        ref = oracle.from_workload(w)
+        ref.step(40)
+        for fid in range(15):
+            a, r = s.get_field(fid), ref.get_field(fid)
+            e = rel_l2(a, r) if np.linalg.norm(r) > 0 else float(np.abs(a).max())
+            assert e <= tol, (q, fid, e)
+        if prec == mmx.FP64:
+            np.testing.assert_array_equal(s.get_iter_log(), ref.iter_log())
+        ref.close()
+    b.close()
+
+
+def test_fp32_and_fp64_iteration_counts_agree_on_the_waveguide():
+    """The FP32 path reduces its residual in FP32 and compares it with tol in
+    FP64; on the full 128x128x512 waveguide (tol 1e-6) every half step of 300
+    steps stops at the same iteration as in FP64."""
+    w = W.waveguide(steps=300)
+    logs = []
+    for prec in (mmx.FP64, mmx.FP32):
+        s = mmx.from_workload(w, prec=prec, path=mmx.PATH_FUSED)
+        s.step(300)
+        assert s.sync(check=False) == 0
+        logs.append(s.get_iter_log())
+        s.close()
+    assert len(logs[0]) == 600
+    np.testing.assert_array_equal(logs[0], logs[1])
+
+
+def test_kernels_are_sm103_code():
+    assert mmx.kernel_binary_version() == 103
+
+
+def test_latched_timeout_makes_later_launches_return_at_once():
+    """A bounded wait that gives up early in a step call leaves the barrier
+    counter out of step; every later launch of the call must return at its
+    entry (without the entry check each barrier of each later launch would
+    spend its ~1 s wait budget).  The host then reads MMX_ERR_TIMEOUT, the
+    barrier words are reset and the context works again."""
+    w = W.yig_slab_32(steps=4, n=16)
+    for prec in (mmx.FP64, mmx.FP32):
+        s = mmx.from_workload(w, prec=prec, path=mmx.PATH_FUSED)
+        s.step(1)
+        assert s.sync(check=False) == 0
+        s.inject_timeout()
+        t0 = time.perf_counter()
+        s.step(4)
+        rc = s.sync(check=False)
+        dt = time.perf_counter() - t0
+        assert rc == -6 and dt < 1.0, (rc, dt)
+        assert s.sync(check=False) == 0
+        assert s.check_bounded_wait() == -6          # the waits still work
+        s.close()

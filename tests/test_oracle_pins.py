@@ -1049,3 +1049,18 @@ def test_r13_r14_readings_move_results_at_rounding_level_only():
         assert rel_l2(b.get_field(fid), a.get_field(fid)) < bar, fid
     # the two builds are different programs: H differs above the 1e-12 bar
     assert max(rel_l2(b.get_field(f), a.get_field(f)) for f in (3, 4, 5)) > 1e-12
+
+
+def test_openmp_timing_build_is_bit_identical():
+    """The OpenMP build of the oracle (used only to time it on all host
+    cores) computes every element with the same operations and reduces the
+    residual with a max: fields and iteration counts equal the serial
+    build's bit for bit."""
+    w = W.waveguide(n=(24, 16, 40), steps=12)
+    a = oracle.from_workload(w)
+    b = oracle.from_workload(w, variant="omp")
+    a.step(12)
+    b.step(12)
+    for fid in range(19):
+        np.testing.assert_array_equal(a.get_field(fid), b.get_field(fid))
+    np.testing.assert_array_equal(a.iter_log(), b.iter_log())
