@@ -223,10 +223,17 @@ MMX_API int mmx_inject_timeout(mmx_ctx *ctx);
  *                       could not be set up (tensor-map encoding or its shared
  *                       memory), so the cp.async staging runs instead.
  *   bulk_staging        the setting of mmx_set_fused_staging (1 by default).
- *   box_blocks          blocks of the cooperative H/M launch (0: no magnetic
- *                       material).
+ *   box_blocks          blocks of the last cooperative H/M launch (0: no
+ *                       magnetic material).
  *   box_faces_magnetic, box_faces_other   faces of the magnetic box with and
- *                       without Ms > 0. */
+ *                       without Ms > 0.
+ *   box_kernel          kernel of the last H/M launch: 0 none yet, 1 the
+ *                       list-driven kernel (per-face records in global
+ *                       memory), 2 the kernel with the records in shared
+ *                       memory (see mmx_set_box_kernel).
+ *   box_resident_faces_per_thread   magnetic faces per thread of the
+ *                       shared-memory kernel (0: the box's magnetic faces do
+ *                       not fit in one resident wave, or FP64 arithmetic). */
 typedef struct {
     int fused_kernel;
     int tma_fallback;
@@ -234,8 +241,20 @@ typedef struct {
     int box_blocks;
     long long box_faces_magnetic;
     long long box_faces_other;
+    int box_kernel;
+    int box_resident_faces_per_thread;
 } mmx_info;
 MMX_API int mmx_get_info(mmx_ctx *ctx, mmx_info *out);
+
+/* Kernel of the H/M half steps.  resident = 1 (default): where the magnetic
+ * faces fit in the GPU's shared memory (FP32 arithmetic, at most 2 faces per
+ * thread over one resident wave of 256-thread blocks; about 0.37 M faces on
+ * a B300), every block keeps its faces' iteration records (M^n, beta, C',
+ * the current increment) in shared memory for the whole launch; elsewhere,
+ * and with resident = 0, the list-driven kernel keeps them in global memory.
+ * Both evaluate the same operations in the same order.  Takes effect at the
+ * next mmx_step; MMX_ERR_INVALID for any other value. */
+MMX_API int mmx_set_box_kernel(mmx_ctx *ctx, int resident);
 
 /* Staging of the vectorised fused kernel: bulk = 1 (default) stages the planes
  * with bulk tensor copies where they apply, bulk = 0 always with per-lane

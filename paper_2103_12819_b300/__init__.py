@@ -45,11 +45,14 @@ class Stats(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("fused_kernel", ctypes.c_int), ("tma_fallback", ctypes.c_int),
                 ("bulk_staging", ctypes.c_int), ("box_blocks", ctypes.c_int),
-                ("box_faces_magnetic", ctypes.c_longlong), ("box_faces_other", ctypes.c_longlong)]
+                ("box_faces_magnetic", ctypes.c_longlong), ("box_faces_other", ctypes.c_longlong),
+                ("box_kernel", ctypes.c_int), ("box_resident_faces_per_thread", ctypes.c_int)]
 
 
 # mmx_info.fused_kernel -> kernel name
 FUSED_KERNELS = {0: "none", 1: "k_fused", 2: "k_fused_vec", 3: "k_fused_vec_tma"}
+# mmx_info.box_kernel -> kernel name
+BOX_KERNELS = {0: "none", 1: "k_hm_box", 2: "k_hm_box_res"}
 
 
 class KernelProfile(ctypes.Structure):
@@ -61,6 +64,7 @@ EXPORTS = ("mmx_create", "mmx_set_materials", "mmx_set_bias", "mmx_set_M_cells",
            "mmx_get_field", "mmx_get_material", "mmx_add_source", "mmx_set_path", "mmx_step",
            "mmx_sync", "mmx_get_stats", "mmx_get_iter_log", "mmx_get_field_device", "mmx_check_bounded_wait",
            "mmx_inject_timeout", "mmx_get_info", "mmx_set_fused_staging", "mmx_kernel_binary_version",
+           "mmx_set_box_kernel",
            "mmx_flux_gradient", "mmx_set_storage_scale", "mmx_add_probe", "mmx_get_probes", "mmx_energy", "mmx_add_flux_plane", "mmx_get_flux",
            "mmx_set_profiling", "mmx_get_profile",
            "mmx_batch_create", "mmx_batch_set_planes", "mmx_batch_step", "mmx_batch_sync",
@@ -118,6 +122,8 @@ def lib():
     L.mmx_get_info.argtypes = [P, ctypes.POINTER(Info)]
     L.mmx_set_fused_staging.restype = I
     L.mmx_set_fused_staging.argtypes = [P, I]
+    L.mmx_set_box_kernel.restype = I
+    L.mmx_set_box_kernel.argtypes = [P, I]
     L.mmx_kernel_binary_version.restype = I
     L.mmx_kernel_binary_version.argtypes = []
     L.mmx_flux_gradient.restype = I
@@ -307,11 +313,16 @@ class Solver:
         self._check(self._L.mmx_get_info(self._h, ctypes.byref(i)), "mmx_get_info")
         d = {k: getattr(i, k) for k, _ in Info._fields_}
         d["fused_kernel_name"] = FUSED_KERNELS.get(d["fused_kernel"], "?")
+        d["box_kernel_name"] = BOX_KERNELS.get(d["box_kernel"], "?")
         return d
 
     def set_fused_staging(self, bulk):
         """1: bulk tensor copies where they apply (default); 0: per-lane cp.async."""
         self._check(self._L.mmx_set_fused_staging(self._h, 1 if bulk else 0), "mmx_set_fused_staging")
+
+    def set_box_kernel(self, resident):
+        """1: records in shared memory where they fit (default); 0: list-driven."""
+        self._check(self._L.mmx_set_box_kernel(self._h, 1 if resident else 0), "mmx_set_box_kernel")
 
     def get_stats(self):
         s = Stats()

@@ -16,6 +16,7 @@
 
 #include "mmx.h"
 #include "mmx_fused.cuh"
+#include "mmx_box_res.cuh"
 #include "mmx_monitor.cuh"
 #include "mmx_batch.cuh"
 #include "mmx_adjoint.cuh"
@@ -27,13 +28,14 @@ namespace {
 // Kernel kinds timed by the optional profiler.
 enum KernelKind {
     KK_HM_BOX = 0, KK_H_UPDATE, KK_E_UPDATE, KK_HARD, KK_FUSED, KK_FUSED_VEC, KK_FUSED_VEC_TMA, KK_ZERO_WALLS,
-    KK_M_SYNC, KK_COUNT
+    KK_M_SYNC, KK_HM_BOX_RES, KK_COUNT
 };
 // fused_eh_vec is k_fused_vec (per-lane cp.async staging), fused_eh_vec_tma
 // k_fused_vec_tma (bulk tensor copies); fused_eh the one-column kernel
 const char *const kKernelNames[KK_COUNT] = {"hm_box",       "h_update",         "e_update",
                                             "hard_source",  "fused_eh",         "fused_eh_vec",
-                                            "fused_eh_vec_tma", "zero_walls",   "box_m_sync"};
+                                            "fused_eh_vec_tma", "zero_walls",   "box_m_sync",
+                                            "hm_box_res"};
 
 struct ProfRec {
     int kind;
@@ -96,6 +98,11 @@ struct mmx_ctx {
     int4 *dmag = nullptr, *dnon = nullptr;
     int nmag = 0, nnon = 0;
     int coop_blocks = 0;
+    // H/M box kernel with the records in shared memory (k_hm_box_res): faces
+    // per thread (0: the magnetic faces do not fit, k_hm_box runs) and blocks
+    int res_faces = 0, res_blocks = 0;
+    int box_resident = 1;    // caller's choice (mmx_set_box_kernel)
+    int last_box = 0;        // kernel of the last box launch (mmx_info.box_kernel)
 
     // point probes of E: (field, padded index) per probe and a device table
     // of samples, one row of nprobe doubles per completed time step
@@ -155,6 +162,11 @@ static int fail(mmx_ctx *c, int code, const char *fmt, ...)
     }
     return code;
 }
+
+#define CK_RAW(call)                                                                              \
+    do {                                                                                          \
+        if ((call) != cudaSuccess) return MMX_ERR_CUDA;                                            \
+    } while (0)
 
 #define CK(call)                                                                                  \
     do {                                                                                          \
@@ -472,6 +484,14 @@ static int box_alloc(mmx_ctx *ctx, void **p)
     return rc;
 }
 
+template <typename T, typename S, int F> static int res_occupancy(int *per)
+{
+    const size_t sm = res_smem_bytes<T>(F);
+    CK_RAW(cudaFuncSetAttribute(k_hm_box_res<T, S, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    CK_RAW(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_hm_box_res<T, S, F>, kResThreads, sm));
+    return MMX_OK;
+}
+
 template <typename T, typename S = T> static int compute_coop(mmx_ctx *ctx)
 {
     int dev = 0, nsm = 0, per = 0;
@@ -482,6 +502,26 @@ template <typename T, typename S = T> static int compute_coop(mmx_ctx *ctx)
     long long need = (std::max(ctx->nmag, ctx->nnon) + 255) / 256;
     long long cap = (long long)per * nsm;
     ctx->coop_blocks = (int)std::max(1LL, std::min(need, cap));
+    // the records in shared memory: the fewest faces per thread (up to
+    // kResMaxF, FP32 arithmetic) with which one resident wave covers every
+    // magnetic face
+    ctx->res_faces = ctx->res_blocks = 0;
+    if constexpr (sizeof(T) == 4) {
+        for (int F = 1; F <= kResMaxF && ctx->nmag > 0; F++) {
+            int pr = 0;
+            int rc = F == 1 ? res_occupancy<T, S, 1>(&pr) : res_occupancy<T, S, 2>(&pr);
+            if (rc) {
+                cudaGetLastError();
+                break;
+            }
+            const long long blocks = ((long long)ctx->nmag + (long long)F * kResThreads - 1) / ((long long)F * kResThreads);
+            if (pr >= 1 && blocks <= (long long)pr * nsm) {
+                ctx->res_faces = F;
+                ctx->res_blocks = (int)blocks;
+                break;
+            }
+        }
+    }
     return MMX_OK;
 }
 
@@ -532,9 +572,25 @@ static int launch_box(mmx_ctx *ctx, const Fields<T, S> &f, const Box<T> &b, Ptr3
     int slot = ctx->box_slot;
     ctx->box_slot ^= 1;
     void *args[] = {(void *)&ctx->g, (void *)&f, (void *)&b, (void *)&Hout, (void *)&nsub, (void *)&slot};
-    prof_begin(ctx, KK_HM_BOX);
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_hm_box<T, S>, dim3(ctx->coop_blocks), dim3(256),
-                                                args, 0, ctx->stream);
+    cudaError_t e = cudaSuccess;
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {   // the resident kernel exists for FP32 arithmetic only
+        if (ctx->res_faces > 0 && ctx->box_resident) {
+            const void *fn =
+                ctx->res_faces == 1 ? (const void *)k_hm_box_res<T, S, 1> : (const void *)k_hm_box_res<T, S, 2>;
+            ctx->last_box = 2;
+            prof_begin(ctx, KK_HM_BOX_RES);
+            e = cudaLaunchCooperativeKernel(fn, dim3(ctx->res_blocks), dim3(kResThreads), args,
+                                            res_smem_bytes<T>(ctx->res_faces), ctx->stream);
+            done = true;
+        }
+    }
+    if (!done) {
+        ctx->last_box = 1;
+        prof_begin(ctx, KK_HM_BOX);
+        e = cudaLaunchCooperativeKernel((const void *)k_hm_box<T, S>, dim3(ctx->coop_blocks), dim3(256), args, 0,
+                                        ctx->stream);
+    }
     prof_end(ctx);
     CK(e);
     return MMX_OK;
@@ -1995,14 +2051,23 @@ int mmx_set_fused_staging(mmx_ctx *ctx, int bulk)
     return MMX_OK;
 }
 
+int mmx_set_box_kernel(mmx_ctx *ctx, int resident)
+{
+    if (!ctx || !ctx->E[0] || (resident != 0 && resident != 1)) return MMX_ERR_INVALID;
+    ctx->box_resident = resident;
+    return MMX_OK;
+}
+
 int mmx_get_info(mmx_ctx *ctx, mmx_info *out)
 {
     if (!ctx || !ctx->E[0] || !out) return MMX_ERR_INVALID;
     memset(out, 0, sizeof *out);
+    out->box_kernel = ctx->last_box;
+    out->box_resident_faces_per_thread = ctx->magnetic ? ctx->res_faces : 0;
     out->fused_kernel = ctx->last_fused;
     out->tma_fallback = ctx->tma_fallback;
     out->bulk_staging = ctx->bulk_staging;
-    out->box_blocks = ctx->magnetic ? ctx->coop_blocks : 0;
+    out->box_blocks = !ctx->magnetic ? 0 : ctx->last_box == 2 ? ctx->res_blocks : ctx->coop_blocks;
     out->box_faces_magnetic = ctx->magnetic ? ctx->nmag : 0;
     out->box_faces_other = ctx->magnetic ? ctx->nnon : 0;
     return MMX_OK;

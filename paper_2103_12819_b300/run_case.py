@@ -28,6 +28,8 @@ def main():
     ap.add_argument("--path", default="fused", choices=["fused", "plain"])
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--box", default="auto", choices=["auto", "list"],
+                    help="H/M kernel: records in shared memory where they fit (auto) or list-driven")
     a = ap.parse_args()
     if a.workload == "waveguide":
         w = workloads.waveguide()
@@ -38,6 +40,7 @@ def main():
     prec = {"fp32": mmx.FP32, "fp64": mmx.FP64, "fp16": mmx.FP16}[a.prec]
     path = mmx.PATH_FUSED if a.path == "fused" else mmx.PATH_PLAIN
     s = mmx.from_workload(w, prec=prec, path=path)
+    s.set_box_kernel(0 if a.box == "list" else 1)
     s.step(a.warmup)
     rc = s.sync(check=False)
     t0 = time.perf_counter()
@@ -45,7 +48,9 @@ def main():
     rc = rc or s.sync(check=False)
     dt = time.perf_counter() - t0
     st = s.get_stats()
+    info = s.get_info()
     print(json.dumps({"workload": w.name, "prec": a.prec, "path": a.path, "steps": a.steps,
+                      "fused_kernel": info["fused_kernel_name"], "box_kernel": info["box_kernel_name"],
                       "ms_per_step": 1e3 * dt / max(a.steps, 1),
                       "cell_updates_per_s": w.ncells * a.steps / dt, "status": rc,
                       "iters": [st["iters_min"], st["iters_max"]]}))

@@ -61,7 +61,10 @@ def _fp32_run(w, bulk):
 
 # FP32 against the FP64 oracle after 300 steps of the reduced waveguide:
 # E, H, M per component, and the PML split parts against their component.
-FP32_TOL = {"E": 1e-4, "H": 1e-4, "M": 1e-4, "PML": 1e-3}
+# Measured on a B300 (bulk-copy staging): E <= 7.6e-6 (Ex, the near-zero
+# component of a TE10 guide), H <= 1.4e-6, M <= 1.5e-6, the Ex PML part
+# 4.3e-5, the other parts <= 1.4e-6; the bars are about four times that.
+FP32_TOL = {"E": 3e-5, "H": 6e-6, "M": 6e-6, "PML": 2e-4}
 
 
 def _group(fid):
@@ -97,7 +100,10 @@ def test_cp_async_pass_agrees_with_bulk_copy_pass(reduced_waveguide):
         diffs[fid] = _err(b, a, fid)
         assert _err(b, ref, fid) <= FP32_TOL[_group(fid)], fid
     print("cp.async vs bulk-copy staging:", {k: "%.1e" % v for k, v in diffs.items()})
-    assert max(diffs.values()) <= 1e-5, diffs
+    # measured on a B300: E, H, M up to 9.9e-6 (Ex, the near-zero component
+    # of a TE10 guide), the Ex PML split part 5.3e-5 against |Ex|
+    for fid, e in diffs.items():
+        assert e <= (2e-4 if fid >= 15 else 3e-5), (fid, e)
 
 
 def test_fp16_storage_against_oracle():
@@ -146,8 +152,12 @@ def test_batched_instances_against_oracle(prec, tol):
             a, r = s.get_field(fid), ref.get_field(fid)
             e = rel_l2(a, r) if np.linalg.norm(r) > 0 else float(np.abs(a).max())
             assert e <= tol, (q, fid, e)
-        if prec == mmx.FP64:
+        if prec == mmx.FP64 and np.any(w.Ms > 0):
             np.testing.assert_array_equal(s.get_iter_log(), ref.iter_log())
+        elif prec == mmx.FP64:
+            # no magnetic faces: the oracle logs 0 iterations per half step,
+            # the GPU logs nothing
+            assert len(s.get_iter_log()) == 0 and not np.any(ref.iter_log())
         ref.close()
     b.close()
 
@@ -192,3 +202,56 @@ def test_latched_timeout_makes_later_launches_return_at_once():
         assert s.sync(check=False) == 0
         assert s.check_bounded_wait() == -6          # the waits still work
         s.close()
+
+
+@pytest.mark.parametrize("prec", [mmx.FP32, mmx.FP16], ids=["fp32", "fp16"])
+def test_resident_box_kernel_equals_list_driven(prec):
+    """The H/M kernel that keeps the face records in shared memory evaluates
+    the same operations as the list-driven kernel: on the full 128x128x512
+    waveguide (0.354 M magnetic faces, two faces per thread) 30 steps give
+    bit-identical fields and iteration counts in FP32.  With FP16 storage
+    the resident kernel reuses the first half step's curl sum while the
+    list-driven one recomputes it from the scaled FP16 loads, where the
+    compiler may contract the scale differently: equal to FP32 rounding."""
+    import hashlib
+    w = W.waveguide(steps=30)
+    out = {}
+    for resident in (1, 0):
+        s = mmx.from_workload(w, prec=prec, path=mmx.PATH_FUSED)
+        s.set_box_kernel(resident)
+        s.step(13)
+        s.step(17)
+        assert s.sync(check=False) == 0
+        info = s.get_info()
+        assert info["box_kernel_name"] == ("k_hm_box_res" if resident else "k_hm_box"), info
+        if resident:
+            assert info["box_resident_faces_per_thread"] == 2, info
+        fields = [s.get_field(f) for f in range(19)]
+        out[resident] = ([hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest() for a in fields],
+                         s.get_iter_log(), fields)
+        s.close()
+    np.testing.assert_array_equal(out[1][1], out[0][1])
+    if prec == mmx.FP32:
+        assert out[1][0] == out[0][0]
+    else:
+        for fid in range(15):
+            a, b = out[1][2][fid], out[0][2][fid]
+            nb = np.linalg.norm(b)
+            assert (np.linalg.norm(a - b) / nb if nb > 0 else np.abs(a).max()) <= 1e-5, fid
+
+
+def test_resident_box_kernel_against_oracle_fp32_slab():
+    """The 32^3 slab in FP32 (records in shared memory, one face per thread)
+    against the oracle after 200 steps, as the list-driven kernel is."""
+    w = W.yig_slab_32()
+    w.tol = 1e-6
+    ref = oracle.from_workload(w)
+    ref.step(w.steps)
+    s = mmx.from_workload(w, prec=mmx.FP32, path=mmx.PATH_FUSED)
+    s.step(w.steps)
+    assert s.sync(check=False) == 0
+    assert s.get_info()["box_kernel_name"] == "k_hm_box_res"
+    errs = {fid: rel_l2(s.get_field(fid), ref.get_field(fid)) for fid in range(15)}
+    print("FP32 (resident H/M kernel) vs oracle, 32^3 slab, 200 steps:", {k: "%.2e" % v for k, v in errs.items()})
+    assert max(errs.values()) < 1e-4, errs
+    np.testing.assert_array_equal(s.get_iter_log(), ref.iter_log())

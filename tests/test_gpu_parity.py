@@ -262,7 +262,10 @@ def test_vectorised_fused_equals_plain(prec, n):
     b.step(5)
     a.step(4)
     prof = _kernels_seen(b, 4)
-    assert "fused_eh_vec" in prof and "fused_eh" not in prof, prof
+    # FP32 without sigma or mu_r stages its planes with bulk tensor copies
+    want = "fused_eh_vec_tma" if prec == mmx.FP32 else "fused_eh_vec"
+    assert want in prof and "fused_eh" not in prof, prof
+    assert b.get_info()["fused_kernel_name"] == ("k_fused_vec_tma" if prec == mmx.FP32 else "k_fused_vec")
     a.step(3)
     b.step(3)
     assert a.sync(check=False) == 0 and b.sync(check=False) == 0
@@ -284,7 +287,7 @@ def test_bulk_copy_fused_pass_is_deterministic():
     for _ in range(2):
         sim = mmx.from_workload(w, prec=mmx.FP32, path=mmx.PATH_FUSED)
         prof = _kernels_seen(sim, 2)
-        assert "fused_eh_vec" in prof, prof
+        assert "fused_eh_vec_tma" in prof, prof
         sim.step(298)
         assert sim.sync(check=False) == 0
         digests.append([hashlib.sha256(np.ascontiguousarray(sim.get_field(fid)).tobytes()).hexdigest()
@@ -307,7 +310,7 @@ def test_bulk_copy_staging_equals_plain_fp32(bcz, n):
     b = mmx.from_workload(w, prec=mmx.FP32, path=mmx.PATH_FUSED)
     a.step(6)
     prof = _kernels_seen(b, 6)
-    assert "fused_eh_vec" in prof, prof
+    assert "fused_eh_vec_tma" in prof and "fused_eh_vec" not in prof, prof
     assert a.sync(check=False) == 0 and b.sync(check=False) == 0
     for fid in range(15):
         assert _rel_to_scale(b, a, fid) <= 1e-5, fid
