@@ -509,7 +509,8 @@ template <typename T, typename S = T> static int compute_coop(mmx_ctx *ctx)
     if constexpr (sizeof(T) == 4) {
         for (int F = 1; F <= kResMaxF && ctx->nmag > 0; F++) {
             int pr = 0;
-            int rc = F == 1 ? res_occupancy<T, S, 1>(&pr) : res_occupancy<T, S, 2>(&pr);
+            int rc = F == 1 ? res_occupancy<T, S, 1>(&pr) : F == 2 ? res_occupancy<T, S, 2>(&pr)
+                                                                   : res_occupancy<T, S, 3>(&pr);
             if (rc) {
                 cudaGetLastError();
                 break;
@@ -576,8 +577,9 @@ static int launch_box(mmx_ctx *ctx, const Fields<T, S> &f, const Box<T> &b, Ptr3
     bool done = false;
     if constexpr (sizeof(T) == 4) {   // the resident kernel exists for FP32 arithmetic only
         if (ctx->res_faces > 0 && ctx->box_resident) {
-            const void *fn =
-                ctx->res_faces == 1 ? (const void *)k_hm_box_res<T, S, 1> : (const void *)k_hm_box_res<T, S, 2>;
+            const void *fn = ctx->res_faces == 1   ? (const void *)k_hm_box_res<T, S, 1>
+                             : ctx->res_faces == 2 ? (const void *)k_hm_box_res<T, S, 2>
+                                                   : (const void *)k_hm_box_res<T, S, 3>;
             ctx->last_box = 2;
             prof_begin(ctx, KK_HM_BOX_RES);
             e = cudaLaunchCooperativeKernel(fn, dim3(ctx->res_blocks), dim3(kResThreads), args,

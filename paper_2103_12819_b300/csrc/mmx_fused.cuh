@@ -372,7 +372,11 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
     const T sE = f.sE, sH = f.sH, isE = f.isE, isH = f.isH;
     constexpr int VB = V * (int)sizeof(S);      // bytes of one lane's S values
 
-    const int lane = threadIdx.x, w = threadIdx.y;
+    // lane and warp from the linear thread index: the same for the (32,
+    // BY+1) blocks of the plain launches and the 1-D blocks of the overlap
+    // launch
+    const int lin = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = lin & 31, w = lin >> 5;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int x0 = bx * xstride;
     const int i0 = x0 + V * lane;
@@ -419,7 +423,7 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
     // TMA variant: one mbarrier per stage, armed by thread (0, 0) with the
     // stage's byte count; every thread waits on its phase
     const unsigned mbar0 = TMA ? smem_u32(smem_raw + L::mb) : 0u;
-    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    const bool leader = lin == 0;
     if constexpr (TMA) {
         if (leader) {
 #pragma unroll

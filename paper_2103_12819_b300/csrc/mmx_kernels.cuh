@@ -413,13 +413,13 @@ __device__ __forceinline__ bool timeout_latched(const int *err)
 }
 constexpr int kVoteRows = 4;   // decision words sit this many residual rows past them
 
-__device__ __forceinline__ bool grid_barrier(unsigned long long *bar, int *err)
+__device__ __forceinline__ bool grid_barrier(unsigned long long *bar, int *err, int nblocks = -1)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned long long nb = gridDim.x;
+        const unsigned long long nb = nblocks < 0 ? gridDim.x : (unsigned)nblocks;
         unsigned long long old;
         asm volatile("atom.add.release.gpu.global.u64 %0, [%1], 1;" : "=l"(old) : "l"(bar) : "memory");
         const unsigned long long target = (old / nb + 1) * nb;
@@ -449,12 +449,12 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *bar, int *err)
 // (134.8 -> 133.4 us per waveguide step).  Returns 1 if no block flagged, 0
 // if some did, -1 if the bounded wait (~2^31 cycles) expired, with
 // kErrTimeout latched.
-__device__ __forceinline__ int grid_vote(unsigned long long *word, bool flag, int *err)
+__device__ __forceinline__ int grid_vote(unsigned long long *word, bool flag, int *err, int nblocks = -1)
 {
     __shared__ int s_v;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned long long nb = gridDim.x;
+        const unsigned long long nb = nblocks < 0 ? gridDim.x : (unsigned)nblocks;
         const unsigned long long add = (1ull << 32) | (flag ? 1ull : 0ull);
         unsigned long long v;
         asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(v) : "l"(word), "l"(add) : "memory");
@@ -729,10 +729,16 @@ __device__ __forceinline__ bool mag_store(const Geo &g, const Box<T> &b, const F
 // Returns the final iterate parity, or -1 if a barrier timed out.
 template <bool SECOND, bool WRITE, typename T, typename S>
 __device__ int hm_half_step(const Geo &g, const Fields<T, S> &f, const Box<T> &b, S *const Hin[3], S *const Hout[3],
-                            int fprev, unsigned long long *res)
+                            int fprev, unsigned long long *res, int bid = -1, int nblocks = -1)
 {
-    const int stride = gridDim.x * blockDim.x;
-    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    // the blocks taking part: the whole grid, or blocks 0 .. nblocks-1 of an
+    // overlap launch
+    if (bid < 0) {
+        bid = blockIdx.x;
+        nblocks = gridDim.x;
+    }
+    const int stride = nblocks * blockDim.x;
+    const int t0 = bid * blockDim.x + threadIdx.x;
     const T h0[3] = {(T)b.h0[0], (T)b.h0[1], (T)b.h0[2]};
     // iterate buffers of this half step; H^n of a second half step
     T *const W0[3] = {SECOND ? b.Hit2[0][0] : b.Hit[0][0], SECOND ? b.Hit2[0][1] : b.Hit[0][1],
@@ -781,7 +787,7 @@ __device__ int hm_half_step(const Geo &g, const Fields<T, S> &f, const Box<T> &b
     // block whose maximum is not positive (NaN included) publishes nothing
     // and does not vote, as it does not raise the published maximum.
     unsigned long long *const vote = res + kVoteRows * (kMaxIter + 1);
-    const int v1 = grid_vote(&vote[1], rmax > T(0) && !((double)rmax < b.tol), b.err);
+    const int v1 = grid_vote(&vote[1], rmax > T(0) && !((double)rmax < b.tol), b.err, nblocks);
     if (v1 < 0) return -1;
 
     int r = 1;
@@ -812,7 +818,7 @@ __device__ int hm_half_step(const Geo &g, const Fields<T, S> &f, const Box<T> &b
         }
         rmax = block_max(rmax);
         publish_residual(&res[r], rmax);
-        const int vr = grid_vote(&vote[r], rmax > T(0) && !((double)rmax < b.tol), b.err);
+        const int vr = grid_vote(&vote[r], rmax > T(0) && !((double)rmax < b.tol), b.err, nblocks);
         if (vr < 0) return -1;
         conv = vr == 1;
     }
@@ -837,7 +843,7 @@ __device__ int hm_half_step(const Geo &g, const Fields<T, S> &f, const Box<T> &b
         }
         if (!ok) atomicOr(b.err, kErrNonFinite);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (bid == 0 && threadIdx.x == 0) {
         if (!conv && b.order == 2) atomicOr(b.err, kErrNotConverged);
         unsigned long long hs = *b.halfsteps;
         b.iterlog[hs % kIterLogCap] = r;
