@@ -28,14 +28,14 @@ namespace {
 // Kernel kinds timed by the optional profiler.
 enum KernelKind {
     KK_HM_BOX = 0, KK_H_UPDATE, KK_E_UPDATE, KK_HARD, KK_FUSED, KK_FUSED_VEC, KK_FUSED_VEC_TMA, KK_ZERO_WALLS,
-    KK_M_SYNC, KK_HM_BOX_RES, KK_COUNT
+    KK_M_SYNC, KK_HM_BOX_RES, KK_H_HALF_VEC, KK_COUNT
 };
 // fused_eh_vec is k_fused_vec (per-lane cp.async staging), fused_eh_vec_tma
 // k_fused_vec_tma (bulk tensor copies); fused_eh the one-column kernel
 const char *const kKernelNames[KK_COUNT] = {"hm_box",       "h_update",         "e_update",
                                             "hard_source",  "fused_eh",         "fused_eh_vec",
                                             "fused_eh_vec_tma", "zero_walls",   "box_m_sync",
-                                            "hm_box_res"};
+                                            "hm_box_res",   "h_half_vec"};
 
 struct ProfRec {
     int kind;
@@ -102,6 +102,12 @@ struct mmx_ctx {
     // per thread (0: the magnetic faces do not fit, k_hm_box runs) and blocks
     int res_faces = 0, res_blocks = 0;
     int box_resident = 1;    // caller's choice (mmx_set_box_kernel)
+    bool h_half_vec = true;  // the fused path's first H half step vectorised
+    // M lives in two places: the box arrays (read and written through the
+    // API) and the magnetic-face records (used while stepping).  Each copy
+    // is refreshed from the other only when something reads it.
+    bool m_rec_stale = true;   // the box arrays hold a newer M than the records
+    bool m_box_stale = false;  // the records hold a newer M than the box arrays
     int last_box = 0;        // kernel of the last box launch (mmx_info.box_kernel)
 
     // point probes of E: (field, padded index) per probe and a device table
@@ -598,18 +604,45 @@ static int launch_box(mmx_ctx *ctx, const Fields<T, S> &f, const Box<T> &b, Ptr3
     return MMX_OK;
 }
 
+// The vectorised H half step (PEC x and y walls) outside the box [lo, hi).
 template <typename T, typename S>
-static int half_step(mmx_ctx *ctx, const Fields<T, S> &f, const Box<T> &b, double t_end)
+static void launch_h_half_vec(mmx_ctx *ctx, const Fields<T, S> &f, const int lo[3], const int hi[3])
+{
+    constexpr int W = 32 * Lanes<T>::V;
+    const int *n = ctx->desc.n;
+    dim3 B(32, 8), G((n[0] + 1 + W - 1) / W, (n[1] + 1 + 7) / 8, n[2] + 1);
+    const bool pml = ctx->g.npml > 0, gen = ctx->any_sigma || ctx->any_mu;
+    prof_begin(ctx, KK_H_HALF_VEC);
+#define MMX_HHV(PV, GV)                                                                                   \
+    if (pml == PV && gen == GV)                                                                           \
+        k_h_half_vec<T, S, PV, GV><<<G, B, 0, ctx->stream>>>(ctx->g, f, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]);
+    MMX_HHV(false, false) MMX_HHV(false, true) MMX_HHV(true, false) MMX_HHV(true, true)
+#undef MMX_HHV
+    prof_end(ctx);
+}
+
+// One H/M half step in place: the box kernel on the magnetic box, then the
+// non-magnetic update on every other face (the vectorised kernel when vec:
+// PEC x and y walls, as on the fused path).
+template <typename T, typename S>
+static int half_step(mmx_ctx *ctx, const Fields<T, S> &f, const Box<T> &b, double t_end, bool vec = false)
 {
     dim3 B = node_block(), G = node_grid(ctx);
+    const int none[3] = {0, 0, 0};
     if (ctx->magnetic) {
         Ptr3<S> Hout = {{f.H[0], f.H[1], f.H[2]}};
         int rc = launch_box<T, S>(ctx, f, b, Hout, 1);
         if (rc) return rc;
-        prof_begin(ctx, KK_H_UPDATE);
-        k_h_update<T, S><<<G, B, 0, ctx->stream>>>(ctx->g, f, ctx->lo[0], ctx->lo[1], ctx->lo[2], ctx->hi[0],
-                                                    ctx->hi[1], ctx->hi[2]);
-        prof_end(ctx);
+        if (vec) {
+            launch_h_half_vec<T, S>(ctx, f, ctx->lo, ctx->hi);
+        } else {
+            prof_begin(ctx, KK_H_UPDATE);
+            k_h_update<T, S><<<G, B, 0, ctx->stream>>>(ctx->g, f, ctx->lo[0], ctx->lo[1], ctx->lo[2], ctx->hi[0],
+                                                        ctx->hi[1], ctx->hi[2]);
+            prof_end(ctx);
+        }
+    } else if (vec) {
+        launch_h_half_vec<T, S>(ctx, f, none, none);
     } else {
         prof_begin(ctx, KK_H_UPDATE);
         k_h_update<T, S><<<G, B, 0, ctx->stream>>>(ctx->g, f, 0, 0, 0, 0, 0, 0);
@@ -714,6 +747,17 @@ template <typename T> static int box_m_sync(mmx_ctx *ctx, int to_rec)
     prof_end(ctx);
     CK(cudaGetLastError());
     return MMX_OK;
+}
+
+// Bring the box arrays up to date before anything reads or writes them
+// there (field copies of M, the adjoint, a batch call); after stepping the
+// records hold the current M.
+static int ensure_box_m(mmx_ctx *ctx)
+{
+    if (!ctx->m_box_stale) return MMX_OK;
+    int rc = is_fp64(ctx) ? box_m_sync<double>(ctx, 0) : box_m_sync<float>(ctx, 0);
+    if (!rc) ctx->m_box_stale = false;
+    return rc;
 }
 
 // z chunk of the fused kernel: as many chunks as fill one resident wave of
@@ -1058,7 +1102,7 @@ template <typename T, typename S = T> static int step_fused(mmx_ctx *ctx, int ns
     // Step 1 of the first step in place: H^n -> H^(n+1/2)
     {
         Fields<T, S> f = make_fields<T, S>(ctx);
-        int rc = half_step<T, S>(ctx, f, b, (ctx->steps + 0.5) * ctx->desc.dt);
+        int rc = half_step<T, S>(ctx, f, b, (ctx->steps + 0.5) * ctx->desc.dt, vec && ctx->h_half_vec);
         if (rc) return rc;
     }
     // Wall values set through mmx_set_field have been used by that half step
@@ -1171,6 +1215,11 @@ template <typename T> static int copy_field_t(mmx_ctx *ctx, int id, double *host
     else if (id < 15) {
         boxed = 1;
         dev = ctx->magnetic ? (T *)ctx->bM[id - 6] : nullptr;
+        if (dev) {
+            rc = ensure_box_m(ctx);
+            if (rc) return rc;
+            if (dir == 1) ctx->m_rec_stale = true;   // the box arrays are written
+        }
     } else if (id < 17) dev = (T *)ctx->Ezp[id - 15];
     else dev = (T *)ctx->Hzp[id - 17];
     Box<T> b = make_box<T>(ctx);
@@ -1784,6 +1833,8 @@ int mmx_set_materials(mmx_ctx *ctx, const double *eps_r, const double *sigma, co
     ctx->any_mu = any_mu;
     // (re)build the magnetic box
     CK(cudaStreamSynchronize(ctx->stream));
+    ctx->m_rec_stale = true;    // the rebuilt box arrays hold M = Ms zhat
+    ctx->m_box_stale = false;
     free_box(ctx);
     if (magnetic) {
         for (int a = 0; a < 3; a++) {
@@ -1868,6 +1919,8 @@ int mmx_set_M_cells(mmx_ctx *ctx, const double *mx, const double *my, const doub
     }
     cudaStreamSynchronize(ctx->stream);
     for (int c = 0; c < 3; c++) cudaFree(dm[c]);
+    ctx->m_rec_stale = true;
+    ctx->m_box_stale = false;
     if (rc) return rc;
     rc = read_status(ctx);
     if (rc == MMX_ERR_INVALID) return fail(ctx, rc, "a magnetic face has no magnetisation direction");
@@ -1996,9 +2049,14 @@ int mmx_step(mmx_ctx *ctx, int nsteps)
     for (auto &q : ctx->src) hard |= q.kind >= 2;
     const bool fp64 = is_fp64(ctx);
     // M lives in the magnetic-face records while stepping and in the box
-    // arrays between calls (where the API reads and writes it)
-    int rc = fp64 ? box_m_sync<double>(ctx, 1) : box_m_sync<float>(ctx, 1);
-    if (rc) return rc;
+    // arrays where the API reads and writes it; the records are refreshed
+    // only if the box arrays were written since the last step
+    int rc = MMX_OK;
+    if (ctx->m_rec_stale) {
+        rc = fp64 ? box_m_sync<double>(ctx, 1) : box_m_sync<float>(ctx, 1);
+        if (rc) return rc;
+        ctx->m_rec_stale = false;
+    }
     ctx->touched = true;
     if (is_fp16(ctx)) {
         if (ctx->path != MMX_PATH_FUSED || hard)
@@ -2009,8 +2067,9 @@ int mmx_step(mmx_ctx *ctx, int nsteps)
         rc = fp64 ? step_fused<double>(ctx, nsteps) : step_fused<float>(ctx, nsteps);
     else
         rc = fp64 ? step_plain<double>(ctx, nsteps) : step_plain<float>(ctx, nsteps);
-    int rc2 = fp64 ? box_m_sync<double>(ctx, 0) : box_m_sync<float>(ctx, 0);
-    return rc ? rc : rc2;
+    // the records now hold M; the box arrays are refreshed when read
+    if (ctx->magnetic) ctx->m_box_stale = true;
+    return rc;
 }
 
 int mmx_sync(mmx_ctx *ctx)
@@ -2190,8 +2249,13 @@ int mmx_flux_gradient(mmx_ctx *ctx, int kp, int nsteps, int checkpoint_every, do
     if (kp < 0 || kp > ctx->desc.n[2]) return fail(ctx, MMX_ERR_INVALID, "flux plane k must be in [0, nz]");
     if (nsteps < 1 || checkpoint_every < 1) return fail(ctx, MMX_ERR_INVALID, "nsteps and checkpoint_every >= 1");
     if (grad_h0) grad_h0[0] = grad_h0[1] = grad_h0[2] = 0.0;
-    return is_fp64(ctx) ? flux_gradient_t<double>(ctx, kp, nsteps, checkpoint_every, loss, grad_eps, grad_h0)
-                        : flux_gradient_t<float>(ctx, kp, nsteps, checkpoint_every, loss, grad_eps, grad_h0);
+    int rc = ensure_box_m(ctx);   // the adjoint works from and on the box arrays
+    if (rc) return rc;
+    rc = is_fp64(ctx) ? flux_gradient_t<double>(ctx, kp, nsteps, checkpoint_every, loss, grad_eps, grad_h0)
+                      : flux_gradient_t<float>(ctx, kp, nsteps, checkpoint_every, loss, grad_eps, grad_h0);
+    ctx->m_rec_stale = true;
+    ctx->m_box_stale = false;
+    return rc;
 }
 
 int mmx_add_probe(mmx_ctx *ctx, int field, int i, int j, int k)
@@ -2623,7 +2687,9 @@ template <typename T, typename S> static int batch_step_t(mmx_batch *b, int nste
     };
     int rc = MMX_OK;
     for (mmx_ctx *c : b->ctx) {
-        rc = box_m_sync<T>(c, 1);
+        // the instance's M may sit in its records after a standalone step
+        rc = ensure_box_m(c);
+        if (!rc) rc = box_m_sync<T>(c, 1);
         if (!rc) {
             Fields<T, S> f = make_fields<T, S>(c);
             rc = half_step<T, S>(c, f, make_box<T>(c), (c->steps + 0.5) * c->desc.dt);
@@ -2670,6 +2736,7 @@ template <typename T, typename S> static int batch_step_t(mmx_batch *b, int nste
         c->steps += nsteps;
         rc = box_m_sync<T>(c, 0);
         if (rc) break;
+        c->m_rec_stale = c->m_box_stale = false;   // both copies hold the new M
     }
     restore();
     return rc;

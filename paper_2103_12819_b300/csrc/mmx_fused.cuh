@@ -1067,6 +1067,176 @@ template <> struct VecRows<double> { static constexpr int value = 8; };
 template <typename T, bool GEN> struct VecStages { static constexpr int value = 2; };
 template <> struct VecStages<float, false> { static constexpr int value = MMX_VEC_F32_STAGES; };
 
+// One H half step (Steps 1/3 on non-magnetic faces, Eq. iterate_H with mu;
+// the same operations as k_h_update / h_face_nonmag_val) on every face
+// outside the magnetic box, in place, for grids with PEC x and y walls: the
+// first H half step of an mmx_step call on the fused path.  A lane owns V
+// consecutive columns of one row j of one plane k (16-byte vectors, 8 bytes
+// with FP16 storage) and updates Hx, Hy at layer k+1/2 and Hz at node k;
+// the column to its right comes from the next lane (lane 31 loads it).  A
+// warp covers W = 32 V columns; blocks are (32, 8): eight rows of one plane.
+template <typename T, typename S, bool PMLK, bool GEN>
+__global__ void __launch_bounds__(256) k_h_half_vec(const __grid_constant__ Geo g,
+                                                    const __grid_constant__ Fields<T, S> f, int blo0, int blo1,
+                                                    int blo2, int bhi0, int bhi1, int bhi2)
+{
+    using P = SV<S>;
+    constexpr int V = Lanes<T>::V, W = 32 * V;
+    const int lane = threadIdx.x;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int x0 = blockIdx.x * W, i0 = x0 + V * lane;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    const bool on = j <= ny && i0 <= nx;   // some column of this lane is a node column
+    const T sE = f.sE, sH = f.sH, isH = f.isH;
+    const T idx = f.inv_d[0], idy = f.inv_d[1], idz = f.inv_d[2];
+    const unsigned X = (unsigned)g.X, XY = (unsigned)g.X * (unsigned)g.Y;
+    const unsigned q = (unsigned)i0 + X * (unsigned)j + XY * (unsigned)k;
+    const bool kin = k < nz, jin = j < ny;           // a cell layer above / row after exists
+    const bool zwall = !g.per[2] && (k == 0 || k == nz);
+    const bool pml = PMLK && kin && pml_h_plane(g, k);
+    T ex[V], ey[V], ez[V], eyk[V], exk[V], ezj[V], exj[V];
+    vzero<T, V>(ex);
+    vzero<T, V>(ey);
+    vzero<T, V>(ez);
+    vzero<T, V>(eyk);
+    vzero<T, V>(exk);
+    vzero<T, V>(ezj);
+    vzero<T, V>(exj);
+    if (on) {
+        P::gld(ex, f.E[0] + q, sE);
+        P::gld(ey, f.E[1] + q, sE);
+        if (kin) {
+            P::gld(ez, f.E[2] + q, sE);
+            P::gld(eyk, f.E[1] + q + XY, sE);
+            P::gld(exk, f.E[0] + q + XY, sE);
+            if (jin) P::gld(ezj, f.E[2] + q + X, sE);
+        }
+        if (jin) P::gld(exj, f.E[0] + q + X, sE);
+    }
+    // column i0 + V: the next lane's first element, lane 31 loads it
+    T eyr = __shfl_down_sync(0xffffffffu, ey[0], 1);
+    T ezr = __shfl_down_sync(0xffffffffu, ez[0], 1);
+    if (lane == 31) {
+        const bool rin = on && x0 + W <= nx;
+        eyr = rin ? ld_s(f.E[1] + q + V, sE) : T(0);
+        ezr = (rin && kin) ? ld_s(f.E[2] + q + V, sE) : T(0);
+    }
+    bool bad = false;
+    const bool yrow_box = j >= blo1 && j < bhi1, k_box = k >= blo2 && k < bhi2;
+    // ---- Hx (i, j+1/2, k+1/2): j < ny, k < nz
+    if (on && jin && kin) {
+        T hn[V], fh[V], sp[V], v[V];
+        P::gld(hn, f.H[0] + q, sH);
+        if (GEN && f.fh[0]) vload(fh, f.fh[0] + q); else vfill<T, V>(fh, f.fh0);
+        if (pml) P::gld_rw(sp, f.Hzp[0] + q, sH); else vzero<T, V>(sp);
+        bool any = false;
+#pragma unroll
+        for (int e = 0; e < V; e++) {
+            const int i = i0 + e;
+            const bool skip = i > nx || (i >= blo0 && i < bhi0 && yrow_box && k_box);
+            T val = hn[e];
+            if (!skip) {
+                if (i == 0 || i == nx) {
+                    val = T(0);
+                    sp[e] = T(0);
+                } else {
+                    const T rest = (ezj[e] - ez[e]) * idy;
+                    const T zp = -(eyk[e] - ey[e]) * idz;
+                    if (pml) {
+                        const T h = f.dampH[k];
+                        const T hz = sp[e];
+                        const T hr = hn[e] - hz;
+                        const T hz1 = (hz * h - fh[e] * zp) * h;
+                        const T hr1 = hr - fh[e] * rest;
+                        sp[e] = hz1;
+                        val = hr1 + hz1;
+                    } else {
+                        val = hn[e] - fh[e] * (rest + zp);
+                    }
+                }
+                any = true;
+                bad |= !isfinite(val);
+            }
+            v[e] = val;
+        }
+        if (any) {
+            P::gst(f.H[0] + q, v, isH);
+            if (pml) P::gst(f.Hzp[0] + q, sp, isH);
+        }
+    }
+    // ---- Hy (i+1/2, j, k+1/2): i < nx, k < nz
+    if (on && kin) {
+        T hn[V], fh[V], sp[V], v[V];
+        P::gld(hn, f.H[1] + q, sH);
+        if (GEN && f.fh[1]) vload(fh, f.fh[1] + q); else vfill<T, V>(fh, f.fh0);
+        if (pml) P::gld_rw(sp, f.Hzp[1] + q, sH); else vzero<T, V>(sp);
+        bool any = false;
+#pragma unroll
+        for (int e = 0; e < V; e++) {
+            const int i = i0 + e;
+            const bool skip = i >= nx || (i >= blo0 && i < bhi0 && yrow_box && k_box);
+            T val = hn[e];
+            if (!skip) {
+                if (j == 0 || j == ny) {
+                    val = T(0);
+                    sp[e] = T(0);
+                } else {
+                    const T ezn = e < V - 1 ? ez[e < V - 1 ? e + 1 : 0] : ezr;
+                    const T zp = (exk[e] - ex[e]) * idz;
+                    const T rest = -(ezn - ez[e]) * idx;
+                    if (pml) {
+                        const T h = f.dampH[k];
+                        const T hz = sp[e];
+                        const T hr = hn[e] - hz;
+                        const T hz1 = (hz * h - fh[e] * zp) * h;
+                        const T hr1 = hr - fh[e] * rest;
+                        sp[e] = hz1;
+                        val = hr1 + hz1;
+                    } else {
+                        val = hn[e] - fh[e] * (rest + zp);
+                    }
+                }
+                any = true;
+                bad |= !isfinite(val);
+            }
+            v[e] = val;
+        }
+        if (any) {
+            P::gst(f.H[1] + q, v, isH);
+            if (pml) P::gst(f.Hzp[1] + q, sp, isH);
+        }
+    }
+    // ---- Hz (i+1/2, j+1/2, k): i < nx, j < ny
+    if (on && jin) {
+        T hn[V], fh[V], v[V];
+        P::gld(hn, f.H[2] + q, sH);
+        if (GEN && f.fh[2]) vload(fh, f.fh[2] + q); else vfill<T, V>(fh, f.fh0);
+        bool any = false;
+#pragma unroll
+        for (int e = 0; e < V; e++) {
+            const int i = i0 + e;
+            const bool skip = i >= nx || (i >= blo0 && i < bhi0 && yrow_box && k_box);
+            T val = hn[e];
+            if (!skip) {
+                if (zwall) {
+                    val = T(0);
+                } else {
+                    const T eyn = e < V - 1 ? ey[e < V - 1 ? e + 1 : 0] : eyr;
+                    const T rest = (eyn - ey[e]) * idx - (exj[e] - ex[e]) * idy;
+                    const T zp = T(0);
+                    val = hn[e] - fh[e] * (rest + zp);
+                }
+                any = true;
+                bad |= !isfinite(val);
+            }
+            v[e] = val;
+        }
+        if (any) P::gst(f.H[2] + q, v, isH);
+    }
+    if (bad) atomicOr(f.err, kErrNonFinite);
+}
+
 // Zero the wall column x = nx and the wall row y = ny (all planes) of up to
 // 16 Yee arrays: every component there is either a PEC wall value or does
 // not exist, and the vectorised kernel never writes it.

@@ -234,10 +234,14 @@ def test_resident_box_kernel_equals_list_driven(prec):
     if prec == mmx.FP32:
         assert out[1][0] == out[0][0]
     else:
-        for fid in range(15):
-            a, b = out[1][2][fid], out[0][2][fid]
-            nb = np.linalg.norm(b)
-            assert (np.linalg.norm(a - b) / nb if nb > 0 else np.abs(a).max()) <= 1e-5, fid
+        # a last-bit difference in a face's H becomes a one-ulp difference of
+        # its FP16 store (4.9e-4 relative); compared per vector field (Ex and
+        # Ez of a TE10 guide are near zero)
+        for grp, fids in (("E", range(0, 3)), ("H", range(3, 6)), ("M", range(6, 15))):
+            e2 = sum(float(np.sum((out[1][2][f] - out[0][2][f]) ** 2)) for f in fids)
+            n2 = sum(float(np.sum(out[0][2][f] ** 2)) for f in fids)
+            print("FP16 resident vs list-driven, %s: %.2e" % (grp, (e2 / n2) ** 0.5))
+            assert (e2 / n2) ** 0.5 <= 2e-3, grp
 
 
 def test_resident_box_kernel_against_oracle_fp32_slab():
