@@ -176,7 +176,8 @@ template <typename T> __device__ __forceinline__ T *pick_ptr(T *const p[3], int 
 template <typename T, typename S>
 __device__ __forceinline__ T res_first(const Geo &g, const Fields<T, S> &f, const Box<T> &b, S *const Hin[3],
                                        T *const Hp[3], T *const Hw[3], const ResSmem<T> &sm, int s,
-                                       const FaceOf &fo, int t, const T h0[3], bool second)
+                                       const FaceOf &fo, int t, const T h0[3], bool second, bool write,
+                                       S *const Hout[3], bool &ok)
 {
     const Q4<T> cs = q4_load(b.cst + t);
     const int d = fo.d;
@@ -223,16 +224,19 @@ __device__ __forceinline__ T res_first(const Geo &g, const Fields<T, S> &f, cons
     sm.mn[s] = q4(Mn[0], Mn[1], Mn[2], e0);
     sm.dm[s] = q4(r.x, r.y, r.z, T(0));
     const bool wall = wall_node(g, d, d == 0 ? fo.i : d == 1 ? fo.j : fo.k);
-    pick_ptr(Hw, d)[fo.l] = wall ? T(0) : cp - r.w;
+    const T hv = wall ? T(0) : cp - r.w;
+    pick_ptr(Hw, d)[fo.l] = hv;
+    if (write) ok &= res_store(g, f, b, Hout, fo, t, hv, q4(Mn[0], Mn[1], Mn[2], e0), q4(r.x, r.y, r.z, T(0)));
     return max(abs(r.x), max(abs(r.y), abs(r.z))) * cs.w;
 }
 
 // Iterate r >= 2 on one magnetic face from the neighbours' iterate r-1 in
 // Hprev: DeltaM^r replaces DeltaM^(r-1) in shared memory, H^r into Hcur.
 // Returns max_c |DeltaM^r_c - DeltaM^(r-1)_c| / Ms.
-template <typename T>
-__device__ __forceinline__ T res_next(const Geo &g, const Box<T> &b, T *const Hprev[3], T *const Hcur[3],
-                                      const ResSmem<T> &sm, int s, const FaceOf &fo, int t, const T h0[3])
+template <typename T, typename S>
+__device__ __forceinline__ T res_next(const Geo &g, const Fields<T, S> &f, const Box<T> &b, T *const Hprev[3],
+                                      T *const Hcur[3], const ResSmem<T> &sm, int s, const FaceOf &fo, int t,
+                                      const T h0[3], bool write, S *const Hout[3], bool &ok)
 {
     const Q4<T> cs = q4_load(b.cst + t);
     const int d = fo.d;
@@ -242,22 +246,40 @@ __device__ __forceinline__ T res_next(const Geo &g, const Box<T> &b, T *const Hp
     const V3<T> he = {h0[0] + h[0], h0[1] + h[1], h0[2] + h[2]};
     const Q4<T> r = llg_solve_rt(V3<T>{mq.x, mq.y, mq.z}, V3<T>{bq.x, bq.y, bq.z}, he, cs.y, cs.z, cs.x, mq.w, d);
     const bool wall = wall_node(g, d, d == 0 ? fo.i : d == 1 ? fo.j : fo.k);
-    pick_ptr(Hcur, d)[fo.l] = wall ? T(0) : bq.w - r.w;
+    const T hv = wall ? T(0) : bq.w - r.w;
+    pick_ptr(Hcur, d)[fo.l] = hv;
     sm.dm[s] = q4(r.x, r.y, r.z, T(0));
+    if (write) ok &= res_store(g, f, b, Hout, fo, t, hv, mq, q4(r.x, r.y, r.z, T(0)));
     return max(abs(r.x - pq.x), max(abs(r.y - pq.y), abs(r.z - pq.z))) * cs.w;
 }
 
 // Phase 0 on a non-magnetic face of run-time family d: its final H in both
 // iterate buffers.
 template <typename T, typename S>
-__device__ __forceinline__ void res_non_first(const Geo &g, const Fields<T, S> &f, S *const Hin[3], T *const Hp[3],
-                                              T *const W0[3], T *const W1[3], const FaceOf &fo, bool second)
+__device__ __forceinline__ T res_non_first(const Geo &g, const Fields<T, S> &f, S *const Hin[3], T *const Hp[3],
+                                           T *const W0[3], T *const W1[3], const FaceOf &fo, bool second)
 {
     const int d = fo.d;
     const T hn = second ? pick_ptr(Hp, d)[fo.l] : ld_s(pick_ptr(Hin, d) + gidx32(g, fo.i, fo.j, fo.k), f.sH);
     const T v = h_face_nonmag_val(g, f, d, fo.i, fo.j, fo.k, hn);
     pick_ptr(W0, d)[fo.l] = v;
     pick_ptr(W1, d)[fo.l] = v;
+    return v;
+}
+
+// When the half step writes back: H^r and M^(n+1/2,r) of one magnetic face
+// into Hout and its global record after every iterate r (the last write
+// stands, so no separate write-back phase is needed; the kernel reads M^n
+// from shared memory, never from the global record).  Returns false if a
+// value is not finite.
+template <typename T, typename S>
+__device__ __forceinline__ bool res_store(const Geo &g, const Fields<T, S> &f, const Box<T> &b, S *const Hout[3],
+                                          const FaceOf &fo, int t, T h, const Q4<T> &mq, const Q4<T> &dq)
+{
+    st_s(pick_ptr(Hout, fo.d) + gidx32(g, fo.i, fo.j, fo.k), h, f.isH);
+    const T m0 = mq.x + dq.x, m1 = mq.y + dq.y, m2 = mq.z + dq.z;
+    b.mn[t] = q4(m0, m1, m2, T(0));
+    return isfinite(h) && isfinite(m0) && isfinite(m1) && isfinite(m2);
 }
 
 // One H/M half step with the records in shared memory (the counterpart of
@@ -283,14 +305,28 @@ __device__ MMX_RES_FN int hm_half_step_res(const Geo &g, const Fields<T, S> &f, 
                       hs ? b.Hit2[1][2] : b.Hit[1][2]};
     T *const Hp[3] = {b.Hit[fprev & 1][0], b.Hit[fprev & 1][1], b.Hit[fprev & 1][2]};
 
-    // ---- phase 0: r = 1
-    for (int t = t0; t < b.nnon; t += stride) res_non_first(g, f, Hin, Hp, W0, W1, face_of(b.nonmag[t]), second);
+    // Writing back into another buffer than the one read (the fused path's
+    // ping-pong), every iterate's H and M go to Hout and the global records
+    // at once and the last write stands: no write-back phase.  In place
+    // (Hout = Hin) that would race with other blocks still reading H^n, so
+    // the final iterate is written after the last barrier instead.
+    const bool spec = write && (const void *)Hout[0] != (const void *)Hin[0];
+    // ---- phase 0: r = 1 (a non-magnetic face has its final H here)
+    bool ok = true;
+    for (int t = t0; t < b.nnon; t += stride) {
+        const FaceOf fo = face_of(b.nonmag[t]);
+        const T v = res_non_first(g, f, Hin, Hp, W0, W1, fo, second);
+        if (spec) {
+            st_s(pick_ptr(Hout, fo.d) + gidx32(g, fo.i, fo.j, fo.k), v, f.isH);
+            ok &= isfinite(v);
+        }
+    }
     T rmax = T(0);
 #pragma unroll 1
     for (int q = 0; q < F; q++) {
         const int t = tb + q * kResThreads, s = q * kResThreads + threadIdx.x;
         if (t >= b.nmag) break;
-        rmax = max(rmax, res_first(g, f, b, Hin, Hp, W1, sm, s, face_of(sm.ent[s]), t, h0, second));
+        rmax = max(rmax, res_first(g, f, b, Hin, Hp, W1, sm, s, face_of(sm.ent[s]), t, h0, second, spec, Hout, ok));
     }
     rmax = block_max(rmax);
     publish_residual(&res[1], rmax);
@@ -310,7 +346,7 @@ __device__ MMX_RES_FN int hm_half_step_res(const Geo &g, const Fields<T, S> &f, 
         for (int q = 0; q < F; q++) {
             const int t = tb + q * kResThreads, s = q * kResThreads + threadIdx.x;
             if (t >= b.nmag) break;
-            rmax = max(rmax, res_next(g, b, Hprev, Hcur, sm, s, face_of(sm.ent[s]), t, h0));
+            rmax = max(rmax, res_next(g, f, b, Hprev, Hcur, sm, s, face_of(sm.ent[s]), t, h0, spec, Hout, ok));
         }
         rmax = block_max(rmax);
         publish_residual(&res[r], rmax);
@@ -320,10 +356,9 @@ __device__ MMX_RES_FN int hm_half_step_res(const Geo &g, const Fields<T, S> &f, 
     }
 
     const int fr = r & 1;
-    if (write) {
+    if (write && !spec) {
         // ---- write back H (all box faces) and M^(n+1/2) (global records)
         T *const Hfin[3] = {fr ? W1[0] : W0[0], fr ? W1[1] : W0[1], fr ? W1[2] : W0[2]};
-        bool ok = true;
         for (int t = t0; t < b.nnon; t += stride) {
             const FaceOf fo = face_of(b.nonmag[t]);
             const T v = pick_ptr(Hfin, fo.d)[fo.l];
@@ -335,15 +370,11 @@ __device__ MMX_RES_FN int hm_half_step_res(const Geo &g, const Fields<T, S> &f, 
             const int t = tb + q * kResThreads, s = q * kResThreads + threadIdx.x;
             if (t >= b.nmag) break;
             const FaceOf fo = face_of(sm.ent[s]);
-            const T v = pick_ptr(Hfin, fo.d)[fo.l];
-            st_s(pick_ptr(Hout, fo.d) + gidx32(g, fo.i, fo.j, fo.k), v, f.isH);
-            const Q4<T> mq = sm.mn[s], dq = sm.dm[s];
-            const T m0 = mq.x + dq.x, m1 = mq.y + dq.y, m2 = mq.z + dq.z;
-            b.mn[t] = q4(m0, m1, m2, T(0));
-            ok &= isfinite(v) && isfinite(m0) && isfinite(m1) && isfinite(m2);
+            ok &= res_store(g, f, b, Hout, fo, t, pick_ptr(Hfin, fo.d)[fo.l], sm.mn[s], sm.dm[s]);
         }
-        if (!ok) atomicOr(b.err, kErrNonFinite);
     }
+    // with spec the last iterate's H and M are already in Hout and the records
+    if (write && !ok) atomicOr(b.err, kErrNonFinite);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (!conv && b.order == 2) atomicOr(b.err, kErrNotConverged);
         unsigned long long n = *b.halfsteps;
