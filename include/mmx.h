@@ -396,6 +396,12 @@ MMX_API int mmx_get_profile(mmx_ctx *ctx, mmx_kernel_profile *out, int cap, int 
 typedef struct mmx_batch mmx_batch;
 MMX_API int mmx_batch_create(mmx_ctx *const *ctxs, int count, void *cuda_stream, mmx_batch **out);
 MMX_API int mmx_batch_set_planes(mmx_batch *b, int planes);
+/* mmx_batch_set_box_blocks caps the cooperative H/M launch of a batch at
+ * per_sm blocks of 256 threads per SM (0, the default: as many as are
+ * resident, at most one per 256 faces).  Fewer blocks mean fewer arrivals at
+ * each grid-wide vote and more faces per thread; the second tuning knob of
+ * the batch.  MMX_ERR_INVALID for per_sm < 0. */
+MMX_API int mmx_batch_set_box_blocks(mmx_batch *b, int per_sm);
 MMX_API int mmx_batch_step(mmx_batch *b, int nsteps);
 MMX_API int mmx_batch_sync(mmx_batch *b);
 MMX_API const char *mmx_batch_last_error(mmx_batch *b);

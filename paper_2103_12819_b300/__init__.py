@@ -67,7 +67,7 @@ EXPORTS = ("mmx_create", "mmx_set_materials", "mmx_set_bias", "mmx_set_M_cells",
            "mmx_set_box_kernel",
            "mmx_flux_gradient", "mmx_set_storage_scale", "mmx_add_probe", "mmx_get_probes", "mmx_energy", "mmx_add_flux_plane", "mmx_get_flux",
            "mmx_set_profiling", "mmx_get_profile",
-           "mmx_batch_create", "mmx_batch_set_planes", "mmx_batch_step", "mmx_batch_sync",
+           "mmx_batch_create", "mmx_batch_set_planes", "mmx_batch_set_box_blocks", "mmx_batch_step", "mmx_batch_sync",
            "mmx_batch_last_error", "mmx_batch_destroy",
            "mmx_material_average_noalloc", "mmx_last_error", "mmx_destroy")
 
@@ -144,6 +144,8 @@ def lib():
     L.mmx_batch_create.argtypes = [ctypes.POINTER(P), I, P, ctypes.POINTER(P)]
     L.mmx_batch_set_planes.restype = I
     L.mmx_batch_set_planes.argtypes = [P, I]
+    L.mmx_batch_set_box_blocks.restype = I
+    L.mmx_batch_set_box_blocks.argtypes = [P, I]
     L.mmx_batch_step.restype = I
     L.mmx_batch_step.argtypes = [P, I]
     L.mmx_batch_sync.restype = I
@@ -446,6 +448,10 @@ class Batch:
     def set_planes(self, planes):
         """z planes each fused CTA marches (0: a whole grid)."""
         self._check(self._L.mmx_batch_set_planes(self._h, int(planes)), "mmx_batch_set_planes")
+
+    def set_box_blocks(self, per_sm):
+        """Cap the batched H/M launch at per_sm blocks per SM (0: all resident)."""
+        self._check(self._L.mmx_batch_set_box_blocks(self._h, int(per_sm)), "mmx_batch_set_box_blocks")
 
     def step(self, nsteps):
         self._check(self._L.mmx_batch_step(self._h, int(nsteps)), "mmx_batch_step")

@@ -2373,6 +2373,10 @@ struct mmx_batch {
     int *err = nullptr;
     int coop_blocks = 0;
     size_t box_smem = 0;
+    // H/M launch size: blocks needed, resident blocks per SM, SMs, and the
+    // caller's cap per SM (0: as many as are resident)
+    long long box_need = 0;
+    int box_per = 0, nsm = 0, box_per_sm = 0;
     // source amplitudes of every instance for one call: [inst][step][source]
     void *amp = nullptr;
     long long amp_cap = 0;                 // elements allocated
@@ -2447,6 +2451,14 @@ template <typename T> static int batch_plan(mmx_batch *b)
 
 // Concatenated face lists with their instance tags, per-instance residual
 // rows, the barrier word and the cooperative grid size.
+// Blocks of the batched H/M launch: enough for the larger face list, at
+// most the resident wave, or box_per_sm blocks per SM if the caller capped it.
+static void batch_box_grid(mmx_batch *b)
+{
+    const int per = b->box_per_sm > 0 ? std::min(b->box_per_sm, b->box_per) : b->box_per;
+    b->coop_blocks = (int)std::max(1LL, std::min(b->box_need, (long long)per * b->nsm));
+}
+
 template <typename T, typename S> static int batch_box_setup(mmx_batch *b)
 {
     const int ninst = (int)b->ctx.size();
@@ -2496,8 +2508,10 @@ template <typename T, typename S> static int batch_box_setup(mmx_batch *b)
     BCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hm_box_batch<T, S>, 256, b->box_smem));
     if (per < 1) return bfail(b, MMX_ERR_CUDA, "batched H/M kernel cannot be resident");
-    const long long need = (std::max(nm, nn) + 255) / 256;
-    b->coop_blocks = (int)std::max(1LL, std::min(need, (long long)per * nsm));
+    b->box_need = (std::max(nm, nn) + 255) / 256;
+    b->box_per = per;
+    b->nsm = nsm;
+    batch_box_grid(b);
     return MMX_OK;
 }
 
@@ -2809,6 +2823,19 @@ int mmx_batch_set_planes(mmx_batch *b, int planes)
         b->graph_steps = -1;
     }
     return b->prec == MMX_FP64 ? batch_plan<double>(b) : batch_plan<float>(b);
+}
+
+int mmx_batch_set_box_blocks(mmx_batch *b, int per_sm)
+{
+    if (!b || b->ctx.empty() || per_sm < 0) return MMX_ERR_INVALID;
+    b->box_per_sm = per_sm;
+    batch_box_grid(b);
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        b->graph_steps = -1;
+    }
+    return MMX_OK;
 }
 
 int mmx_batch_step(mmx_batch *b, int nsteps)

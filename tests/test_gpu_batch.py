@@ -105,3 +105,31 @@ def test_autotuner_picks_a_candidate_and_caches_it(tmp_path):
     table = json.load(open(cache))
     assert len(table) == 1 and list(table.values())[0]["planes"] == best
     assert autotune.tune_planes(make, candidates=(0, 16, 8), cache=cache) == best   # from the cache
+
+
+def test_box_block_cap_keeps_results_and_tuner_picks_both_knobs(tmp_path):
+    """Capping the batched H/M launch at fewer blocks per SM changes only how
+    the faces are spread over threads: FP64 fields and iteration counts stay
+    equal to the uncapped batch to 1e-13.  The tuner then returns a
+    (planes, box blocks) pair from its candidates and caches it."""
+    from paper_2103_12819_b300 import autotune
+    ws = _instances(mmx.FP64)
+    a = [mmx.from_workload(w, prec=mmx.FP64) for w in ws]
+    c = [mmx.from_workload(w, prec=mmx.FP64) for w in ws]
+    ba, bc = mmx.Batch(a), mmx.Batch(c)
+    bc.set_box_blocks(1)
+    ba.step(9)
+    bc.step(9)
+    assert ba.sync(check=False) == 0 and bc.sync(check=False) == 0
+    for x, y in zip(a, c):
+        for fid in range(15):
+            assert rel_l2(y.get_field(fid), x.get_field(fid)) <= 1e-13, fid
+        np.testing.assert_array_equal(x.get_iter_log(), y.get_iter_log())
+    ba.close()
+    bc.close()
+    wt = [W.tunable_filter(n, 1e5, seed=n) for n in (24, 32, 24)]
+    make = lambda: [mmx.from_workload(w, prec=mmx.FP32) for w in wt]
+    cache = str(tmp_path / "tune2.json")
+    cfg = autotune.tune(make, candidates=(0, 16), box_candidates=(0, 2), steps=4, warmup=1, cache=cache)
+    assert cfg["planes"] in (0, 16) and cfg["box_blocks"] in (0, 2)
+    assert autotune.tune(make, candidates=(0, 16), box_candidates=(0, 2), cache=cache) == cfg
