@@ -363,6 +363,28 @@ def _oracle_rate(w, variant, budget_s, max_steps=50):
     return w.ncells * n / el, n, el
 
 
+def oracle_stress_timing(single_steps=1, omp_steps=3):
+    """The FP64 oracle on the 512^3 configuration (bounded samples: set-up
+    excluded, `single_steps` steps on one thread, `omp_steps` steps of the
+    OpenMP build on all host cores).  Opt-in (--oracle-512): the oracle's
+    arrays take about 44 GB of host memory and its set-up minutes."""
+    import workloads
+    w = workloads.stress()
+    out = {"workload": "stress_512^3", "cells": w.ncells}
+    for variant, steps, key in (("", single_steps, "single_thread"), ("omp", omp_steps, "all_cores")):
+        import oracle
+        t0 = time.perf_counter()
+        s = oracle.from_workload(w, variant=variant)
+        setup = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        s.step(steps)
+        el = time.perf_counter() - t0
+        s.close()
+        out[key] = {"value": w.ncells * steps / el, "unit": UNIT, "steps": steps, "seconds": round(el, 1),
+                    "setup_s": round(setup, 1), "cores": 1 if not variant else (os.cpu_count() or 1)}
+    return out
+
+
 def cpu_baseline(w, budget_s=15.0, all_cores=True):
     """The FP64 oracle as it stands, single thread, on a bounded sample of
     the same workload (first steps of the run); beside it the oracle's
@@ -543,6 +565,8 @@ def ours_arm(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0 and args.oracle_512:
+        line["oracle_stress_512"] = oracle_stress_timing()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -560,6 +584,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stress", action="store_true", help="skip the 512^3 sub-record")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 256-instance sweep sub-record")
+    ap.add_argument("--oracle-512", action="store_true",
+                    help="also time the FP64 oracle on the 512^3 configuration (about 44 GB of host memory)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
