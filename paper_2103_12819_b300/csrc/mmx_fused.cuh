@@ -1124,12 +1124,23 @@ __global__ void __launch_bounds__(256) k_h_half_vec(const __grid_constant__ Geo 
     }
     bool bad = false;
     const bool yrow_box = j >= blo1 && j < bhi1, k_box = k >= blo2 && k < bhi2;
+    // every H this thread reads before any of its stores: the three
+    // components (and the PML split parts) are then in flight together
+    // instead of one round trip per component.  No other thread reads or
+    // writes them.
+    const bool onx = on && jin && kin, ony = on && kin, onz = on && jin;
+    T hn0[V], hn1[V], hn2[V], sp0[V], sp1[V];
+    if (onx) P::gld(hn0, f.H[0] + q, sH); else vzero<T, V>(hn0);
+    if (ony) P::gld(hn1, f.H[1] + q, sH); else vzero<T, V>(hn1);
+    if (onz) P::gld(hn2, f.H[2] + q, sH); else vzero<T, V>(hn2);
+    if (pml && onx) P::gld_rw(sp0, f.Hzp[0] + q, sH); else vzero<T, V>(sp0);
+    if (pml && ony) P::gld_rw(sp1, f.Hzp[1] + q, sH); else vzero<T, V>(sp1);
     // ---- Hx (i, j+1/2, k+1/2): j < ny, k < nz
-    if (on && jin && kin) {
-        T hn[V], fh[V], sp[V], v[V];
-        P::gld(hn, f.H[0] + q, sH);
+    if (onx) {
+        T fh[V], v[V];
+        T (&hn)[V] = hn0;
+        T (&sp)[V] = sp0;
         if (GEN && f.fh[0]) vload(fh, f.fh[0] + q); else vfill<T, V>(fh, f.fh0);
-        if (pml) P::gld_rw(sp, f.Hzp[0] + q, sH); else vzero<T, V>(sp);
         bool any = false;
 #pragma unroll
         for (int e = 0; e < V; e++) {
@@ -1166,11 +1177,11 @@ __global__ void __launch_bounds__(256) k_h_half_vec(const __grid_constant__ Geo 
         }
     }
     // ---- Hy (i+1/2, j, k+1/2): i < nx, k < nz
-    if (on && kin) {
-        T hn[V], fh[V], sp[V], v[V];
-        P::gld(hn, f.H[1] + q, sH);
+    if (ony) {
+        T fh[V], v[V];
+        T (&hn)[V] = hn1;
+        T (&sp)[V] = sp1;
         if (GEN && f.fh[1]) vload(fh, f.fh[1] + q); else vfill<T, V>(fh, f.fh0);
-        if (pml) P::gld_rw(sp, f.Hzp[1] + q, sH); else vzero<T, V>(sp);
         bool any = false;
 #pragma unroll
         for (int e = 0; e < V; e++) {
@@ -1208,9 +1219,9 @@ __global__ void __launch_bounds__(256) k_h_half_vec(const __grid_constant__ Geo 
         }
     }
     // ---- Hz (i+1/2, j+1/2, k): i < nx, j < ny
-    if (on && jin) {
-        T hn[V], fh[V], v[V];
-        P::gld(hn, f.H[2] + q, sH);
+    if (onz) {
+        T fh[V], v[V];
+        T (&hn)[V] = hn2;
         if (GEN && f.fh[2]) vload(fh, f.fh[2] + q); else vfill<T, V>(fh, f.fh0);
         bool any = false;
 #pragma unroll

@@ -316,11 +316,14 @@ def test_bulk_copy_staging_equals_plain_fp32(bcz, n):
         assert _rel_to_scale(b, a, fid) <= 1e-5, fid
 
 
-def test_vectorised_fused_after_set_field_keeps_walls():
+@pytest.mark.parametrize("n", [(20, 12, 32), (64, 16, 32)], ids=["ragged", "strip_multiple"])
+def test_vectorised_fused_after_set_field_keeps_walls(n):
     """Nonzero values written onto the x = nx / y = ny PEC walls by set_field
     are cleared before the vectorised kernel runs, as the per-update path
-    clears them in its first step."""
-    w = W.waveguide(n=(20, 12, 32), steps=4)
+    clears them in its first step.  With nx a multiple of the FP64 strip
+    width (64) and ny of the row block (8), the vectorised first half step
+    leaves the wall column and row to the wall clearing."""
+    w = W.waveguide(n=n, steps=4)
     a = mmx.from_workload(w, prec=mmx.FP64, path=mmx.PATH_PLAIN)
     b = mmx.from_workload(w, prec=mmx.FP64, path=mmx.PATH_FUSED)
     rng = np.random.default_rng(5)
