@@ -98,8 +98,11 @@ CASES = [
     dict(seed=17, bc=(W.PEC, W.PERIODIC, W.PEC), order=1),
     dict(seed=18, bc=(W.PERIODIC, W.PEC, W.PEC), magnetic=False),
     dict(seed=19, bc=(W.PEC, W.PEC, W.PEC), n=(2, 9, 7)),
-    # wider than one FP64 strip of the vectorised fused kernel (64 columns):
-    # two and three overlapping strips, ragged last strip, ragged row tile
+    # wider than one FP64 strip (64 columns): two and three strips, ragged
+    # last strip and row tile.  Seed 20's magnetic box reaches the PML's
+    # neighbouring layer, so its fused path is k_fused; seed 21 runs the
+    # vectorised kernel (more such grids, with the kernel that ran checked,
+    # in test_gpu_edge_cases.py)
     dict(seed=20, bc=(W.PEC, W.PEC, W.PML), pml_cells=3, n=(70, 10, 14)),
     dict(seed=21, bc=(W.PEC, W.PEC, W.PEC), n=(131, 4, 5)),
 ]

@@ -323,11 +323,13 @@ def convergence(n: int, order: int = 2, tol: float = 1e-10) -> Workload:
 
 def random_small(seed: int, n=(6, 5, 7), bc=(PEC, PEC, PEC), pml_cells: int = 0,
                  magnetic: bool = True, sources: bool = True, order: int = 2,
-                 tol: float = 1e-10, dx=(1e-6, 1.3e-6, 0.8e-6), hard: bool = False) -> Workload:
+                 tol: float = 1e-10, dx=(1e-6, 1.3e-6, 0.8e-6), hard: bool = False,
+                 pml_gap: int = 1) -> Workload:
     """Small randomised problem for parity tests: random eps_r in [1, 4],
     sigma in [0, 50) S/m, mu_r in [1, 2] where non-magnetic, a random magnetic
-    blob (kept out of PML slabs), random initial E and H, random bias and
-    point/plane (optionally hard) sources."""
+    blob (kept out of PML slabs and the pml_gap cell layers next to them),
+    random initial E and H, random bias and point/plane (optionally hard)
+    sources."""
     rng = np.random.default_rng(seed)
     shp = _cell_shape(n)
     dt = cfl_dt(dx, 0.9)
@@ -337,8 +339,8 @@ def random_small(seed: int, n=(6, 5, 7), bc=(PEC, PEC, PEC), pml_cells: int = 0,
     if magnetic:
         blob = rng.uniform(size=shp) < 0.5
         if pml_cells:
-            blob[:pml_cells + 1] = False
-            blob[n[2] - pml_cells - 1:] = False
+            blob[:pml_cells + pml_gap] = False
+            blob[n[2] - pml_cells - pml_gap:] = False
         Ms = np.where(blob, rng.uniform(0.5e5, 1.5e5, size=shp), 0.0)
     mu = np.where(Ms > 0, 1.0, rng.uniform(1.0, 2.0, size=shp))
     if pml_cells:
