@@ -784,16 +784,34 @@ __device__ __forceinline__ void fused_vec_body(const Geo &g, const Fields<T, S> 
                     else
                         e_cols(with_src, std::integral_constant<int, 0>{});
                 };
-                // FP32 arithmetic: a copy without source terms on the planes
-                // that have none; FP64 keeps the copy with source terms
-                // only (the second copy's registers cost it more than the
-                // subtractions it saves).  Hoisting the PML test out of the
-                // columns cut the FP32 launch from 56.9 M to 50.4 M warp
-                // instructions and 87.6 to 85.7 us on the waveguide.
-                if (sizeof(T) == 8 || src_here)
+                // FP32 arithmetic: the copy without source terms on every
+                // plane, then on the few planes that hold sources their
+                // -cb J added to the finished E (a second, source-carrying
+                // copy of the update in the loop cost the source-free planes
+                // 4 % of their instructions: 84.4 against 85.3 us per
+                // launch); FP64 keeps the copy with source terms only (a
+                // second copy's registers cost it more than the subtractions
+                // it saves).  Hoisting the PML test out of the columns cut
+                // the FP32 launch from 56.9 M to 50.4 M warp instructions
+                // and 87.6 to 85.7 us on the waveguide.
+                if (sizeof(T) == 8) {
                     e_pml(std::true_type{});
-                else
+                } else {
                     e_pml(std::false_type{});
+                    if (src_here) {
+#pragma unroll
+                        for (int e = 0; e < V; e++) {
+                            if (!cin[e] || !lane_on) continue;
+                            const int i = i0 + e;
+                            const T J0 = j_source_a(g, f, amp, src, nsrc, 0, i, j, k);
+                            const T J1 = j_source_a(g, f, amp, src, nsrc, 1, i, j, k);
+                            const T J2 = j_source_a(g, f, amp, src, nsrc, 2, i, j, k);
+                            if (!wy && !wz) ex[e] -= cb[0][e] * J0;
+                            if (!xw[e] && !wz) ey[e] -= cb[1][e] * J1;
+                            if (!xw[e] && !wy && k < nz) ez[e] -= cb[2][e] * J2;
+                        }
+                    }
+                }
             }
         }
         vstore(SEx(b, w) + col, ex);
