@@ -490,11 +490,17 @@ static int box_alloc(mmx_ctx *ctx, void **p)
     return rc;
 }
 
+// Resident blocks per SM of the shared-memory H/M kernel with F faces per
+// thread: the smaller of its second- and first-order instantiations.
 template <typename T, typename S, int F> static int res_occupancy(int *per)
 {
     const size_t sm = res_smem_bytes<T>(F);
-    CK_RAW(cudaFuncSetAttribute(k_hm_box_res<T, S, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    CK_RAW(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_hm_box_res<T, S, F>, kResThreads, sm));
+    int p1 = 0, p2 = 0;
+    CK_RAW(cudaFuncSetAttribute(k_hm_box_res<T, S, F, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    CK_RAW(cudaFuncSetAttribute(k_hm_box_res<T, S, F, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    CK_RAW(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_hm_box_res<T, S, F, 1>, kResThreads, sm));
+    CK_RAW(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_hm_box_res<T, S, F, 2>, kResThreads, sm));
+    *per = std::min(p1, p2);
     return MMX_OK;
 }
 
@@ -503,7 +509,12 @@ template <typename T, typename S = T> static int compute_coop(mmx_ctx *ctx)
     int dev = 0, nsm = 0, per = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hm_box<T, S>, 256, 0));
+    {
+        int p1 = 0, p2 = 0;   // first- and second-order instantiations
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_hm_box<T, S, 1>, 256, 0));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_hm_box<T, S, 2>, 256, 0));
+        per = std::min(p1, p2);
+    }
     if (per < 1) return fail(ctx, MMX_ERR_CUDA, "H/M kernel cannot be resident");
     long long need = (std::max(ctx->nmag, ctx->nnon) + 255) / 256;
     long long cap = (long long)per * nsm;
@@ -583,9 +594,15 @@ static int launch_box(mmx_ctx *ctx, const Fields<T, S> &f, const Box<T> &b, Ptr3
     bool done = false;
     if constexpr (sizeof(T) == 4) {   // the resident kernel exists for FP32 arithmetic only
         if (ctx->res_faces > 0 && ctx->box_resident) {
-            const void *fn = ctx->res_faces == 1   ? (const void *)k_hm_box_res<T, S, 1>
-                             : ctx->res_faces == 2 ? (const void *)k_hm_box_res<T, S, 2>
-                                                   : (const void *)k_hm_box_res<T, S, 3>;
+            // the scheme order is a template argument: with a run-time test
+            // the first-order branch cost the second-order launch 1.5 us
+            const bool o2 = ctx->desc.order == 2;
+            const void *fn = ctx->res_faces == 1   ? (o2 ? (const void *)k_hm_box_res<T, S, 1, 2>
+                                                         : (const void *)k_hm_box_res<T, S, 1, 1>)
+                             : ctx->res_faces == 2 ? (o2 ? (const void *)k_hm_box_res<T, S, 2, 2>
+                                                         : (const void *)k_hm_box_res<T, S, 2, 1>)
+                                                   : (o2 ? (const void *)k_hm_box_res<T, S, 3, 2>
+                                                         : (const void *)k_hm_box_res<T, S, 3, 1>);
             ctx->last_box = 2;
             prof_begin(ctx, KK_HM_BOX_RES);
             e = cudaLaunchCooperativeKernel(fn, dim3(ctx->res_blocks), dim3(kResThreads), args,
@@ -596,8 +613,8 @@ static int launch_box(mmx_ctx *ctx, const Fields<T, S> &f, const Box<T> &b, Ptr3
     if (!done) {
         ctx->last_box = 1;
         prof_begin(ctx, KK_HM_BOX);
-        e = cudaLaunchCooperativeKernel((const void *)k_hm_box<T, S>, dim3(ctx->coop_blocks), dim3(256), args, 0,
-                                        ctx->stream);
+        const void *fn = ctx->desc.order == 2 ? (const void *)k_hm_box<T, S, 2> : (const void *)k_hm_box<T, S, 1>;
+        e = cudaLaunchCooperativeKernel(fn, dim3(ctx->coop_blocks), dim3(256), args, 0, ctx->stream);
     }
     prof_end(ctx);
     CK(e);

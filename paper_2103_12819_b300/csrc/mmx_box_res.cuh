@@ -173,7 +173,7 @@ template <typename T> __device__ __forceinline__ T *pick_ptr(T *const p[3], int 
 // (or the first-order update); H^1 into Hw.  second: H^n from the previous
 // half step's iterate buffer Hp, M^n = M^n + DeltaM of that half step, and
 // the curl sum stored by the first half step.
-template <typename T, typename S>
+template <int ORD, typename T, typename S>
 __device__ __forceinline__ T res_first(const Geo &g, const Fields<T, S> &f, const Box<T> &b, S *const Hin[3],
                                        T *const Hp[3], T *const Hw[3], const ResSmem<T> &sm, int s,
                                        const FaceOf &fo, int t, const T h0[3], bool second, bool write,
@@ -212,7 +212,7 @@ __device__ __forceinline__ T res_first(const Geo &g, const Fields<T, S> &f, cons
     T beta[3] = {T(0), T(0), T(0)};
     Q4<T> r;
     const V3<T> mn = {Mn[0], Mn[1], Mn[2]}, he = {heff[0], heff[1], heff[2]};
-    if (b.order == 2) {
+    if constexpr (ORD == 2) {
         beta[0] = -k1 * (Mn[1] * heff[2] - Mn[2] * heff[1]);
         beta[1] = -k1 * (Mn[2] * heff[0] - Mn[0] * heff[2]);
         beta[2] = -k1 * (Mn[0] * heff[1] - Mn[1] * heff[0]);
@@ -289,7 +289,7 @@ __device__ __forceinline__ bool res_store(const Geo &g, const Fields<T, S> &f, c
 // hm_half_step, at run time: one copy of the code serves all three half
 // steps of the launches, which keeps the kernel's instruction footprint
 // small.  Returns the final iterate parity, or -1 if a barrier timed out.
-template <int F, typename T, typename S>
+template <int F, int ORD, typename T, typename S>
 __device__ MMX_RES_FN int hm_half_step_res(const Geo &g, const Fields<T, S> &f, const Box<T> &b, S *const Hin[3],
                                              S *const Hout[3], int fprev, unsigned long long *res,
                                              const ResSmem<T> sm, bool second, bool write)
@@ -326,7 +326,8 @@ __device__ MMX_RES_FN int hm_half_step_res(const Geo &g, const Fields<T, S> &f, 
     for (int q = 0; q < F; q++) {
         const int t = tb + q * kResThreads, s = q * kResThreads + threadIdx.x;
         if (t >= b.nmag) break;
-        rmax = max(rmax, res_first(g, f, b, Hin, Hp, W1, sm, s, face_of(sm.ent[s]), t, h0, second, spec, Hout, ok));
+        rmax = max(rmax, res_first<ORD>(g, f, b, Hin, Hp, W1, sm, s, face_of(sm.ent[s]), t, h0, second, spec, Hout,
+                                        ok));
     }
     rmax = block_max(rmax);
     publish_residual(&res[1], rmax);
@@ -335,7 +336,7 @@ __device__ MMX_RES_FN int hm_half_step_res(const Geo &g, const Fields<T, S> &f, 
     if (v1 < 0) return -1;
 
     int r = 1;
-    bool conv = v1 == 1 || b.order == 1;
+    bool conv = v1 == 1 || ORD == 1;
     while (!conv && r < b.max_iter) {
         r++;
         const int pr = (r - 1) & 1, cr = r & 1;
@@ -376,11 +377,11 @@ __device__ MMX_RES_FN int hm_half_step_res(const Geo &g, const Fields<T, S> &f, 
     // with spec the last iterate's H and M are already in Hout and the records
     if (write && !ok) atomicOr(b.err, kErrNonFinite);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (!conv && b.order == 2) atomicOr(b.err, kErrNotConverged);
+        if (!conv && ORD == 2) atomicOr(b.err, kErrNotConverged);
         unsigned long long n = *b.halfsteps;
         b.iterlog[n % kIterLogCap] = r;
         *b.halfsteps = n + 1;
-        *b.last_res = b.order == 2 ? __longlong_as_double((long long)res[r]) : 0.0;
+        *b.last_res = ORD == 2 ? __longlong_as_double((long long)res[r]) : 0.0;
     }
     return fr;
 }
@@ -389,7 +390,7 @@ __device__ MMX_RES_FN int hm_half_step_res(const Geo &g, const Fields<T, S> &f, 
 // (F faces per thread, res_smem_bytes<T>(F) bytes of dynamic shared memory
 // per block); nsub and slot as for k_hm_box.  Requires gridDim.x F 256 >=
 // nmag.
-template <typename T, typename S, int F>
+template <typename T, typename S, int F, int ORD>
 __global__ void __launch_bounds__(kResThreads, MMX_RES_MINB)
     k_hm_box_res(const __grid_constant__ Geo g, const __grid_constant__ Fields<T, S> f,
                  const __grid_constant__ Box<T> b, const __grid_constant__ Ptr3<S> Hout, int nsub, int slot)
@@ -416,9 +417,9 @@ __global__ void __launch_bounds__(kResThreads, MMX_RES_MINB)
     // each thread reads back only its own slots: no block barrier needed.
     // nsub = 2: the first half step keeps its result in the iterate buffers
     // and shared memory, the second starts from there and writes back.
-    const int fr = hm_half_step_res<F>(g, f, b, f.H, Hout.p, 0, b.res + 2 * slot * W, sm, false, nsub != 2);
+    const int fr = hm_half_step_res<F, ORD>(g, f, b, f.H, Hout.p, 0, b.res + 2 * slot * W, sm, false, nsub != 2);
     if (fr < 0 || nsub != 2) return;
-    hm_half_step_res<F>(g, f, b, f.H, Hout.p, fr, b.res + (2 * slot + 1) * W, sm, true, true);
+    hm_half_step_res<F, ORD>(g, f, b, f.H, Hout.p, fr, b.res + (2 * slot + 1) * W, sm, true, true);
 }
 
 } // namespace mmx

@@ -615,7 +615,7 @@ __device__ __forceinline__ void first_load(const Geo &g, const Fields<T, S> &f, 
 // Arithmetic and stores of phase 0: C' = H^n - dt/(2 mu0) curl E,
 // beta = -kappa M^n x H_eff^n, e0 and DeltaM^1; H^1 into Hw.  Returns
 // max_c |DeltaM^1_c| / Ms.
-template <int D, typename T>
+template <int D, int ORD = 0, typename T>
 __device__ __forceinline__ T first_finish(const Geo &g, const Box<T> &b, T *const Hw[3], const FaceOf &fo, int t,
                                           const FirstIn<T> &in, const T h0[3])
 {
@@ -628,7 +628,7 @@ __device__ __forceinline__ T first_finish(const Geo &g, const Box<T> &b, T *cons
     for (int c = 0; c < 3; c++) heff[c] = h0[c] + in.h[c];
     T dM[3], dMh;
     T beta[3] = {T(0), T(0), T(0)};
-    if (b.order == 2) {
+    if (ORD == 0 ? b.order == 2 : ORD == 2) {
         beta[0] = -k1 * (Mn[1] * heff[2] - Mn[2] * heff[1]);
         beta[1] = -k1 * (Mn[2] * heff[0] - Mn[0] * heff[2]);
         beta[2] = -k1 * (Mn[0] * heff[1] - Mn[1] * heff[0]);
@@ -727,10 +727,13 @@ __device__ __forceinline__ bool mag_store(const Geo &g, const Box<T> &b, const F
 //   WRITE true:   H^(n+1/2) goes to the global Hout and M^(n+1/2) into the
 //                 records; otherwise both stay in the iterate buffers.
 // Returns the final iterate parity, or -1 if a barrier timed out.
-template <bool SECOND, bool WRITE, typename T, typename S>
+//   ORD:          the scheme order (2 or 1) as a compile-time constant, or
+//                 0 to read it from the box descriptor.
+template <bool SECOND, bool WRITE, int ORD = 0, typename T, typename S>
 __device__ int hm_half_step(const Geo &g, const Fields<T, S> &f, const Box<T> &b, S *const Hin[3], S *const Hout[3],
                             int fprev, unsigned long long *res, int bid = -1, int nblocks = -1)
 {
+    const bool second_order = ORD == 0 ? b.order == 2 : ORD == 2;
     // the blocks taking part: the whole grid, or blocks 0 .. nblocks-1 of an
     // overlap launch
     if (bid < 0) {
@@ -768,13 +771,13 @@ __device__ int hm_half_step(const Geo &g, const Fields<T, S> &f, const Box<T> &b
             T rv;
             if (fo.d == 0) {
                 first_load<0, SECOND>(g, f, b, Hin, Hp, dmp, fo, t, in);
-                rv = first_finish<0>(g, b, W1, fo, t, in, h0);
+                rv = first_finish<0, ORD>(g, b, W1, fo, t, in, h0);
             } else if (fo.d == 1) {
                 first_load<1, SECOND>(g, f, b, Hin, Hp, dmp, fo, t, in);
-                rv = first_finish<1>(g, b, W1, fo, t, in, h0);
+                rv = first_finish<1, ORD>(g, b, W1, fo, t, in, h0);
             } else {
                 first_load<2, SECOND>(g, f, b, Hin, Hp, dmp, fo, t, in);
-                rv = first_finish<2>(g, b, W1, fo, t, in, h0);
+                rv = first_finish<2, ORD>(g, b, W1, fo, t, in, h0);
             }
             rmax = max(rmax, rv);
         }
@@ -791,7 +794,7 @@ __device__ int hm_half_step(const Geo &g, const Fields<T, S> &f, const Box<T> &b
     if (v1 < 0) return -1;
 
     int r = 1;
-    bool conv = v1 == 1 || b.order == 1;
+    bool conv = v1 == 1 || !second_order;
     while (!conv && r < b.max_iter) {
         r++;
         const int pr = (r - 1) & 1, cr = r & 1;
@@ -844,11 +847,11 @@ __device__ int hm_half_step(const Geo &g, const Fields<T, S> &f, const Box<T> &b
         if (!ok) atomicOr(b.err, kErrNonFinite);
     }
     if (bid == 0 && threadIdx.x == 0) {
-        if (!conv && b.order == 2) atomicOr(b.err, kErrNotConverged);
+        if (!conv && second_order) atomicOr(b.err, kErrNotConverged);
         unsigned long long hs = *b.halfsteps;
         b.iterlog[hs % kIterLogCap] = r;
         *b.halfsteps = hs + 1;
-        *b.last_res = b.order == 2 ? __longlong_as_double((long long)res[r]) : 0.0;
+        *b.last_res = second_order ? __longlong_as_double((long long)res[r]) : 0.0;
     }
     return fr;
 }
@@ -869,7 +872,7 @@ template <typename T> struct BoxMinBlocks {
 // result.  Residual words: launch parity `slot` uses rows 2 slot and
 // 2 slot + 1 of res (residual maxima) and the rows kVoteRows further on
 // (decision words), and clears the other parity's rows for the next launch.
-template <typename T, typename S = T>
+template <typename T, typename S = T, int ORD = 0>
 __global__ void __launch_bounds__(256, BoxMinBlocks<T>::value) k_hm_box(const __grid_constant__ Geo g,
                                                 const __grid_constant__ Fields<T, S> f,
                                                 const __grid_constant__ Box<T> b,
@@ -891,11 +894,11 @@ __global__ void __launch_bounds__(256, BoxMinBlocks<T>::value) k_hm_box(const __
     if (nsub == 2) {
         // two half steps with one E; the first keeps its result in the
         // iterate buffers, the second starts from there and writes back
-        const int fr = hm_half_step<false, false>(g, f, b, f.H, Hout.p, 0, b.res + 2 * slot * W);
+        const int fr = hm_half_step<false, false, ORD>(g, f, b, f.H, Hout.p, 0, b.res + 2 * slot * W);
         if (fr < 0) return;
-        hm_half_step<true, true>(g, f, b, f.H, Hout.p, fr, b.res + (2 * slot + 1) * W);
+        hm_half_step<true, true, ORD>(g, f, b, f.H, Hout.p, fr, b.res + (2 * slot + 1) * W);
     } else {
-        hm_half_step<false, true>(g, f, b, f.H, Hout.p, 0, b.res + 2 * slot * W);
+        hm_half_step<false, true, ORD>(g, f, b, f.H, Hout.p, 0, b.res + 2 * slot * W);
     }
 }
 
