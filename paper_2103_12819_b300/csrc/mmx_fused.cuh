@@ -1174,89 +1174,98 @@ __global__ void __launch_bounds__(256) k_h_half_vec(const __grid_constant__ Geo 
     if (onz) P::gld(hn2, f.H[2] + q, sH); else vzero<T, V>(hn2);
     if (pml && onx) P::gld_rw(sp0, f.Hzp[0] + q, sH); else vzero<T, V>(sp0);
     if (pml && ony) P::gld_rw(sp1, f.Hzp[1] + q, sH); else vzero<T, V>(sp1);
-    // ---- Hx (i, j+1/2, k+1/2): j < ny, k < nz
-    if (onx) {
-        T fh[V], v[V];
-        T (&hn)[V] = hn0;
-        T (&sp)[V] = sp0;
-        if (GEN && f.fh[0]) vload(fh, f.fh[0] + q); else vfill<T, V>(fh, f.fh0);
-        bool any = false;
+    // Hx and Hy with and without the PML split update, chosen per plane
+    // (block) rather than inside the unrolled columns
+    auto hxy = [&](auto with_pml) {
+        constexpr bool PML = decltype(with_pml)::value;
+        // ---- Hx (i, j+1/2, k+1/2): j < ny, k < nz
+        if (onx) {
+            T fh[V], v[V];
+            T (&hn)[V] = hn0;
+            T (&sp)[V] = sp0;
+            if (GEN && f.fh[0]) vload(fh, f.fh[0] + q); else vfill<T, V>(fh, f.fh0);
+            bool any = false;
 #pragma unroll
-        for (int e = 0; e < V; e++) {
-            const int i = i0 + e;
-            const bool skip = i > nx || (i >= blo0 && i < bhi0 && yrow_box && k_box);
-            T val = hn[e];
-            if (!skip) {
-                if (i == 0 || i == nx) {
-                    val = T(0);
-                    sp[e] = T(0);
-                } else {
-                    const T rest = (ezj[e] - ez[e]) * idy;
-                    const T zp = -(eyk[e] - ey[e]) * idz;
-                    if (pml) {
-                        const T h = f.dampH[k];
-                        const T hz = sp[e];
-                        const T hr = hn[e] - hz;
-                        const T hz1 = (hz * h - fh[e] * zp) * h;
-                        const T hr1 = hr - fh[e] * rest;
-                        sp[e] = hz1;
-                        val = hr1 + hz1;
+            for (int e = 0; e < V; e++) {
+                const int i = i0 + e;
+                const bool skip = i > nx || (i >= blo0 && i < bhi0 && yrow_box && k_box);
+                T val = hn[e];
+                if (!skip) {
+                    if (i == 0 || i == nx) {
+                        val = T(0);
+                        sp[e] = T(0);
                     } else {
-                        val = hn[e] - fh[e] * (rest + zp);
+                        const T rest = (ezj[e] - ez[e]) * idy;
+                        const T zp = -(eyk[e] - ey[e]) * idz;
+                        if constexpr (PML) {
+                            const T h = f.dampH[k];
+                            const T hz = sp[e];
+                            const T hr = hn[e] - hz;
+                            const T hz1 = (hz * h - fh[e] * zp) * h;
+                            const T hr1 = hr - fh[e] * rest;
+                            sp[e] = hz1;
+                            val = hr1 + hz1;
+                        } else {
+                            val = hn[e] - fh[e] * (rest + zp);
+                        }
                     }
+                    any = true;
+                    bad |= !isfinite(val);
                 }
-                any = true;
-                bad |= !isfinite(val);
+                v[e] = val;
             }
-            v[e] = val;
+            if (any) {
+                P::gst(f.H[0] + q, v, isH);
+                if constexpr (PML) P::gst(f.Hzp[0] + q, sp, isH);
+            }
         }
-        if (any) {
-            P::gst(f.H[0] + q, v, isH);
-            if (pml) P::gst(f.Hzp[0] + q, sp, isH);
-        }
-    }
-    // ---- Hy (i+1/2, j, k+1/2): i < nx, k < nz
-    if (ony) {
-        T fh[V], v[V];
-        T (&hn)[V] = hn1;
-        T (&sp)[V] = sp1;
-        if (GEN && f.fh[1]) vload(fh, f.fh[1] + q); else vfill<T, V>(fh, f.fh0);
-        bool any = false;
+        // ---- Hy (i+1/2, j, k+1/2): i < nx, k < nz
+        if (ony) {
+            T fh[V], v[V];
+            T (&hn)[V] = hn1;
+            T (&sp)[V] = sp1;
+            if (GEN && f.fh[1]) vload(fh, f.fh[1] + q); else vfill<T, V>(fh, f.fh0);
+            bool any = false;
 #pragma unroll
-        for (int e = 0; e < V; e++) {
-            const int i = i0 + e;
-            const bool skip = i >= nx || (i >= blo0 && i < bhi0 && yrow_box && k_box);
-            T val = hn[e];
-            if (!skip) {
-                if (j == 0 || j == ny) {
-                    val = T(0);
-                    sp[e] = T(0);
-                } else {
-                    const T ezn = e < V - 1 ? ez[e < V - 1 ? e + 1 : 0] : ezr;
-                    const T zp = (exk[e] - ex[e]) * idz;
-                    const T rest = -(ezn - ez[e]) * idx;
-                    if (pml) {
-                        const T h = f.dampH[k];
-                        const T hz = sp[e];
-                        const T hr = hn[e] - hz;
-                        const T hz1 = (hz * h - fh[e] * zp) * h;
-                        const T hr1 = hr - fh[e] * rest;
-                        sp[e] = hz1;
-                        val = hr1 + hz1;
+            for (int e = 0; e < V; e++) {
+                const int i = i0 + e;
+                const bool skip = i >= nx || (i >= blo0 && i < bhi0 && yrow_box && k_box);
+                T val = hn[e];
+                if (!skip) {
+                    if (j == 0 || j == ny) {
+                        val = T(0);
+                        sp[e] = T(0);
                     } else {
-                        val = hn[e] - fh[e] * (rest + zp);
+                        const T ezn = e < V - 1 ? ez[e < V - 1 ? e + 1 : 0] : ezr;
+                        const T zp = (exk[e] - ex[e]) * idz;
+                        const T rest = -(ezn - ez[e]) * idx;
+                        if constexpr (PML) {
+                            const T h = f.dampH[k];
+                            const T hz = sp[e];
+                            const T hr = hn[e] - hz;
+                            const T hz1 = (hz * h - fh[e] * zp) * h;
+                            const T hr1 = hr - fh[e] * rest;
+                            sp[e] = hz1;
+                            val = hr1 + hz1;
+                        } else {
+                            val = hn[e] - fh[e] * (rest + zp);
+                        }
                     }
+                    any = true;
+                    bad |= !isfinite(val);
                 }
-                any = true;
-                bad |= !isfinite(val);
+                v[e] = val;
             }
-            v[e] = val;
+            if (any) {
+                P::gst(f.H[1] + q, v, isH);
+                if constexpr (PML) P::gst(f.Hzp[1] + q, sp, isH);
+            }
         }
-        if (any) {
-            P::gst(f.H[1] + q, v, isH);
-            if (pml) P::gst(f.Hzp[1] + q, sp, isH);
-        }
-    }
+    };
+    if (pml)
+        hxy(std::true_type{});
+    else
+        hxy(std::false_type{});
     // ---- Hz (i+1/2, j+1/2, k): i < nx, j < ny
     if (onz) {
         T fh[V], v[V];
