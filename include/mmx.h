@@ -247,8 +247,8 @@ typedef struct {
 MMX_API int mmx_get_info(mmx_ctx *ctx, mmx_info *out);
 
 /* Kernel of the H/M half steps.  resident = 1 (default): where the magnetic
- * faces fit in the GPU's shared memory (FP32 arithmetic, at most 2 faces per
- * thread over one resident wave of 256-thread blocks; about 0.37 M faces on
+ * faces fit in the GPU's shared memory (FP32 arithmetic, at most 3 faces per
+ * thread over one resident wave of 256-thread blocks; about 0.45 M faces on
  * a B300), every block keeps its faces' iteration records (M^n, beta, C',
  * the current increment) in shared memory for the whole launch; elsewhere,
  * and with resident = 0, the list-driven kernel keeps them in global memory.
