@@ -2397,6 +2397,7 @@ struct mmx_batch {
     int *err = nullptr;
     int coop_blocks = 0;
     size_t box_smem = 0;
+    int order = 0;           // every instance's scheme order, or 0 if they differ
     // H/M launch size: blocks needed, resident blocks per SM, SMs, and the
     // caller's cap per SM (0: as many as are resident)
     long long box_need = 0;
@@ -2524,13 +2525,20 @@ template <typename T, typename S> static int batch_box_setup(mmx_batch *b)
     if (nn) BCK(cudaMemcpyAsync(b->non_inst, ni.data(), ni.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     BCK(cudaStreamSynchronize(b->stream));
     b->box_smem = (size_t)ninst * (sizeof(unsigned long long) + 2 * sizeof(int));
+    // the H/M launch is specialised for the scheme order when every instance
+    // has the same one
+    b->order = b->ctx[0]->desc.order;
+    for (mmx_ctx *c : b->ctx)
+        if (c->desc.order != b->order) b->order = 0;
+    const void *boxk = b->order == 2 ? (const void *)k_hm_box_batch<T, S, 2>
+                     : b->order == 1 ? (const void *)k_hm_box_batch<T, S, 1>
+                                     : (const void *)k_hm_box_batch<T, S, 0>;
     if (b->box_smem > 48 * 1024)
-        BCK(cudaFuncSetAttribute(k_hm_box_batch<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)b->box_smem));
+        BCK(cudaFuncSetAttribute(boxk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->box_smem));
     int dev = 0, nsm = 0, per = 0;
     BCK(cudaGetDevice(&dev));
     BCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hm_box_batch<T, S>, 256, b->box_smem));
+    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, boxk, 256, b->box_smem));
     if (per < 1) return bfail(b, MMX_ERR_CUDA, "batched H/M kernel cannot be resident");
     b->box_need = (std::max(nm, nn) + 255) / 256;
     b->box_per = per;
@@ -2703,7 +2711,10 @@ template <typename T, typename S> static int batch_enqueue(mmx_batch *b, int nst
             cfg.stream = b->stream;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            BCK(cudaLaunchKernelExC(&cfg, (const void *)k_hm_box_batch<T, S>, args));
+            const void *boxk = b->order == 2 ? (const void *)k_hm_box_batch<T, S, 2>
+                             : b->order == 1 ? (const void *)k_hm_box_batch<T, S, 1>
+                                             : (const void *)k_hm_box_batch<T, S, 0>;
+            BCK(cudaLaunchKernelExC(&cfg, boxk, args));
         }
     }
     return MMX_OK;

@@ -62,7 +62,8 @@ __device__ __forceinline__ bool batch_update(const BatchShared &sh, const BoxIns
     return __syncthreads_or(any) != 0;
 }
 
-template <bool SECOND, bool WRITE, typename T, typename S>
+// ORD: the scheme order of every instance (2 or 1), or 0 when they differ.
+template <bool SECOND, bool WRITE, int ORD, typename T, typename S>
 __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const int4 *mag, const int *mag_inst,
                                    int nmag, const int4 *non, const int *non_inst, int nnon,
                                    unsigned long long *res, unsigned long long *bar, int *berr,
@@ -111,13 +112,13 @@ __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const i
         T rv;
         if (fo.d == 0) {
             first_load<0, SECOND>(I.g, I.f, I.b, Hin, Hp, I.b.dm[fp], fo, tl, in);
-            rv = first_finish<0>(I.g, I.b, W1, fo, tl, in, h0);
+            rv = first_finish<0, ORD>(I.g, I.b, W1, fo, tl, in, h0);
         } else if (fo.d == 1) {
             first_load<1, SECOND>(I.g, I.f, I.b, Hin, Hp, I.b.dm[fp], fo, tl, in);
-            rv = first_finish<1>(I.g, I.b, W1, fo, tl, in, h0);
+            rv = first_finish<1, ORD>(I.g, I.b, W1, fo, tl, in, h0);
         } else {
             first_load<2, SECOND>(I.g, I.f, I.b, Hin, Hp, I.b.dm[fp], fo, tl, in);
-            rv = first_finish<2>(I.g, I.b, W1, fo, tl, in, h0);
+            rv = first_finish<2, ORD>(I.g, I.b, W1, fo, tl, in, h0);
         }
         if (rv > T(0)) atomicMax(&sh.res[qi], (unsigned long long)__double_as_longlong((double)rv));
     }
@@ -209,7 +210,7 @@ __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const i
 // nsub H/M half steps of every instance with one E.  res holds, for launch
 // parity `slot`, rows [2 slot + h][instance][kMaxIter + 1] (h = half step);
 // the other parity's rows are cleared here for the next launch.
-template <typename T, typename S = T>
+template <typename T, typename S = T, int ORD = 0>
 __global__ void __launch_bounds__(256, BoxMinBlocks<T>::value)
     k_hm_box_batch(const BoxInst<T, S> *__restrict__ inst, int ninst, const int4 *__restrict__ mag,
                    const int *__restrict__ mag_inst, int nmag, const int4 *__restrict__ non,
@@ -231,13 +232,13 @@ __global__ void __launch_bounds__(256, BoxMinBlocks<T>::value)
     __syncthreads();
     unsigned long long *r0 = res + 2 * slot * rows;
     if (nsub == 2) {
-        if (!hm_half_step_batch<false, false>(inst, ninst, mag, mag_inst, nmag, non, non_inst, nnon, r0, bar, berr,
+        if (!hm_half_step_batch<false, false, ORD>(inst, ninst, mag, mag_inst, nmag, non, non_inst, nnon, r0, bar, berr,
                                               sh))
             return;
-        hm_half_step_batch<true, true>(inst, ninst, mag, mag_inst, nmag, non, non_inst, nnon, r0 + rows, bar, berr,
+        hm_half_step_batch<true, true, ORD>(inst, ninst, mag, mag_inst, nmag, non, non_inst, nnon, r0 + rows, bar, berr,
                                        sh);
     } else {
-        hm_half_step_batch<false, true>(inst, ninst, mag, mag_inst, nmag, non, non_inst, nnon, r0, bar, berr, sh);
+        hm_half_step_batch<false, true, ORD>(inst, ninst, mag, mag_inst, nmag, non, non_inst, nnon, r0, bar, berr, sh);
     }
 }
 
