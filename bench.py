@@ -423,13 +423,16 @@ def reference_arm(args):
     return 0
 
 
-def stress_leg(torch, mmx, stream, peak, K=10, W=3):
+def stress_leg(torch, mmx, stream, peak, K=10, W=3, prec=None):
     """The 512^3 throughput configuration (PEC box, centred random 256^3
-    magnetic block, no source, FP32, tol 1e-6): cell-updates/s, the
-    step-level HBM fraction and the per-kernel shares (CUDA events)."""
+    magnetic block, no source, FP32 or FP16 storage with FP32 arithmetic,
+    tol 1e-6): cell-updates/s, the step-level HBM fraction and the
+    per-kernel shares (CUDA events).  With FP16 storage B_alg counts E and H
+    as 2-byte words: (12 x 2 + 4) + 21 f x 4 bytes."""
     import workloads
+    prec = mmx.FP32 if prec is None else prec
     w = workloads.stress()
-    sim = mmx.from_workload(w, prec=mmx.FP32, stream=stream.cuda_stream, path=mmx.PATH_FUSED)
+    sim = mmx.from_workload(w, prec=prec, stream=stream.cuda_stream, path=mmx.PATH_FUSED)
     sim.step(W)
     if sim.sync(check=False):
         raise RuntimeError("stress warm-up failed: %s" % sim.last_error())
@@ -445,9 +448,12 @@ def stress_leg(torch, mmx, stream, peak, K=10, W=3):
     value = w.ncells * K / (ms * 1e-3)
     tot = sum(v[1] for v in prof.values())
     eff, f = effective_fraction(w, value, 4, peak)
+    if prec == mmx.FP16:
+        eff = round((28 + 84 * f) * value / (peak * 1e9), 4)
     return {"workload": "stress_512^3 (PEC, centred random 256^3 magnetic block, no source, tol 1e-6)",
             "cells": w.ncells, "steps": K, "warmup": W, "value": value, "unit": UNIT,
-            "ms_per_step": ms / K, "dtype": "f32", "magnetic_fraction": round(f, 4),
+            "ms_per_step": ms / K, "dtype": "f32" if prec != mmx.FP16 else "f16 storage, f32 arithmetic",
+            "magnetic_fraction": round(f, 4),
             "effective_hbm_fraction": eff, "fused_kernel": info["fused_kernel_name"],
             "box_faces_magnetic": info["box_faces_magnetic"],
             "kernel_shares": {k: round(v[1] / tot, 4) for k, v in prof.items()},
@@ -531,6 +537,7 @@ def ours_arm(args):
         acc16 = accuracy_leg(mmx, w, stream, checkpoints=(1000,), prec=mmx.FP16)
         e2e = e2e_leg(torch, mmx, w, mmx.FP32, path, K, stream)
         stress = None if args.no_stress else stress_leg(torch, mmx, stream, peak)
+        stress16 = None if args.no_stress else stress_leg(torch, mmx, stream, peak, prec=mmx.FP16)
         sweep = None if args.no_sweep else sweep_leg(torch, mmx, stream, peak)
     value = whole_job_rate(w.ncells, world, K, ms32)
     eff, mag_frac = effective_fraction(w, value / world, 4, peak)
@@ -561,6 +568,7 @@ def ours_arm(args):
         "fp32_vs_fp64_rel_l2_after_steps": acc,
         "iters": {"min": stats32["iters_min"], "max": stats32["iters_max"]},
         "stress_512": stress,
+        "stress_512_fp16": stress16,
         "bias_sweep_256": sweep,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
