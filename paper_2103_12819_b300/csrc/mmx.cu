@@ -96,6 +96,7 @@ struct mmx_ctx {
     void *fcst = nullptr, *fmn = nullptr, *fbc = nullptr, *fdm[2] = {};   // per magnetic face (list order)
     void *bms[3] = {}, *bk1[3] = {}, *bk2[3] = {};
     int4 *dmag = nullptr, *dnon = nullptr;
+    unsigned *dmag32 = nullptr;   // the magnetic list's packed first words
     int nmag = 0, nnon = 0;
     int coop_blocks = 0;
     // H/M box kernel with the records in shared memory (k_hm_box_res): faces
@@ -339,6 +340,7 @@ template <typename T> static Box<T> make_box(mmx_ctx *c)
     b.err = c->errw;
     b.mag = c->dmag;
     b.nonmag = c->dnon;
+    b.mag32 = c->dmag32;
     b.nmag = c->nmag;
     b.nnon = c->nnon;
     return b;
@@ -428,6 +430,7 @@ static void free_box(mmx_ctx *c)
     c->magnetic = false;
     c->nb = 0;
     c->dmag = c->dnon = nullptr;
+    c->dmag32 = nullptr;
     c->nmag = c->nnon = 0;
     c->fcst = c->fmn = c->fbc = c->fdm[0] = c->fdm[1] = nullptr;
 }
@@ -480,6 +483,14 @@ static int build_box_lists(mmx_ctx *ctx, const double *Ms)
     if (!non.empty()) CK(cudaMemcpy(pn, non.data(), non.size() * sizeof(int4), cudaMemcpyHostToDevice));
     ctx->dmag = (int4 *)pm;
     ctx->dnon = (int4 *)pn;
+    std::vector<unsigned> m32(mag.size());
+    for (size_t q = 0; q < mag.size(); q++) m32[q] = (unsigned)mag[q].x;
+    void *p32 = nullptr;
+    rc = dalloc(ctx, &p32, std::max<size_t>(1, m32.size()) * sizeof(unsigned));
+    if (rc) return rc;
+    ctx->box_allocs.push_back(p32);
+    if (!m32.empty()) CK(cudaMemcpy(p32, m32.data(), m32.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
+    ctx->dmag32 = (unsigned *)p32;
     return MMX_OK;
 }
 

@@ -154,6 +154,10 @@ template <typename T> struct Box {
     // and of the other (non-magnetic) faces of the box
     const int4 *mag;
     const int4 *nonmag;
+    // the magnetic list's first words alone (box index | family << 30): the
+    // list-driven kernel rebuilds i, j, k from the box index, reading 4 bytes
+    // per face and phase instead of 16
+    const unsigned *mag32;
     int nmag, nnon;
 };
 

@@ -512,6 +512,22 @@ struct FaceOf {
     unsigned l;
 };
 
+// A face from its packed word alone: i, j, k from the box index l =
+// (i - lo0) + bx ((j - lo1) + by (k - lo2)), the inverse of the list build.
+template <typename T> __device__ __forceinline__ FaceOf face_of32(unsigned e, const Box<T> &b)
+{
+    FaceOf fo;
+    fo.l = e & 0x3fffffffu;
+    fo.d = (int)(e >> 30);
+    const unsigned bx = (unsigned)b.bx, bxy = bx * (unsigned)b.by;
+    const unsigned bk = fo.l / bxy, r = fo.l - bk * bxy;
+    const unsigned bj = r / bx;
+    fo.i = b.lo[0] + (int)(r - bj * bx);
+    fo.j = b.lo[1] + (int)bj;
+    fo.k = b.lo[2] + (int)bk;
+    return fo;
+}
+
 __device__ __forceinline__ FaceOf face_of(int4 e)
 {
     FaceOf fo;
@@ -763,10 +779,10 @@ __device__ int hm_half_step(const Geo &g, const Fields<T, S> &f, const Box<T> &b
     }
     T rmax = T(0);
     {
-        int4 nx = t0 < b.nmag ? b.mag[t0] : make_int4(0, 0, 0, 0);
+        unsigned nx = t0 < b.nmag ? b.mag32[t0] : 0u;
         for (int t = t0; t < b.nmag; t += stride) {
-            const FaceOf fo = face_of(nx);
-            if (t + stride < b.nmag) nx = b.mag[t + stride];
+            const FaceOf fo = face_of32(nx, b);
+            if (t + stride < b.nmag) nx = b.mag32[t + stride];
             FirstIn<T> in;
             T rv;
             if (fo.d == 0) {
@@ -801,10 +817,10 @@ __device__ int hm_half_step(const Geo &g, const Fields<T, S> &f, const Box<T> &b
         T *const Hprev[3] = {pr ? W1[0] : W0[0], pr ? W1[1] : W0[1], pr ? W1[2] : W0[2]};
         T *const Hcur[3] = {cr ? W1[0] : W0[0], cr ? W1[1] : W0[1], cr ? W1[2] : W0[2]};
         rmax = T(0);
-        int4 nx = t0 < b.nmag ? b.mag[t0] : make_int4(0, 0, 0, 0);
+        unsigned nx = t0 < b.nmag ? b.mag32[t0] : 0u;
         for (int t = t0; t < b.nmag; t += stride) {
-            const FaceOf fo = face_of(nx);
-            if (t + stride < b.nmag) nx = b.mag[t + stride];
+            const FaceOf fo = face_of32(nx, b);
+            if (t + stride < b.nmag) nx = b.mag32[t + stride];
             NextIn<T> in;
             T rv;
             if (fo.d == 0) {
@@ -839,7 +855,7 @@ __device__ int hm_half_step(const Geo &g, const Fields<T, S> &f, const Box<T> &b
             ok &= isfinite(v);
         }
         for (int t = t0; t < b.nmag; t += stride) {
-            const FaceOf fo = face_of(b.mag[t]);
+            const FaceOf fo = face_of32(b.mag32[t], b);
             ok &= fo.d == 0   ? mag_store<0>(g, b, fo, t, Hfin, Hout, fr, f.isH)
                   : fo.d == 1 ? mag_store<1>(g, b, fo, t, Hfin, Hout, fr, f.isH)
                               : mag_store<2>(g, b, fo, t, Hfin, Hout, fr, f.isH);
