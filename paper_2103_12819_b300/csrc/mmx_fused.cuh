@@ -15,8 +15,9 @@
 //
 // Per plane k of the chunk: H^(n+1/2) of plane k is staged for the warp
 // below; E^(n+1) of plane k (Ex, Ey at node k; Ez at layer k+1/2) is formed
-// and staged for the warp above; the next plane is prefetched into
-// registers; then Hz at plane k and Hx, Hy at layer k-1/2 take NH half steps
+// and staged for the warp above, while the next planes are in flight into
+// a ring of shared-memory stages (bulk tensor copies, or per-lane cp.async);
+// then Hz at plane k and Hx, Hy at layer k-1/2 take NH half steps
 // (Steps 3 and the next step's 1, both with E^(n+1)).  Faces of the magnetic
 // box are written here too and overwritten by the H/M box kernel, which runs
 // after this one from the old H buffer.  Walls: Ey, Ez at x = 0, Ex, Ez at
