@@ -2,7 +2,8 @@
 oracle through the C ABI: the vectorised fused kernel on multi-strip grids
 with a z-PML (checked to be the kernel that ran), a magnetic region of a
 single cell, magnetisation parallel to its effective field (a fixed point of
-the H/M iteration), and a call of zero steps."""
+the H/M iteration), a call of zero steps, and the headline kernels on a
+guide whose width and height are not multiples of their tiles."""
 import numpy as np
 import pytest
 
@@ -19,6 +20,10 @@ TOL64 = 1e-12
 # random fields can amplify that by a few units per step; measured 2.1-2.3e-7
 # on the grids below, and the bar leaves a factor of about 9.
 TOL32 = 2e-6
+# The 100 x 37 x 50 guide after 120 FP32 steps: measured E <= 4.2e-6 (Ex, the
+# near-zero component of a TE10 guide), H <= 7.7e-7, M <= 9.7e-7, PML split
+# parts <= 7.0e-6 of their component; the bars are about four times that.
+RAGGED_TOL = {"E": 2e-5, "H": 3e-6, "M": 4e-6, "PML": 3e-5}
 
 
 def _fids(w):
@@ -168,3 +173,34 @@ def test_zero_steps_change_nothing(path):
     assert len(sim.get_iter_log()) == 0
     for fid, a in zip(range(15), before):
         np.testing.assert_array_equal(sim.get_field(fid), a)
+
+
+def test_bulk_copy_pass_on_a_ragged_guide_against_oracle():
+    """The headline kernels (bulk-copy fused pass, shared-memory H/M kernel)
+    on a guide whose width and height fill neither a lane's 4 columns nor a
+    7-row tile (100 x 37 cells; z-PML, TE10 plane, YIG slab), FP32 against
+    the FP64 oracle after 120 steps, with the kernels that ran asserted."""
+    w = W.waveguide(n=(100, 37, 50), steps=120)
+    w.tol = 1e-6
+    ref = oracle.from_workload(w)
+    ref.step(w.steps)
+    sim = mmx.from_workload(w, prec=mmx.FP32, path=mmx.PATH_FUSED)
+    sim.step(w.steps)
+    assert sim.sync(check=False) == 0, sim.last_error()
+    info = sim.get_info()
+    assert info["fused_kernel_name"] == "k_fused_vec_tma" and info["box_kernel_name"] == "k_hm_box_res", info
+    worst = {}
+    for fid in range(19):
+        a, b = sim.get_field(fid), ref.get_field(fid)
+        if fid >= 15:   # PML split parts against the component they belong to
+            scale = np.linalg.norm(ref.get_field({15: 0, 16: 1, 17: 3, 18: 4}[fid]))
+            worst[fid] = float(np.linalg.norm(a - b) / scale)
+        else:
+            worst[fid] = rel_l2(a, b)
+    print("ragged guide FP32 vs oracle:", {k: "%.2e" % v for k, v in worst.items()})
+    assert max(worst[f] for f in range(3)) <= RAGGED_TOL["E"], worst
+    assert max(worst[f] for f in range(3, 6)) <= RAGGED_TOL["H"], worst
+    assert max(worst[f] for f in range(6, 15)) <= RAGGED_TOL["M"], worst
+    assert max(worst[f] for f in range(15, 19)) <= RAGGED_TOL["PML"], worst
+    np.testing.assert_array_equal(sim.get_iter_log(), ref.iter_log())
+
