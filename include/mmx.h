@@ -203,6 +203,14 @@ MMX_API int mmx_get_stats(mmx_ctx *ctx, mmx_stats *out);
  * earlier work is returned first, without the check. */
 MMX_API int mmx_check_bounded_wait(mmx_ctx *ctx);
 
+/* Guard check: every device array the context allocates for its state,
+ * coefficients, box records and work lists is followed by 256 bytes of a
+ * fixed pattern; this reads them all back.  Returns MMX_OK when every guard
+ * is intact, MMX_ERR_INVALID (with a message naming how many arrays and the
+ * size of the first) when a kernel wrote past the end of an array, or
+ * MMX_ERR_CUDA.  Synchronises the context's stream; no kernel is launched. */
+MMX_API int mmx_check_guards(mmx_ctx *ctx);
+
 /* Failure-detection test hook (the failure is made on the host, no GPU
  * fault): the next mmx_step call starts as if a bounded wait had given up in
  * its first launch, with MMX_ERR_TIMEOUT latched in the device status word

@@ -95,6 +95,8 @@ struct mmx_ctx {
     void *bM[9] = {}, *bHit[2][3] = {}, *bHit2[2][3] = {};
     void *fcst = nullptr, *fmn = nullptr, *fbc = nullptr, *fdm[2] = {};   // per magnetic face (list order)
     void *bms[3] = {}, *bk1[3] = {}, *bk2[3] = {};
+    // arrays placed by dalloc, each with its guard bytes after `second` bytes
+    std::vector<std::pair<void *, size_t>> guards;
     int4 *dmag = nullptr, *dnon = nullptr;
     unsigned *dmag32 = nullptr;   // the magnetic list's packed first words
     int nmag = 0, nnon = 0;
@@ -268,11 +270,33 @@ static dim3 node_grid(const mmx_ctx *c)
     return dim3((c->desc.n[0] + 1 + 31) / 32, (c->desc.n[1] + 1 + 7) / 8, c->desc.n[2] + 1);
 }
 
+// Every array dalloc places is followed by kGuardBytes of a fixed pattern;
+// mmx_check_guards reads them back, so that a kernel writing past the end
+// of one of the context's arrays is caught (the canary check of the tests,
+// in place of a memory sanitizer).
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xC3;
+
 static int dalloc(mmx_ctx *ctx, void **p, size_t bytes)
 {
-    CK(cudaMalloc(p, bytes > 0 ? bytes : 1));
-    CK(cudaMemsetAsync(*p, 0, bytes > 0 ? bytes : 1, ctx->stream));
+    const size_t n = bytes > 0 ? bytes : 1;
+    CK(cudaMalloc(p, n + kGuardBytes));
+    CK(cudaMemsetAsync(*p, 0, n, ctx->stream));
+    CK(cudaMemsetAsync((unsigned char *)*p + n, kGuardByte, kGuardBytes, ctx->stream));
+    ctx->guards.push_back({*p, n});
     return MMX_OK;
+}
+
+// Free an array dalloc placed before the context ends (its guard goes too).
+static void dfree(mmx_ctx *ctx, void *p)
+{
+    if (!p) return;
+    for (size_t q = 0; q < ctx->guards.size(); q++)
+        if (ctx->guards[q].first == p) {
+            ctx->guards.erase(ctx->guards.begin() + (long)q);
+            break;
+        }
+    cudaFree(p);
 }
 
 template <typename T, typename S = T> static Fields<T, S> make_fields(mmx_ctx *c)
@@ -425,7 +449,7 @@ static int ensure_stage(mmx_ctx *ctx, size_t elems)
 
 static void free_box(mmx_ctx *c)
 {
-    for (void *p : c->box_allocs) cudaFree(p);
+    for (void *p : c->box_allocs) dfree(c, p);
     c->box_allocs.clear();
     c->magnetic = false;
     c->nb = 0;
@@ -1860,9 +1884,9 @@ int mmx_set_materials(mmx_ctx *ctx, const double *eps_r, const double *sigma, co
     size_t fb = ctx->npad * ctx->esz;
     for (int a = 0; a < 3; a++) {
         if (any_sigma && !ctx->ca[a]) { int rc = dalloc(ctx, &ctx->ca[a], fb); if (rc) return rc; }
-        if (!any_sigma && ctx->ca[a]) { cudaFree(ctx->ca[a]); ctx->ca[a] = nullptr; }
+        if (!any_sigma && ctx->ca[a]) { dfree(ctx, ctx->ca[a]); ctx->ca[a] = nullptr; }
         if (any_mu && !ctx->fh[a]) { int rc = dalloc(ctx, &ctx->fh[a], fb); if (rc) return rc; }
-        if (!any_mu && ctx->fh[a]) { cudaFree(ctx->fh[a]); ctx->fh[a] = nullptr; }
+        if (!any_mu && ctx->fh[a]) { dfree(ctx, ctx->fh[a]); ctx->fh[a] = nullptr; }
     }
     ctx->any_sigma = any_sigma;
     ctx->any_mu = any_mu;
@@ -2144,6 +2168,29 @@ int mmx_set_fused_staging(mmx_ctx *ctx, int bulk)
         ctx->bulk_staging = bulk;
         ctx->vec_chunk = 0;     // plan the vectorised pass again at the next step
     }
+    return MMX_OK;
+}
+
+int mmx_check_guards(mmx_ctx *ctx)
+{
+    if (!ctx || !ctx->E[0]) return MMX_ERR_INVALID;
+    CK(cudaStreamSynchronize(ctx->stream));
+    unsigned char h[kGuardBytes];
+    int bad = 0;
+    size_t first = 0;
+    for (size_t q = 0; q < ctx->guards.size(); q++) {
+        const unsigned char *g = (const unsigned char *)ctx->guards[q].first + ctx->guards[q].second;
+        CK(cudaMemcpy(h, g, kGuardBytes, cudaMemcpyDeviceToHost));
+        for (size_t u = 0; u < kGuardBytes; u++)
+            if (h[u] != kGuardByte) {
+                if (!bad) first = q;
+                bad++;
+                break;
+            }
+    }
+    if (bad)
+        return fail(ctx, MMX_ERR_INVALID, "%d of %zu device arrays were written past their end (first: %zu bytes)",
+                    bad, ctx->guards.size(), ctx->guards[first].second);
     return MMX_OK;
 }
 
