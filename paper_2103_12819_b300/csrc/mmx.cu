@@ -2,6 +2,7 @@
 // lifetime, device memory, material/field setup and the per-step launch
 // sequence of the coupled Maxwell-LLG scheme (arXiv 2103.12819, Sec. 3).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -155,6 +156,7 @@ struct mmx_ctx {
     long long prof_launches[KK_COUNT] = {};
     double prof_ms[KK_COUNT] = {};
     int prof_open = -1;
+    bool nvtx_open = false;  // an NVTX range of the current launch is open
 };
 
 // ------------------------------------------------------------- helpers
@@ -203,8 +205,13 @@ static cudaEvent_t prof_event(mmx_ctx *c)
 }
 
 // Bracket the next launch with events when profiling is enabled.
+// Every timed launch is also an NVTX range named like its profile entry, so
+// that a timeline tool shows the kernels of a step by name (the calls do
+// nothing when no tool is attached).
 static void prof_begin(mmx_ctx *c, int kind)
 {
+    nvtxRangePushA(kKernelNames[kind]);
+    c->nvtx_open = true;
     if (!c->prof_on) return;
     ProfRec r;
     r.kind = kind;
@@ -217,6 +224,10 @@ static void prof_begin(mmx_ctx *c, int kind)
 
 static void prof_end(mmx_ctx *c)
 {
+    if (c->nvtx_open) {
+        nvtxRangePop();
+        c->nvtx_open = false;
+    }
     if (!c->prof_on || c->prof_open < 0) return;
     cudaEventRecord(c->prof_recs[c->prof_open].b, c->stream);
     c->prof_open = -1;
