@@ -188,6 +188,14 @@ MMX_API int mmx_step(mmx_ctx *ctx, int nsteps);
  * Reading the status clears it. */
 MMX_API int mmx_sync(mmx_ctx *ctx);
 
+/* Set the count of full time steps done, the time t = steps dt at which the
+ * next step starts (the source waveforms are evaluated from it).  With
+ * mmx_get_field / mmx_set_field over every field id (E, H, the 9 M
+ * components and the PML split parts) this restores a checkpoint into a
+ * context built with the same descriptor, materials, bias and sources.
+ * MMX_ERR_INVALID for steps < 0. */
+MMX_API int mmx_set_step_count(mmx_ctx *ctx, long long steps);
+
 /* Statistics since creation; synchronises. */
 MMX_API int mmx_get_stats(mmx_ctx *ctx, mmx_stats *out);
 

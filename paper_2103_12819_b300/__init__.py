@@ -63,7 +63,7 @@ class KernelProfile(ctypes.Structure):
 EXPORTS = ("mmx_create", "mmx_set_materials", "mmx_set_bias", "mmx_set_M_cells", "mmx_set_field",
            "mmx_get_field", "mmx_get_material", "mmx_add_source", "mmx_set_path", "mmx_step",
            "mmx_sync", "mmx_get_stats", "mmx_get_iter_log", "mmx_get_field_device", "mmx_check_bounded_wait",
-           "mmx_check_guards",
+           "mmx_check_guards", "mmx_set_step_count",
            "mmx_inject_timeout", "mmx_get_info", "mmx_set_fused_staging", "mmx_kernel_binary_version",
            "mmx_set_box_kernel",
            "mmx_flux_gradient", "mmx_set_storage_scale", "mmx_add_probe", "mmx_get_probes", "mmx_energy", "mmx_add_flux_plane", "mmx_get_flux",
@@ -119,6 +119,8 @@ def lib():
     L.mmx_check_bounded_wait.argtypes = [P]
     L.mmx_check_guards.restype = I
     L.mmx_check_guards.argtypes = [P]
+    L.mmx_set_step_count.restype = I
+    L.mmx_set_step_count.argtypes = [P, LL]
     L.mmx_inject_timeout.restype = I
     L.mmx_inject_timeout.argtypes = [P]
     L.mmx_get_info.restype = I
@@ -305,6 +307,11 @@ class Solver:
         """Run the device-wait check (mmx_check_bounded_wait); returns its code,
         -6 (TIMEOUT) when both bounded waits gave up as designed."""
         return self._L.mmx_check_bounded_wait(self._h)
+
+    def set_step_count(self, steps):
+        """Set the steps done (the time the next step starts from), to resume
+        from a checkpoint taken with get_field (mmx_set_step_count)."""
+        self._check(self._L.mmx_set_step_count(self._h, int(steps)), "mmx_set_step_count")
 
     def check_guards(self):
         """Read back the guard bytes after every device array of the context

@@ -2238,6 +2238,13 @@ int mmx_kernel_binary_version(void)
     return a.binaryVersion;
 }
 
+int mmx_set_step_count(mmx_ctx *ctx, long long steps)
+{
+    if (!ctx || !ctx->E[0] || steps < 0) return MMX_ERR_INVALID;
+    ctx->steps = steps;
+    return MMX_OK;
+}
+
 int mmx_get_stats(mmx_ctx *ctx, mmx_stats *out)
 {
     if (!ctx || !ctx->E[0] || !out) return MMX_ERR_INVALID;
