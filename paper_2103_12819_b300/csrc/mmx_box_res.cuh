@@ -117,7 +117,7 @@ __device__ MMX_RES_FN Q4<T> llg_solve_rt(V3<T> mn, V3<T> bt, V3<T> he, T kap, T 
     T uxb[3] = {u[1] * beta[2] - u[2] * beta[1], u[2] * beta[0] - u[0] * beta[2], u[0] * beta[1] - u[1] * beta[0]};
     T mxb[3] = {Mn[1] * beta[2] - Mn[2] * beta[1], Mn[2] * beta[0] - Mn[0] * beta[2],
                 Mn[0] * beta[1] - Mn[1] * beta[0]};
-    T inv = T(1) / (T(1) + uu + T(2) * s * p + s * s * m2);
+    T inv = llg_rcp(T(1) + uu + T(2) * s * p + s * s * m2);
     T del[3];
 #pragma unroll
     for (int c = 0; c < 3; c++)
@@ -127,8 +127,8 @@ __device__ MMX_RES_FN Q4<T> llg_solve_rt(V3<T> mn, V3<T> bt, V3<T> he, T kap, T 
     T dd = del[0] * del[0] + del[1] * del[1] + del[2] * del[2];
     T q0 = -(T(2) * md + dd);
     T qv = e0 + q0;
-    T xn = sqrt(Ms * Ms - qv);
-    T den = T(1) / (xn * (Ms + xn));
+    T xn = llg_sqrt(Ms * Ms - qv);
+    T den = llg_rcp(xn * (Ms + xn));
     T sm1 = qv * den;
     T dM[3];
 #pragma unroll
@@ -153,8 +153,8 @@ __device__ MMX_RES_FN Q4<T> llg_euler_rt(V3<T> mn, V3<T> he, T c1, T c2, T Ms, T
     T dd = del[0] * del[0] + del[1] * del[1] + del[2] * del[2];
     T q0 = -(T(2) * md + dd);
     T qv = e0 + q0;
-    T xn = sqrt(Ms * Ms - qv);
-    T den = T(1) / (xn * (Ms + xn));
+    T xn = llg_sqrt(Ms * Ms - qv);
+    T den = llg_rcp(xn * (Ms + xn));
     T sm1 = qv * den;
     T dM[3];
 #pragma unroll

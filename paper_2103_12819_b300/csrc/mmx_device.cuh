@@ -423,6 +423,28 @@ __device__ __forceinline__ float norm_defect(float Ms, float mx, float my, float
     return s + c;
 }
 
+// The quotient and square root of the FP32 LLG solve in the hardware's
+// approximate forms (reciprocal and square root to about 2 ulp).  Their
+// error enters the increment delta and the N() correction relative to
+// those small terms, not relative to |M|; FP64 keeps the IEEE forms.
+template <typename T> __device__ __forceinline__ T llg_rcp(T x)
+{
+    return T(1) / x;
+}
+template <> __device__ __forceinline__ float llg_rcp<float>(float x)
+{
+    return __fdividef(1.0f, x);
+}
+template <typename T> __device__ __forceinline__ T llg_sqrt(T x)
+{
+    return sqrt(x);
+}
+template <> __device__ __forceinline__ float llg_sqrt<float>(float x)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // N(M^n + delta) - M^n without cancellation against |M| ~ Ms:
 // DeltaM = delta + (delta + M^n)(s - 1), s - 1 = q/(|x|(Ms + |x|)),
@@ -438,8 +460,8 @@ __device__ __forceinline__ void renormalised_increment(const T Mn[3], const T de
     T dd = del[0] * del[0] + del[1] * del[1] + del[2] * del[2];
     T q0 = -(T(2) * md + dd);
     T qv = e0 + q0;
-    T xn = sqrt(Ms * Ms - qv);
-    T den = T(1) / (xn * (Ms + xn));
+    T xn = llg_sqrt(Ms * Ms - qv);
+    T den = llg_rcp(xn * (Ms + xn));
     T sm1 = qv * den;
 #pragma unroll
     for (int c = 0; c < 3; c++) dM[c] = del[c] + (del[c] + Mn[c]) * sm1;
@@ -474,7 +496,7 @@ __device__ __forceinline__ void llg_iterate(const T Mn[3], const T beta[3], cons
     T uxb[3] = {u[1] * beta[2] - u[2] * beta[1], u[2] * beta[0] - u[0] * beta[2], u[0] * beta[1] - u[1] * beta[0]};
     T mxb[3] = {Mn[1] * beta[2] - Mn[2] * beta[1], Mn[2] * beta[0] - Mn[0] * beta[2],
                 Mn[0] * beta[1] - Mn[1] * beta[0]};
-    T inv = T(1) / (T(1) + uu + T(2) * s * p + s * s * m2);
+    T inv = llg_rcp(T(1) + uu + T(2) * s * p + s * s * m2);
     T del[3];
 #pragma unroll
     for (int c = 0; c < 3; c++)
