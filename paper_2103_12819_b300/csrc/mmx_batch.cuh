@@ -112,13 +112,13 @@ __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const i
         T rv;
         if (fo.d == 0) {
             first_load<0, SECOND>(I.g, I.f, I.b, Hin, Hp, I.b.dm[fp], fo, tl, in);
-            rv = first_finish<0, ORD>(I.g, I.b, W1, fo, tl, in, h0);
+            rv = first_finish<0, SECOND, ORD>(I.g, I.b, W1, fo, tl, in, h0);
         } else if (fo.d == 1) {
             first_load<1, SECOND>(I.g, I.f, I.b, Hin, Hp, I.b.dm[fp], fo, tl, in);
-            rv = first_finish<1, ORD>(I.g, I.b, W1, fo, tl, in, h0);
+            rv = first_finish<1, SECOND, ORD>(I.g, I.b, W1, fo, tl, in, h0);
         } else {
             first_load<2, SECOND>(I.g, I.f, I.b, Hin, Hp, I.b.dm[fp], fo, tl, in);
-            rv = first_finish<2, ORD>(I.g, I.b, W1, fo, tl, in, h0);
+            rv = first_finish<2, SECOND, ORD>(I.g, I.b, W1, fo, tl, in, h0);
         }
         if (rv > T(0)) atomicMax(&sh.res[qi], (unsigned long long)__double_as_longlong((double)rv));
     }

@@ -133,9 +133,9 @@ template <typename T> struct Box {
     T *Hit2[2][3];      // H iterates of the second half step of a launch
     // per magnetic face, in the order of the magnetic-face list:
     const Q4<T> *cst;   // Ms, k1, k2, 1/Ms
-    Q4<T> *mn;          // M^n, e0 = Ms^2 - |M^n|^2
+    Q4<T> *mn;          // M^n (w unused)
     Q4<T> *bc;          // beta = -kappa M^n x Heff^n, C' = H^n - dt/(2 mu0) curl E
-    Q4<T> *dm[2];       // iterates of DeltaM = M^r - M^n
+    Q4<T> *dm[2];       // iterates of DeltaM = M^r - M^n; w: e0 = Ms^2 - |M^n|^2
     const T *ms[3];     // Ms on faces
     const T *k1[3];     // order 2: kappa = mu0|gamma|dt/4; order 1: (dt/2) mu0 gamma_L
     const T *k2[3];     // order 2: alpha/Ms;               order 1: (dt/2) alpha mu0 gamma_L / Ms

@@ -629,9 +629,11 @@ __device__ __forceinline__ void first_load(const Geo &g, const Fields<T, S> &f, 
 }
 
 // Arithmetic and stores of phase 0: C' = H^n - dt/(2 mu0) curl E,
-// beta = -kappa M^n x H_eff^n, e0 and DeltaM^1; H^1 into Hw.  Returns
-// max_c |DeltaM^1_c| / Ms.
-template <int D, int ORD = 0, typename T>
+// beta = -kappa M^n x H_eff^n, e0 and DeltaM^1; H^1 into Hw.  e0 rides in
+// the w slot of the increment record, which every iterate rewrites anyway,
+// so a first half step (SECOND false, M^n unchanged in its record) writes
+// no M record.  Returns max_c |DeltaM^1_c| / Ms.
+template <int D, bool SECOND, int ORD = 0, typename T>
 __device__ __forceinline__ T first_finish(const Geo &g, const Box<T> &b, T *const Hw[3], const FaceOf &fo, int t,
                                           const FirstIn<T> &in, const T h0[3])
 {
@@ -653,8 +655,8 @@ __device__ __forceinline__ T first_finish(const Geo &g, const Box<T> &b, T *cons
         llg_euler(Mn, heff, k1, k2, Ms, e0, D, dM, dMh);
     }
     b.bc[t] = q4(beta[0], beta[1], beta[2], cp);
-    b.mn[t] = q4(Mn[0], Mn[1], Mn[2], e0);
-    b.dm[1][t] = q4(dM[0], dM[1], dM[2], T(0));
+    if (SECOND) b.mn[t] = q4(Mn[0], Mn[1], Mn[2], T(0));
+    b.dm[1][t] = q4(dM[0], dM[1], dM[2], e0);
     const bool wall = wall_node(g, D, D == 0 ? fo.i : D == 1 ? fo.j : fo.k);
     Hw[D][fo.l] = wall ? T(0) : cp - dMh;
     return max(abs(dM[0]), max(abs(dM[1]), abs(dM[2]))) * in.cs.w;
@@ -689,8 +691,9 @@ __device__ __forceinline__ void next_load(const Geo &g, const Box<T> &b, const F
     h_vector<D>(g, b, Hprev, Hprev, 1, fo.i, fo.j, fo.k, in.h);
 }
 
-// Iterate r >= 2 from the neighbours' iterate r-1: DeltaM^r into dm[cr], H^r
-// into Hcur; returns max_c |DeltaM^r_c - DeltaM^(r-1)_c| / Ms.
+// Iterate r >= 2 from the neighbours' iterate r-1: DeltaM^r into dm[cr]
+// (e0 carried on in its w slot), H^r into Hcur; returns
+// max_c |DeltaM^r_c - DeltaM^(r-1)_c| / Ms.
 template <int D, typename T>
 __device__ __forceinline__ T next_finish(const Geo &g, const Box<T> &b, const FaceOf &fo, int t, T *const Hcur[3],
                                          int cr, const NextIn<T> &in, const T h0[3])
@@ -702,10 +705,10 @@ __device__ __forceinline__ T next_finish(const Geo &g, const Box<T> &b, const Fa
 #pragma unroll
     for (int c = 0; c < 3; c++) heff[c] = h0[c] + in.h[c];
     T dM[3], dMh;
-    llg_iterate(Mn, beta, heff, k1, k2, Ms, in.mq.w, D, dM, dMh);
+    llg_iterate(Mn, beta, heff, k1, k2, Ms, in.pq.w, D, dM, dMh);
     const bool wall = wall_node(g, D, D == 0 ? fo.i : D == 1 ? fo.j : fo.k);
     Hcur[D][fo.l] = wall ? T(0) : in.bq.w - dMh;
-    b.dm[cr][t] = q4(dM[0], dM[1], dM[2], T(0));
+    b.dm[cr][t] = q4(dM[0], dM[1], dM[2], in.pq.w);
     return max(abs(dM[0] - in.pq.x), max(abs(dM[1] - in.pq.y), abs(dM[2] - in.pq.z))) * in.cs.w;
 }
 
@@ -787,13 +790,13 @@ __device__ int hm_half_step(const Geo &g, const Fields<T, S> &f, const Box<T> &b
             T rv;
             if (fo.d == 0) {
                 first_load<0, SECOND>(g, f, b, Hin, Hp, dmp, fo, t, in);
-                rv = first_finish<0, ORD>(g, b, W1, fo, t, in, h0);
+                rv = first_finish<0, SECOND, ORD>(g, b, W1, fo, t, in, h0);
             } else if (fo.d == 1) {
                 first_load<1, SECOND>(g, f, b, Hin, Hp, dmp, fo, t, in);
-                rv = first_finish<1, ORD>(g, b, W1, fo, t, in, h0);
+                rv = first_finish<1, SECOND, ORD>(g, b, W1, fo, t, in, h0);
             } else {
                 first_load<2, SECOND>(g, f, b, Hin, Hp, dmp, fo, t, in);
-                rv = first_finish<2, ORD>(g, b, W1, fo, t, in, h0);
+                rv = first_finish<2, SECOND, ORD>(g, b, W1, fo, t, in, h0);
             }
             rmax = max(rmax, rv);
         }
