@@ -27,7 +27,7 @@ template <typename T, typename S> struct BoxInst {
 struct BatchShared {
     unsigned long long *res;   // [ninst] block partial residuals (bit patterns)
     int *done;                 // [ninst] iteration the instance stopped at (0: active)
-    int *fprev;                // [ninst] final iterate parity of the previous half step
+    int *fprev;                // [ninst] iterate the previous half step stopped at
 };
 
 __device__ __forceinline__ void batch_publish(const BatchShared &sh, int ninst, unsigned long long *res, int r,
@@ -112,13 +112,13 @@ __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const i
         T rv;
         if (fo.d == 0) {
             first_load<0, SECOND>(I.g, I.f, I.b, Hin, Hp, I.b.dm[fp], fo, tl, in);
-            rv = first_finish<0, SECOND, ORD>(I.g, I.b, W1, fo, tl, in, h0);
+            rv = first_finish<0, SECOND, ORD>(I.g, I.b, W1, fo, tl, in, h0, sh.fprev[qi] > 1);
         } else if (fo.d == 1) {
             first_load<1, SECOND>(I.g, I.f, I.b, Hin, Hp, I.b.dm[fp], fo, tl, in);
-            rv = first_finish<1, SECOND, ORD>(I.g, I.b, W1, fo, tl, in, h0);
+            rv = first_finish<1, SECOND, ORD>(I.g, I.b, W1, fo, tl, in, h0, sh.fprev[qi] > 1);
         } else {
             first_load<2, SECOND>(I.g, I.f, I.b, Hin, Hp, I.b.dm[fp], fo, tl, in);
-            rv = first_finish<2, SECOND, ORD>(I.g, I.b, W1, fo, tl, in, h0);
+            rv = first_finish<2, SECOND, ORD>(I.g, I.b, W1, fo, tl, in, h0, sh.fprev[qi] > 1);
         }
         if (rv > T(0)) atomicMax(&sh.res[qi], (unsigned long long)__double_as_longlong((double)rv));
     }
@@ -129,30 +129,48 @@ __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const i
     while (more && r < kMaxIter) {
         r++;
         const int pr = (r - 1) & 1, cr = r & 1;
-        for (int t = t0; t < nmag; t += stride) {
-            const int qi = mag_inst[t];
-            if (sh.done[qi]) continue;
-            const BoxInst<T, S> &I = inst[qi];
-            const int tl = t - I.base_mag;
-            T *const Wp[3] = {SECOND ? I.b.Hit2[pr][0] : I.b.Hit[pr][0], SECOND ? I.b.Hit2[pr][1] : I.b.Hit[pr][1],
-                              SECOND ? I.b.Hit2[pr][2] : I.b.Hit[pr][2]};
-            T *const Wc[3] = {SECOND ? I.b.Hit2[cr][0] : I.b.Hit[cr][0], SECOND ? I.b.Hit2[cr][1] : I.b.Hit[cr][1],
-                              SECOND ? I.b.Hit2[cr][2] : I.b.Hit[cr][2]};
-            const T h0[3] = {(T)I.b.h0[0], (T)I.b.h0[1], (T)I.b.h0[2]};
-            const FaceOf fo = face_of(mag[t]);
-            NextIn<T> in;
-            T rv;
-            if (fo.d == 0) {
-                next_load<0>(I.g, I.b, fo, tl, Wp, pr, in);
-                rv = next_finish<0>(I.g, I.b, fo, tl, Wc, cr, in, h0);
-            } else if (fo.d == 1) {
-                next_load<1>(I.g, I.b, fo, tl, Wp, pr, in);
-                rv = next_finish<1>(I.g, I.b, fo, tl, Wc, cr, in, h0);
-            } else {
-                next_load<2>(I.g, I.b, fo, tl, Wp, pr, in);
-                rv = next_finish<2>(I.g, I.b, fo, tl, Wc, cr, in, h0);
+        // one copy of the sweep per source of beta and C' (RecomputeBC), each
+        // register-allocated on its own: the record, or at iterate 2 of an
+        // instance whose phase 0 stored none, beta and C' formed again
+        auto sweep = [&](auto have) {
+            constexpr bool HB = decltype(have)::value;
+            for (int t = t0; t < nmag; t += stride) {
+                const int qi = mag_inst[t];
+                if (sh.done[qi]) continue;
+                if (RecomputeBC<T>::value && (sh.fprev[qi] > 1 || r > 2) != HB) continue;
+                const BoxInst<T, S> &I = inst[qi];
+                const int tl = t - I.base_mag;
+                T *const Wp[3] = {SECOND ? I.b.Hit2[pr][0] : I.b.Hit[pr][0], SECOND ? I.b.Hit2[pr][1] : I.b.Hit[pr][1],
+                                  SECOND ? I.b.Hit2[pr][2] : I.b.Hit[pr][2]};
+                T *const Wc[3] = {SECOND ? I.b.Hit2[cr][0] : I.b.Hit[cr][0], SECOND ? I.b.Hit2[cr][1] : I.b.Hit[cr][1],
+                                  SECOND ? I.b.Hit2[cr][2] : I.b.Hit[cr][2]};
+                const T h0[3] = {(T)I.b.h0[0], (T)I.b.h0[1], (T)I.b.h0[2]};
+                const int fp = sh.fprev[qi] & 1;
+                T *const Hp[3] = {I.b.Hit[fp][0], I.b.Hit[fp][1], I.b.Hit[fp][2]};
+                S *const Hin[3] = {I.f.H[0], I.f.H[1], I.f.H[2]};
+                const FaceOf fo = face_of(mag[t]);
+                NextIn<T> in;
+                T rv;
+                if (fo.d == 0) {
+                    next_load<0, SECOND, HB>(I.g, I.b, fo, tl, Wp, pr, in, &I.f, Hin, Hp);
+                    rv = next_finish<0, HB>(I.g, I.b, fo, tl, Wc, cr, in, h0);
+                } else if (fo.d == 1) {
+                    next_load<1, SECOND, HB>(I.g, I.b, fo, tl, Wp, pr, in, &I.f, Hin, Hp);
+                    rv = next_finish<1, HB>(I.g, I.b, fo, tl, Wc, cr, in, h0);
+                } else {
+                    next_load<2, SECOND, HB>(I.g, I.b, fo, tl, Wp, pr, in, &I.f, Hin, Hp);
+                    rv = next_finish<2, HB>(I.g, I.b, fo, tl, Wc, cr, in, h0);
+                }
+                if (rv > T(0)) atomicMax(&sh.res[qi], (unsigned long long)__double_as_longlong((double)rv));
             }
-            if (rv > T(0)) atomicMax(&sh.res[qi], (unsigned long long)__double_as_longlong((double)rv));
+        };
+        sweep(std::true_type{});
+        if (RecomputeBC<T>::value && r == 2) {
+            // the second copy only where an active instance has no record
+            int rc = 0;
+            for (int q = threadIdx.x; q < ninst; q += blockDim.x)
+                if (!sh.done[q] && sh.fprev[q] <= 1) rc = 1;
+            if (__syncthreads_or(rc)) sweep(std::false_type{});
         }
         batch_publish(sh, ninst, res, r, W);
         if (!grid_barrier(bar, berr)) return false;
@@ -228,7 +246,15 @@ __global__ void __launch_bounds__(256, BoxMinBlocks<T>::value)
         unsigned long long *other = res + 2 * (1 - slot) * rows;
         for (size_t q = threadIdx.x; q < 2 * rows; q += blockDim.x) other[q] = 0ull;
     }
-    for (int q = threadIdx.x; q < ninst; q += blockDim.x) sh.fprev[q] = 0;
+    // each instance's last logged iterate count (2 when none is): read
+    // before block 0 logs this launch's first half step, which it does only
+    // after that half step's grid barriers, which every block joins after
+    // this
+    for (int q = threadIdx.x; q < ninst; q += blockDim.x) {
+        const Box<T> &bq = inst[q].b;
+        const unsigned long long hs = *bq.halfsteps;
+        sh.fprev[q] = hs == 0 ? 2 : bq.iterlog[(hs - 1) % kIterLogCap];
+    }
     __syncthreads();
     unsigned long long *r0 = res + 2 * slot * rows;
     if (nsub == 2) {

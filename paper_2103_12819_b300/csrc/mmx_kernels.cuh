@@ -599,9 +599,55 @@ template <typename T> struct FirstIn {
     T h[3];
 };
 
-// Loads of phase 0 on a magnetic face of family D (list position t): H^n is
+// Where the iterates r >= 2 get beta and C'.  Phase 0 stores them in a
+// 16-byte record per face for the iterates to read back.  The batched launch
+// in FP32 skips that store for an instance whose previous half step stopped
+// at its first iterate (then this one most likely does too, and the record
+// would never be read); an iterate 2 of such an instance forms beta and C'
+// again from H^n and E and stores them for any later iterate.  The
+// single-instance launches always keep the record: the second copy of the
+// iterate sweep would cost them instruction fetch where the box is
+// L2-resident, and their benchmark boxes take two iterates per half step.
+// FP64, bound by its arithmetic, always keeps the record.
+template <typename T> struct RecomputeBC {
+    static constexpr bool value = sizeof(T) == 4;
+};
+
+// C' = H^n - dt/(2 mu0) curl E (curl E = rest + zp) and
+// beta = -kappa M^n x H_eff^n: one expression each for phase 0 and for the
+// iterates that form them again, so both round alike.
+template <typename T> __device__ __forceinline__ T c_prime(const Box<T> &b, T hn, T rest, T zp)
+{
+    return hn - b.cfar * (rest + zp);
+}
+
+template <typename T> __device__ __forceinline__ void beta_of(const T Mn[3], const T heff[3], T k1, T beta[3])
+{
+    beta[0] = -k1 * (Mn[1] * heff[2] - Mn[2] * heff[1]);
+    beta[1] = -k1 * (Mn[2] * heff[0] - Mn[0] * heff[2]);
+    beta[2] = -k1 * (Mn[0] * heff[1] - Mn[1] * heff[0]);
+}
+
+// The H^n and curl E loads of phase 0 on a magnetic face of family D: H^n is
 // the global H (SECOND false) or the previous half step's box-local iterate
-// Hp (SECOND true); M^n is the face record, plus the previous half step's
+// Hp (SECOND true); h gets the four-point H vector at the face.
+template <int D, bool SECOND, typename T, typename S>
+__device__ __forceinline__ void hn_loads(const Geo &g, const Fields<T, S> &f, const Box<T> &b, S *const Hin[3],
+                                         T *const Hp[3], const FaceOf &fo, T &hn, T &rest, T &zp, T h[3])
+{
+    const unsigned q = gidx32(g, fo.i, fo.j, fo.k);
+    curl_e32(g, f.E, f.inv_d, D, q, rest, zp, f.sE);
+    if (SECOND) {
+        hn = Hp[D][fo.l];
+        h_vector<D>(g, b, Hin, Hp, 1, fo.i, fo.j, fo.k, h);
+    } else {
+        hn = ld_s(Hin[D] + q, f.sH);
+        h_vector<D>(g, b, Hin, Hp, 0, fo.i, fo.j, fo.k, h, f.sH);
+    }
+}
+
+// Loads of phase 0 on a magnetic face of family D (list position t): H^n and
+// curl E as hn_loads; M^n is the face record, plus the previous half step's
 // converged increment dmp when SECOND.
 template <int D, bool SECOND, typename T, typename S>
 __device__ __forceinline__ void first_load(const Geo &g, const Fields<T, S> &f, const Box<T> &b, S *const Hin[3],
@@ -609,37 +655,33 @@ __device__ __forceinline__ void first_load(const Geo &g, const Fields<T, S> &f, 
                                            FirstIn<T> &in)
 {
     in.cs = q4_load(b.cst + t);
-    const unsigned q = gidx32(g, fo.i, fo.j, fo.k);
-    curl_e32(g, f.E, f.inv_d, D, q, in.rest, in.zp, f.sE);
     const Q4<T> m0 = q4_load(b.mn + t);
     if (SECOND) {
         const Q4<T> d0 = q4_load(dmp + t);
         in.Mn[0] = m0.x + d0.x;
         in.Mn[1] = m0.y + d0.y;
         in.Mn[2] = m0.z + d0.z;
-        in.hn = Hp[D][fo.l];
-        h_vector<D>(g, b, Hin, Hp, 1, fo.i, fo.j, fo.k, in.h);
     } else {
         in.Mn[0] = m0.x;
         in.Mn[1] = m0.y;
         in.Mn[2] = m0.z;
-        in.hn = ld_s(Hin[D] + q, f.sH);
-        h_vector<D>(g, b, Hin, Hp, 0, fo.i, fo.j, fo.k, in.h, f.sH);
     }
+    hn_loads<D, SECOND>(g, f, b, Hin, Hp, fo, in.hn, in.rest, in.zp, in.h);
 }
 
 // Arithmetic and stores of phase 0: C' = H^n - dt/(2 mu0) curl E,
 // beta = -kappa M^n x H_eff^n, e0 and DeltaM^1; H^1 into Hw.  e0 rides in
 // the w slot of the increment record, which every iterate rewrites anyway,
 // so a first half step (SECOND false, M^n unchanged in its record) writes
-// no M record.  Returns max_c |DeltaM^1_c| / Ms.
+// no M record; the {beta, C'} record is stored when store_bc is true (see
+// RecomputeBC).  Returns max_c |DeltaM^1_c| / Ms.
 template <int D, bool SECOND, int ORD = 0, typename T>
 __device__ __forceinline__ T first_finish(const Geo &g, const Box<T> &b, T *const Hw[3], const FaceOf &fo, int t,
-                                          const FirstIn<T> &in, const T h0[3])
+                                          const FirstIn<T> &in, const T h0[3], bool store_bc = true)
 {
     const T Ms = in.cs.x, k1 = in.cs.y, k2 = in.cs.z;
     const T *Mn = in.Mn;
-    const T cp = in.hn - b.cfar * (in.rest + in.zp);
+    const T cp = c_prime(b, in.hn, in.rest, in.zp);
     const T e0 = norm_defect(Ms, Mn[0], Mn[1], Mn[2]);
     T heff[3];
 #pragma unroll
@@ -647,14 +689,12 @@ __device__ __forceinline__ T first_finish(const Geo &g, const Box<T> &b, T *cons
     T dM[3], dMh;
     T beta[3] = {T(0), T(0), T(0)};
     if (ORD == 0 ? b.order == 2 : ORD == 2) {
-        beta[0] = -k1 * (Mn[1] * heff[2] - Mn[2] * heff[1]);
-        beta[1] = -k1 * (Mn[2] * heff[0] - Mn[0] * heff[2]);
-        beta[2] = -k1 * (Mn[0] * heff[1] - Mn[1] * heff[0]);
+        beta_of(Mn, heff, k1, beta);
         llg_iterate(Mn, beta, heff, k1, k2, Ms, e0, D, dM, dMh);
     } else {
         llg_euler(Mn, heff, k1, k2, Ms, e0, D, dM, dMh);
     }
-    b.bc[t] = q4(beta[0], beta[1], beta[2], cp);
+    if (!RecomputeBC<T>::value || store_bc) b.bc[t] = q4(beta[0], beta[1], beta[2], cp);
     if (SECOND) b.mn[t] = q4(Mn[0], Mn[1], Mn[2], T(0));
     b.dm[1][t] = q4(dM[0], dM[1], dM[2], e0);
     const bool wall = wall_node(g, D, D == 0 ? fo.i : D == 1 ? fo.j : fo.k);
@@ -674,40 +714,59 @@ __device__ __forceinline__ void non_first(const Geo &g, const Fields<T, S> &f, S
     W1[D][fo.l] = v;
 }
 
-// Everything iteration r reads for one magnetic face.
+// Everything iteration r reads for one magnetic face: the {beta, C'} record
+// bq, or (HAVE_BC false) what phase 0 formed it from.
 template <typename T> struct NextIn {
     Q4<T> cs, mq, bq, pq;
     T h[3];
+    T hn, rest, zp, hN[3];
 };
 
-template <int D, typename T>
+// Loads of iterate r on a magnetic face of family D; without the record
+// (HAVE_BC false) the H^n and curl E loads of phase 0 instead, with H^n
+// from Hin or Hp as in phase 0 (SECOND).
+template <int D, bool SECOND = false, bool HAVE_BC = true, typename T, typename S = T>
 __device__ __forceinline__ void next_load(const Geo &g, const Box<T> &b, const FaceOf &fo, int t, T *const Hprev[3],
-                                          int pr, NextIn<T> &in)
+                                          int pr, NextIn<T> &in, const Fields<T, S> *f = nullptr,
+                                          S *const *Hin = nullptr, T *const *Hp = nullptr)
 {
     in.cs = q4_load(b.cst + t);
     in.mq = q4_load(b.mn + t);
-    in.bq = q4_load(b.bc + t);
+    if constexpr (HAVE_BC)
+        in.bq = q4_load(b.bc + t);
+    else
+        hn_loads<D, SECOND>(g, *f, b, Hin, Hp, fo, in.hn, in.rest, in.zp, in.hN);
     in.pq = q4_load(b.dm[pr] + t);
     h_vector<D>(g, b, Hprev, Hprev, 1, fo.i, fo.j, fo.k, in.h);
 }
 
 // Iterate r >= 2 from the neighbours' iterate r-1: DeltaM^r into dm[cr]
-// (e0 carried on in its w slot), H^r into Hcur; returns
+// (e0 carried on in its w slot), H^r into Hcur; without the record
+// (HAVE_BC false) beta and C' are formed first and stored.  Returns
 // max_c |DeltaM^r_c - DeltaM^(r-1)_c| / Ms.
-template <int D, typename T>
+template <int D, bool HAVE_BC = true, typename T>
 __device__ __forceinline__ T next_finish(const Geo &g, const Box<T> &b, const FaceOf &fo, int t, T *const Hcur[3],
                                          int cr, const NextIn<T> &in, const T h0[3])
 {
     const T Ms = in.cs.x, k1 = in.cs.y, k2 = in.cs.z;
     const T Mn[3] = {in.mq.x, in.mq.y, in.mq.z};
-    const T beta[3] = {in.bq.x, in.bq.y, in.bq.z};
+    Q4<T> bq = in.bq;
+    if constexpr (!HAVE_BC) {
+        T heffn[3], bt[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) heffn[c] = h0[c] + in.hN[c];
+        beta_of(Mn, heffn, k1, bt);
+        bq = q4(bt[0], bt[1], bt[2], c_prime(b, in.hn, in.rest, in.zp));
+        b.bc[t] = bq;
+    }
+    const T beta[3] = {bq.x, bq.y, bq.z};
     T heff[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) heff[c] = h0[c] + in.h[c];
     T dM[3], dMh;
     llg_iterate(Mn, beta, heff, k1, k2, Ms, in.pq.w, D, dM, dMh);
     const bool wall = wall_node(g, D, D == 0 ? fo.i : D == 1 ? fo.j : fo.k);
-    Hcur[D][fo.l] = wall ? T(0) : in.bq.w - dMh;
+    Hcur[D][fo.l] = wall ? T(0) : bq.w - dMh;
     b.dm[cr][t] = q4(dM[0], dM[1], dM[2], in.pq.w);
     return max(abs(dM[0] - in.pq.x), max(abs(dM[1] - in.pq.y), abs(dM[2] - in.pq.z))) * in.cs.w;
 }
