@@ -2466,7 +2466,8 @@ struct mmx_batch {
     int nwork = 0;
     // box launch
     void *binst[2] = {};                   // BoxInst<T, S>[ninst] per parity
-    int4 *mag = nullptr, *non = nullptr;
+    unsigned long long *mag = nullptr;   // packed magnetic-face list (k_pack_faces)
+    int4 *non = nullptr;
     int *mag_inst = nullptr, *non_inst = nullptr;
     int nmag = 0, nnon = 0;
     unsigned long long *res = nullptr, *bar = nullptr;
@@ -2572,7 +2573,10 @@ template <typename T, typename S> static int batch_box_setup(mmx_batch *b)
     if (nm >= (1LL << 31) || nn >= (1LL << 31)) return bfail(b, MMX_ERR_INVALID, "batch has too many box faces");
     b->nmag = (int)nm;
     b->nnon = (int)nn;
-    int rc = balloc(b, (void **)&b->mag, (size_t)std::max(1LL, nm) * sizeof(int4));
+    for (mmx_ctx *c : b->ctx)
+        for (int a = 0; a < 3; a++)
+            if (c->desc.n[a] >= (1 << 20)) return bfail(b, MMX_ERR_INVALID, "batched instance wider than 2^20 - 1 cells");
+    int rc = balloc(b, (void **)&b->mag, (size_t)std::max(1LL, nm) * sizeof(unsigned long long));
     if (!rc) rc = balloc(b, (void **)&b->non, (size_t)std::max(1LL, nn) * sizeof(int4));
     if (!rc) rc = balloc(b, (void **)&b->mag_inst, (size_t)std::max(1LL, nm) * sizeof(int));
     if (!rc) rc = balloc(b, (void **)&b->non_inst, (size_t)std::max(1LL, nn) * sizeof(int));
@@ -2586,9 +2590,10 @@ template <typename T, typename S> static int batch_box_setup(mmx_batch *b)
     for (int q = 0; q < ninst; q++) {
         mmx_ctx *c = b->ctx[q];
         if (!c->magnetic) continue;
-        if (c->nmag)
-            BCK(cudaMemcpyAsync(b->mag + om, c->dmag, (size_t)c->nmag * sizeof(int4), cudaMemcpyDeviceToDevice,
-                                b->stream));
+        if (c->nmag) {
+            k_pack_faces<<<(unsigned)((c->nmag + 255) / 256), 256, 0, b->stream>>>(c->dmag, b->mag + om, c->nmag);
+            BCK(cudaGetLastError());
+        }
         if (c->nnon)
             BCK(cudaMemcpyAsync(b->non + on, c->dnon, (size_t)c->nnon * sizeof(int4), cudaMemcpyDeviceToDevice,
                                 b->stream));

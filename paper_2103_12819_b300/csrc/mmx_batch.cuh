@@ -24,6 +24,32 @@ template <typename T, typename S> struct BoxInst {
 };
 
 // Per-block state of a batched half step, in dynamic shared memory.
+// The batched magnetic-face list packs each entry into 8 bytes,
+// d << 60 | i << 40 | j << 20 | k (every index below 2^20), half the 16-byte
+// entry {l | d << 30, i, j, k} of the single-instance lists; the box index l
+// comes back from i, j, k and the instance's box with multiply-adds, so the
+// neighbour addresses (from i, j, k) wait on no load of the instance.
+__global__ void k_pack_faces(const int4 *__restrict__ in, unsigned long long *__restrict__ out, int n)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int4 e = in[t];
+    out[t] = (unsigned long long)((unsigned)e.x >> 30) << 60 | (unsigned long long)(unsigned)e.y << 40 |
+             (unsigned long long)(unsigned)e.z << 20 | (unsigned long long)(unsigned)e.w;
+}
+
+template <typename T> __device__ __forceinline__ FaceOf face_of64(unsigned long long e, const Box<T> &b)
+{
+    FaceOf fo;
+    fo.d = (int)(e >> 60);
+    fo.i = (int)((e >> 40) & 0xfffffu);
+    fo.j = (int)((e >> 20) & 0xfffffu);
+    fo.k = (int)(e & 0xfffffu);
+    fo.l = (unsigned)(fo.i - b.lo[0]) +
+           (unsigned)b.bx * ((unsigned)(fo.j - b.lo[1]) + (unsigned)b.by * (unsigned)(fo.k - b.lo[2]));
+    return fo;
+}
+
 struct BatchShared {
     unsigned long long *res;   // [ninst] block partial residuals (bit patterns)
     int *done;                 // [ninst] iteration the instance stopped at (0: active)
@@ -64,7 +90,8 @@ __device__ __forceinline__ bool batch_update(const BatchShared &sh, const BoxIns
 
 // ORD: the scheme order of every instance (2 or 1), or 0 when they differ.
 template <bool SECOND, bool WRITE, int ORD, typename T, typename S>
-__device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const int4 *mag, const int *mag_inst,
+__device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const unsigned long long *mag,
+                                   const int *mag_inst,
                                    int nmag, const int4 *non, const int *non_inst, int nnon,
                                    unsigned long long *res, unsigned long long *bar, int *berr,
                                    const BatchShared &sh)
@@ -107,7 +134,7 @@ __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const i
         T *const Hp[3] = {I.b.Hit[fp][0], I.b.Hit[fp][1], I.b.Hit[fp][2]};
         S *const Hin[3] = {I.f.H[0], I.f.H[1], I.f.H[2]};
         const T h0[3] = {(T)I.b.h0[0], (T)I.b.h0[1], (T)I.b.h0[2]};
-        const FaceOf fo = face_of(mag[t]);
+        const FaceOf fo = face_of64(mag[t], I.b);
         FirstIn<T> in;
         T rv;
         if (fo.d == 0) {
@@ -148,7 +175,7 @@ __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const i
                 const int fp = sh.fprev[qi] & 1;
                 T *const Hp[3] = {I.b.Hit[fp][0], I.b.Hit[fp][1], I.b.Hit[fp][2]};
                 S *const Hin[3] = {I.f.H[0], I.f.H[1], I.f.H[2]};
-                const FaceOf fo = face_of(mag[t]);
+                const FaceOf fo = face_of64(mag[t], I.b);
                 NextIn<T> in;
                 T rv;
                 if (fo.d == 0) {
@@ -200,7 +227,7 @@ __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const i
             T *const Hfin[3] = {SECOND ? I.b.Hit2[fr][0] : I.b.Hit[fr][0], SECOND ? I.b.Hit2[fr][1] : I.b.Hit[fr][1],
                                 SECOND ? I.b.Hit2[fr][2] : I.b.Hit[fr][2]};
             S *const Ho[3] = {I.Hout.p[0], I.Hout.p[1], I.Hout.p[2]};
-            const FaceOf fo = face_of(mag[t]);
+            const FaceOf fo = face_of64(mag[t], I.b);
             ok &= fo.d == 0   ? mag_store<0>(I.g, I.b, fo, tl, Hfin, Ho, fr, I.f.isH)
                   : fo.d == 1 ? mag_store<1>(I.g, I.b, fo, tl, Hfin, Ho, fr, I.f.isH)
                               : mag_store<2>(I.g, I.b, fo, tl, Hfin, Ho, fr, I.f.isH);
@@ -230,7 +257,7 @@ __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const i
 // the other parity's rows are cleared here for the next launch.
 template <typename T, typename S = T, int ORD = 0>
 __global__ void __launch_bounds__(256, BoxMinBlocks<T>::value)
-    k_hm_box_batch(const BoxInst<T, S> *__restrict__ inst, int ninst, const int4 *__restrict__ mag,
+    k_hm_box_batch(const BoxInst<T, S> *__restrict__ inst, int ninst, const unsigned long long *__restrict__ mag,
                    const int *__restrict__ mag_inst, int nmag, const int4 *__restrict__ non,
                    const int *__restrict__ non_inst, int nnon, unsigned long long *res, unsigned long long *bar,
                    int *berr, int nsub, int slot)
