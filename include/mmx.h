@@ -397,9 +397,10 @@ MMX_API int mmx_get_profile(mmx_ctx *ctx, mmx_kernel_profile *out, int cap, int 
  * keep them alive and not step them through mmx_step while a batch call is
  * in flight).  All instances must share the precision and the PML /
  * conductive-or-permeable variant, have PEC x and y walls, no hard sources,
- * probes or flux planes, and fewer than 2^20 cells along every axis (the
- * batched magnetic-face list packs each face's indices into 8 bytes);
- * otherwise MMX_ERR_INVALID (with *out holding a batch
+ * probes or flux planes, and fewer than 65536 cells along every axis, with
+ * count at most 16384 (the batched magnetic-face list packs each face's
+ * indices and instance into 8 bytes); otherwise MMX_ERR_INVALID (with *out
+ * holding a batch
  * usable only with mmx_batch_last_error and mmx_batch_destroy).  Between
  * batch calls every instance can be read, written and stepped on its own.
  * cuda_stream is the batch's stream (NULL: the batch creates and owns a

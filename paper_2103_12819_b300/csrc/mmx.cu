@@ -2468,7 +2468,7 @@ struct mmx_batch {
     void *binst[2] = {};                   // BoxInst<T, S>[ninst] per parity
     unsigned long long *mag = nullptr;   // packed magnetic-face list (k_pack_faces)
     int4 *non = nullptr;
-    int *mag_inst = nullptr, *non_inst = nullptr;
+    int *non_inst = nullptr;
     int nmag = 0, nnon = 0;
     unsigned long long *res = nullptr, *bar = nullptr;
     int *err = nullptr;
@@ -2564,7 +2564,7 @@ static void batch_box_grid(mmx_batch *b)
 template <typename T, typename S> static int batch_box_setup(mmx_batch *b)
 {
     const int ninst = (int)b->ctx.size();
-    std::vector<int> mi, ni;
+    std::vector<int> ni;
     long long nm = 0, nn = 0;
     for (mmx_ctx *c : b->ctx) {
         nm += c->magnetic ? c->nmag : 0;
@@ -2575,34 +2575,31 @@ template <typename T, typename S> static int batch_box_setup(mmx_batch *b)
     b->nnon = (int)nn;
     for (mmx_ctx *c : b->ctx)
         for (int a = 0; a < 3; a++)
-            if (c->desc.n[a] >= (1 << 20)) return bfail(b, MMX_ERR_INVALID, "batched instance wider than 2^20 - 1 cells");
+            if (c->desc.n[a] >= (1 << 16)) return bfail(b, MMX_ERR_INVALID, "batched instance wider than 65535 cells");
+    if (ninst > (1 << 14)) return bfail(b, MMX_ERR_INVALID, "more than 16384 batched instances");
     int rc = balloc(b, (void **)&b->mag, (size_t)std::max(1LL, nm) * sizeof(unsigned long long));
     if (!rc) rc = balloc(b, (void **)&b->non, (size_t)std::max(1LL, nn) * sizeof(int4));
-    if (!rc) rc = balloc(b, (void **)&b->mag_inst, (size_t)std::max(1LL, nm) * sizeof(int));
     if (!rc) rc = balloc(b, (void **)&b->non_inst, (size_t)std::max(1LL, nn) * sizeof(int));
     if (!rc) rc = balloc(b, (void **)&b->res, 4 * (size_t)ninst * (kMaxIter + 1) * sizeof(unsigned long long));
     if (!rc) rc = balloc(b, (void **)&b->bar, kBarWords * sizeof(unsigned long long));
     if (!rc) rc = balloc(b, (void **)&b->err, sizeof(int));
     if (rc) return rc;
     long long om = 0, on = 0;
-    mi.reserve(nm);
     ni.reserve(nn);
     for (int q = 0; q < ninst; q++) {
         mmx_ctx *c = b->ctx[q];
         if (!c->magnetic) continue;
         if (c->nmag) {
-            k_pack_faces<<<(unsigned)((c->nmag + 255) / 256), 256, 0, b->stream>>>(c->dmag, b->mag + om, c->nmag);
+            k_pack_faces<<<(unsigned)((c->nmag + 255) / 256), 256, 0, b->stream>>>(c->dmag, b->mag + om, c->nmag, q);
             BCK(cudaGetLastError());
         }
         if (c->nnon)
             BCK(cudaMemcpyAsync(b->non + on, c->dnon, (size_t)c->nnon * sizeof(int4), cudaMemcpyDeviceToDevice,
                                 b->stream));
-        mi.insert(mi.end(), c->nmag, q);
         ni.insert(ni.end(), c->nnon, q);
         om += c->nmag;
         on += c->nnon;
     }
-    if (nm) BCK(cudaMemcpyAsync(b->mag_inst, mi.data(), mi.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     if (nn) BCK(cudaMemcpyAsync(b->non_inst, ni.data(), ni.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     BCK(cudaStreamSynchronize(b->stream));
     b->box_smem = (size_t)ninst * (sizeof(unsigned long long) + 2 * sizeof(int));
@@ -2778,7 +2775,7 @@ template <typename T, typename S> static int batch_enqueue(mmx_batch *b, int nst
         if (b->magnetic) {
             const BoxInst<T, S> *inst = (const BoxInst<T, S> *)b->binst[p];
             int nsub = nhalf, slot = s & 1;
-            void *args[] = {(void *)&inst,       (void *)&ninst,       (void *)&b->mag, (void *)&b->mag_inst,
+            void *args[] = {(void *)&inst,       (void *)&ninst,       (void *)&b->mag,
                             (void *)&b->nmag,    (void *)&b->non,      (void *)&b->non_inst, (void *)&b->nnon,
                             (void *)&b->res,     (void *)&b->bar,      (void *)&b->err, (void *)&nsub,
                             (void *)&slot};

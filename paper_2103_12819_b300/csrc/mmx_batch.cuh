@@ -24,27 +24,34 @@ template <typename T, typename S> struct BoxInst {
 };
 
 // Per-block state of a batched half step, in dynamic shared memory.
-// The batched magnetic-face list packs each entry into 8 bytes,
-// d << 60 | i << 40 | j << 20 | k (every index below 2^20), half the 16-byte
-// entry {l | d << 30, i, j, k} of the single-instance lists; the box index l
+// The batched magnetic-face list packs each entry and its instance q into
+// 8 bytes, d << 62 | q << 48 | i << 32 | j << 16 | k (q below 2^14, every
+// index below 2^16), against 20 bytes for the single-instance entry
+// {l | d << 30, i, j, k} and a separate instance index; the box index l
 // comes back from i, j, k and the instance's box with multiply-adds, so the
 // neighbour addresses (from i, j, k) wait on no load of the instance.
-__global__ void k_pack_faces(const int4 *__restrict__ in, unsigned long long *__restrict__ out, int n)
+__global__ void k_pack_faces(const int4 *__restrict__ in, unsigned long long *__restrict__ out, int n, int q)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     const int4 e = in[t];
-    out[t] = (unsigned long long)((unsigned)e.x >> 30) << 60 | (unsigned long long)(unsigned)e.y << 40 |
-             (unsigned long long)(unsigned)e.z << 20 | (unsigned long long)(unsigned)e.w;
+    out[t] = (unsigned long long)((unsigned)e.x >> 30) << 62 | (unsigned long long)(unsigned)q << 48 |
+             (unsigned long long)(unsigned)e.y << 32 | (unsigned long long)(unsigned)e.z << 16 |
+             (unsigned long long)(unsigned)e.w;
+}
+
+__device__ __forceinline__ int inst_of64(unsigned long long e)
+{
+    return (int)((e >> 48) & 0x3fffu);
 }
 
 template <typename T> __device__ __forceinline__ FaceOf face_of64(unsigned long long e, const Box<T> &b)
 {
     FaceOf fo;
-    fo.d = (int)(e >> 60);
-    fo.i = (int)((e >> 40) & 0xfffffu);
-    fo.j = (int)((e >> 20) & 0xfffffu);
-    fo.k = (int)(e & 0xfffffu);
+    fo.d = (int)(e >> 62);
+    fo.i = (int)((e >> 32) & 0xffffu);
+    fo.j = (int)((e >> 16) & 0xffffu);
+    fo.k = (int)(e & 0xffffu);
     fo.l = (unsigned)(fo.i - b.lo[0]) +
            (unsigned)b.bx * ((unsigned)(fo.j - b.lo[1]) + (unsigned)b.by * (unsigned)(fo.k - b.lo[2]));
     return fo;
@@ -91,7 +98,6 @@ __device__ __forceinline__ bool batch_update(const BatchShared &sh, const BoxIns
 // ORD: the scheme order of every instance (2 or 1), or 0 when they differ.
 template <bool SECOND, bool WRITE, int ORD, typename T, typename S>
 __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const unsigned long long *mag,
-                                   const int *mag_inst,
                                    int nmag, const int4 *non, const int *non_inst, int nnon,
                                    unsigned long long *res, unsigned long long *bar, int *berr,
                                    const BatchShared &sh)
@@ -125,7 +131,8 @@ __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const u
             non_first<2, SECOND>(I.g, I.f, Hin, Hp, W0, W1, fo);
     }
     for (int t = t0; t < nmag; t += stride) {
-        const int qi = mag_inst[t];
+        const unsigned long long e = mag[t];
+        const int qi = inst_of64(e);
         const BoxInst<T, S> &I = inst[qi];
         const int tl = t - I.base_mag;
         const int fp = sh.fprev[qi] & 1;
@@ -134,7 +141,7 @@ __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const u
         T *const Hp[3] = {I.b.Hit[fp][0], I.b.Hit[fp][1], I.b.Hit[fp][2]};
         S *const Hin[3] = {I.f.H[0], I.f.H[1], I.f.H[2]};
         const T h0[3] = {(T)I.b.h0[0], (T)I.b.h0[1], (T)I.b.h0[2]};
-        const FaceOf fo = face_of64(mag[t], I.b);
+        const FaceOf fo = face_of64(e, I.b);
         FirstIn<T> in;
         T rv;
         if (fo.d == 0) {
@@ -162,7 +169,8 @@ __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const u
         auto sweep = [&](auto have) {
             constexpr bool HB = decltype(have)::value;
             for (int t = t0; t < nmag; t += stride) {
-                const int qi = mag_inst[t];
+                const unsigned long long e = mag[t];
+                const int qi = inst_of64(e);
                 if (sh.done[qi]) continue;
                 if (RecomputeBC<T>::value && (sh.fprev[qi] > 1 || r > 2) != HB) continue;
                 const BoxInst<T, S> &I = inst[qi];
@@ -175,7 +183,7 @@ __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const u
                 const int fp = sh.fprev[qi] & 1;
                 T *const Hp[3] = {I.b.Hit[fp][0], I.b.Hit[fp][1], I.b.Hit[fp][2]};
                 S *const Hin[3] = {I.f.H[0], I.f.H[1], I.f.H[2]};
-                const FaceOf fo = face_of64(mag[t], I.b);
+                const FaceOf fo = face_of64(e, I.b);
                 NextIn<T> in;
                 T rv;
                 if (fo.d == 0) {
@@ -220,14 +228,15 @@ __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const u
             ok &= isfinite(v);
         }
         for (int t = t0; t < nmag; t += stride) {
-            const int qi = mag_inst[t];
+            const unsigned long long e = mag[t];
+            const int qi = inst_of64(e);
             const BoxInst<T, S> &I = inst[qi];
             const int tl = t - I.base_mag;
             const int fr = sh.done[qi] & 1;
             T *const Hfin[3] = {SECOND ? I.b.Hit2[fr][0] : I.b.Hit[fr][0], SECOND ? I.b.Hit2[fr][1] : I.b.Hit[fr][1],
                                 SECOND ? I.b.Hit2[fr][2] : I.b.Hit[fr][2]};
             S *const Ho[3] = {I.Hout.p[0], I.Hout.p[1], I.Hout.p[2]};
-            const FaceOf fo = face_of64(mag[t], I.b);
+            const FaceOf fo = face_of64(e, I.b);
             ok &= fo.d == 0   ? mag_store<0>(I.g, I.b, fo, tl, Hfin, Ho, fr, I.f.isH)
                   : fo.d == 1 ? mag_store<1>(I.g, I.b, fo, tl, Hfin, Ho, fr, I.f.isH)
                               : mag_store<2>(I.g, I.b, fo, tl, Hfin, Ho, fr, I.f.isH);
@@ -258,7 +267,7 @@ __device__ bool hm_half_step_batch(const BoxInst<T, S> *inst, int ninst, const u
 template <typename T, typename S = T, int ORD = 0>
 __global__ void __launch_bounds__(256, BoxMinBlocks<T>::value)
     k_hm_box_batch(const BoxInst<T, S> *__restrict__ inst, int ninst, const unsigned long long *__restrict__ mag,
-                   const int *__restrict__ mag_inst, int nmag, const int4 *__restrict__ non,
+                   int nmag, const int4 *__restrict__ non,
                    const int *__restrict__ non_inst, int nnon, unsigned long long *res, unsigned long long *bar,
                    int *berr, int nsub, int slot)
 {
@@ -285,13 +294,13 @@ __global__ void __launch_bounds__(256, BoxMinBlocks<T>::value)
     __syncthreads();
     unsigned long long *r0 = res + 2 * slot * rows;
     if (nsub == 2) {
-        if (!hm_half_step_batch<false, false, ORD>(inst, ninst, mag, mag_inst, nmag, non, non_inst, nnon, r0, bar, berr,
+        if (!hm_half_step_batch<false, false, ORD>(inst, ninst, mag, nmag, non, non_inst, nnon, r0, bar, berr,
                                               sh))
             return;
-        hm_half_step_batch<true, true, ORD>(inst, ninst, mag, mag_inst, nmag, non, non_inst, nnon, r0 + rows, bar, berr,
+        hm_half_step_batch<true, true, ORD>(inst, ninst, mag, nmag, non, non_inst, nnon, r0 + rows, bar, berr,
                                        sh);
     } else {
-        hm_half_step_batch<false, true, ORD>(inst, ninst, mag, mag_inst, nmag, non, non_inst, nnon, r0, bar, berr, sh);
+        hm_half_step_batch<false, true, ORD>(inst, ninst, mag, nmag, non, non_inst, nnon, r0, bar, berr, sh);
     }
 }
 
