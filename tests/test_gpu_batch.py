@@ -59,6 +59,20 @@ def test_batch_refuses_mismatched_instances():
         mmx.Batch([a, a])                                  # the same context twice
 
 
+def test_batch_refuses_an_instance_wider_than_its_packed_face_indices():
+    """The batched magnetic-face list keeps i, j, k in 16 bits each: an
+    instance 65536 cells long (magnetic along its whole length) is refused
+    with MMX_ERR_INVALID (-1) and a message naming the limit when the batch
+    is created; one a cell shorter is accepted."""
+    small = mmx.from_workload(W.random_small(41, n=(8, 6, 7), tol=1e-6), prec=mmx.FP32)
+    wide = mmx.from_workload(W.random_small(42, n=(65536, 2, 2), tol=1e-6), prec=mmx.FP32)
+    with pytest.raises(mmx.MMXError) as ei:
+        mmx.Batch([small, wide])
+    assert ei.value.code == -1 and "65535" in str(ei.value), ei.value
+    ok = mmx.from_workload(W.random_small(43, n=(65535, 2, 2), tol=1e-6), prec=mmx.FP32)
+    mmx.Batch([small, ok]).close()
+
+
 def test_full_bias_sweep_2000_steps_fp32():
     specs = W.bias_sweep(256)
     sols = []
