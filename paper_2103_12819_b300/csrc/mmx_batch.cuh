@@ -23,7 +23,6 @@ template <typename T, typename S> struct BoxInst {
     int base_mag;       // first entry of the instance in the magnetic list
 };
 
-// Per-block state of a batched half step, in dynamic shared memory.
 // The batched magnetic-face list packs each entry and its instance q into
 // 8 bytes, d << 62 | q << 48 | i << 32 | j << 16 | k (q below 2^14, every
 // index below 2^16), against 20 bytes for the single-instance entry
@@ -57,6 +56,7 @@ template <typename T> __device__ __forceinline__ FaceOf face_of64(unsigned long 
     return fo;
 }
 
+// Per-block state of a batched half step, in dynamic shared memory.
 struct BatchShared {
     unsigned long long *res;   // [ninst] block partial residuals (bit patterns)
     int *done;                 // [ninst] iteration the instance stopped at (0: active)
