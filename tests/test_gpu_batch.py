@@ -9,6 +9,7 @@ import time
 import numpy as np
 import pytest
 
+import oracle
 import paper_2103_12819_b300 as mmx
 import workloads as W
 from conftest import rel_l2
@@ -57,6 +58,61 @@ def test_batch_refuses_mismatched_instances():
         mmx.Batch([a, p])                                  # periodic x
     with pytest.raises(mmx.MMXError):
         mmx.Batch([a, a])                                  # the same context twice
+
+
+def _first_to_second(log):
+    """Half steps that needed a second iterate right after one that stopped
+    at the first."""
+    log = np.asarray(log)
+    return int(np.sum((log[:-1] == 1) & (log[1:] >= 2)))
+
+
+def _median_first_residual(seed, steps):
+    """Median over `steps` steps of the oracle's first-iterate residual
+    (tolerance 1, so every half step stops at its first iterate; the value
+    read after each step is that of its second half step)."""
+    ref = oracle.from_workload(W.random_small(seed, n=(9, 7, 8), tol=1.0))
+    r1 = []
+    for _ in range(steps):
+        ref.step(1)
+        r1.append(ref.last_residual)
+    return float(np.median(r1))
+
+
+def test_batch_forms_beta_and_c_prime_again_after_a_first_iterate_stop_fp32():
+    """In FP32 the batched launch stores no {beta, C'} record for an instance
+    whose last half step stopped at its first iterate; if the next half step
+    needs a second iterate, that iterate forms beta and C' again from H^n and
+    E.  Random small instances whose tolerance is the median of their own
+    first-iterate residual (from the oracle) stop at the first iterate for a
+    stretch of steps and then need the second again, so the path runs.  The
+    batch matches the instances stepped on their own: a wrong beta or C'
+    would move M by about the first-iterate residual (5e-4 of Ms) and H by
+    far more, while a residual that rounds to the other side of the
+    tolerance in one of the two runs moves them by the second-iterate
+    residual only, so the bar is 1e-5 and one log entry per instance may
+    differ."""
+    seeds = (44, 46, 47, 48, 50, 52)
+    ws = [W.random_small(q, n=(9, 7, 8), tol=_median_first_residual(q, 60)) for q in seeds]
+    batched = [mmx.from_workload(w, prec=mmx.FP32) for w in ws]
+    alone = [mmx.from_workload(w, prec=mmx.FP32) for w in ws]
+    b = mmx.Batch(batched)
+    for n in (25, 35):
+        b.step(n)
+        for s in alone:
+            s.step(n)
+    assert b.sync(check=False) == 0, b._L.mmx_batch_last_error(b._h)
+    switches = 0
+    for q, (x, y) in enumerate(zip(batched, alone)):
+        assert y.sync(check=False) == 0
+        for fid in range(15):
+            assert rel_l2(x.get_field(fid), y.get_field(fid)) <= 1e-5, (seeds[q], fid)
+        lx, ly = x.get_iter_log(), y.get_iter_log()
+        assert len(lx) == len(ly) == 120 and int(np.sum(lx != ly)) <= 1, (seeds[q], lx, ly)
+        switches += _first_to_second(lx)
+    print("half steps needing a second iterate right after a first-iterate stop:", switches)
+    assert switches >= 3, switches
+    b.close()
 
 
 def test_batch_refuses_an_instance_wider_than_its_packed_face_indices():
